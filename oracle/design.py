@@ -170,7 +170,7 @@ def oc_update(rho: np.ndarray, s: np.ndarray, vstar: float, move: float, damp: f
     def new(lam):
         return np.clip(rho * (B / lam) ** damp, lo, hi)
 
-    grow = B > 0.0
+    grow = (B > 0.0) & (rho > 0.0)       # elements whose update factor is non-zero
     v_full = np.where(grow, hi, lo).mean()
     if v_full <= vstar:
         return np.where(grow, hi, lo), 0.0

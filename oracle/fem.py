@@ -123,6 +123,53 @@ def apply_operator(n: int, k: np.ndarray, u: np.ndarray, K0: np.ndarray | None =
     return out
 
 
+def apply_operator_at(n: int, k: np.ndarray, u: np.ndarray, nodes, K0: np.ndarray | None = None) -> np.ndarray:
+    """[K u]_v (Sec. 2.4) at the listed nodes only: sum over the eight
+    incident elements e of k_e (K^0 u_e)_{loc(v, e)}.  u has shape (m, n^3);
+    returns (m, len(nodes)).  For sampled checks on grids too large to
+    assemble."""
+    if K0 is None:
+        K0 = k0_matrix()
+    u = np.atleast_2d(u)
+    out = np.zeros((u.shape[0], len(nodes)))
+    for j, v in enumerate(nodes):
+        x, y, z = v % n, (v // n) % n, v // (n * n)
+        for l in range(8):                      # v is local corner l of element v - offset(l)
+            a, b, c = corner_offset(l)
+            ex, ey, ez = (x - a) % n, (y - b) % n, (z - c) % n
+            e = ex + n * (ey + n * ez)
+            corners = []
+            for m in range(8):
+                am, bm, cm = corner_offset(m)
+                corners.append(((ex + am) % n) + n * (((ey + bm) % n) + n * ((ez + cm) % n)))
+            out[:, j] += k[e] * (u[:, corners] @ K0[l, :])
+    return out
+
+
+def gauss_seidel_pass(K: sp.csr_matrix, f: np.ndarray, T: np.ndarray, nodes) -> np.ndarray:
+    """One Gauss-Seidel relaxation over `nodes` in the given order
+    (Sec. 2.4): S_v T_v = f_v - M_v with S_v = K_vv and M_v the row of K
+    times T without the diagonal term.  Returns the updated copy of T."""
+    T = T.astype(np.float64).copy()
+    K = K.tocsr()
+    for v in nodes:
+        lo, hi = K.indptr[v], K.indptr[v + 1]
+        cols, vals = K.indices[lo:hi], K.data[lo:hi]
+        diag = vals[cols == v].sum()
+        m = vals @ T[cols] - diag * T[v]
+        T[v] = (f[v] - m) / diag
+    return T
+
+
+def colour_nodes(n: int, colour: int) -> np.ndarray:
+    """Nodes of colour (x%2) + 2(y%2) + 4(z%2) (the 8-colour ordering of
+    Sec. 2.4)."""
+    r = np.arange(n)
+    Z, Y, X = np.meshgrid(r, r, r, indexing="ij")
+    c = (X % 2) + 2 * (Y % 2) + 4 * (Z % 2)
+    return np.flatnonzero(c.ravel() == colour)
+
+
 def pcg(K: sp.csr_matrix, f: np.ndarray, tol: float = 1e-12, maxit: int | None = None,
         x0: np.ndarray | None = None):
     """Jacobi-preconditioned CG for the singular periodic system K x = f.

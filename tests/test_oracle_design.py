@@ -112,8 +112,8 @@ def _oc_exact(rho, s, vstar, move, damp, rho_min):
     lo = np.maximum(rho_min, rho - move)
     hi = np.minimum(1.0, rho + move)
     B = np.maximum(0.0, -s)
-    grow = B > 0
-    c = np.where(grow, rho * B ** damp, 0.0)
+    c = rho * B ** damp
+    grow = c > 0
     N = rho.size
     full = np.where(grow, hi, lo)
     if full.sum() <= vstar * N:
@@ -156,6 +156,16 @@ def test_oc_against_exact_breakpoint_solution(seed):
         assert active
     if active:
         assert abs(new.mean() - vstar) < 1e-9
+
+
+def test_oc_zero_density_stays_at_lower_bound():
+    """rho = 0 gives a zero update factor for every lambda, so the element
+    takes its lower bound even when the constraint is inactive."""
+    rho = np.array([0.0, 0.5])
+    s = np.array([-1.0, -1.0])
+    new, lam = design.oc_update(rho, s, 1.0, 0.05, 0.5, 1e-3)
+    assert lam == 0.0
+    assert np.allclose(new, [1e-3, 0.55])
 
 
 def test_oc_inactive_and_infeasible():

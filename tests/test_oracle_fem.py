@@ -283,3 +283,46 @@ def test_level_sizes():
     assert fem.level_sizes(16) == [16, 8, 4]
     assert fem.level_sizes(96) == [96, 48, 24, 12, 6]
     assert fem.level_sizes(6) == [6]
+
+
+def test_apply_operator_at_matches_full():
+    n = 5
+    k = _random_k(n, 15)
+    rng = np.random.default_rng(5)
+    u = rng.standard_normal((3, n ** 3))
+    full = fem.apply_operator(n, k, u)
+    nodes = [0, 7, 63, 124]
+    assert np.allclose(fem.apply_operator_at(n, k, u, nodes), full[:, nodes], atol=1e-13)
+
+
+def test_gauss_seidel_pass_zeroes_residual_on_colour():
+    """Nodes of one colour are uncoupled, so after one pass over them their
+    residual vanishes exactly (and the order within the colour is
+    irrelevant)."""
+    n = 6
+    k = _random_k(n, 16)
+    K = fem.assemble(n, k)
+    rng = np.random.default_rng(6)
+    f = rng.standard_normal(n ** 3)
+    T = rng.standard_normal(n ** 3)
+    for colour in range(8):
+        nodes = fem.colour_nodes(n, colour)
+        T1 = fem.gauss_seidel_pass(K, f, T, nodes)
+        T2 = fem.gauss_seidel_pass(K, f, T, nodes[::-1])
+        assert np.allclose(T1, T2, atol=1e-13)
+        r = f - K @ T1
+        assert np.max(np.abs(r[nodes])) < 1e-12
+        others = np.setdiff1d(np.arange(n ** 3), nodes)
+        assert np.array_equal(T1[others], T[others])
+
+
+def test_x_parity_pairs_are_uncoupled():
+    """Colours differing only in x parity share no matrix entry (face
+    neighbours carry 0), so a pass over colour 2c then 2c+1 equals one pass
+    over their union."""
+    n = 6
+    k = _random_k(n, 17)
+    K = fem.assemble(n, k).toarray()
+    for c in range(0, 8, 2):
+        a, b = fem.colour_nodes(n, c), fem.colour_nodes(n, c + 1)
+        assert np.max(np.abs(K[np.ix_(a, b)])) < 1e-15
