@@ -1,0 +1,306 @@
+/*
+ * otm.h -- C ABI of libotm.so: GB300 (sm_103a) periodic thermal-microstructure
+ * homogenization and optimality-criteria design, after Quan, Zhai & Fu,
+ * "OpenTM: an open-source, single-GPU, large-scale thermal microstructure
+ * design framework" (arXiv 2405.19991).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Grid: an n^3 periodic voxel unit cell, unit voxels, |Omega| = n^3.  A
+ *    scalar field is a flat array of n^3 values with x fastest: voxel
+ *    (x, y, z) is at x + n*(y + n*z).  Node (x, y, z) is the lower corner of
+ *    element (x, y, z); element (x, y, z) has corners ((x+a)%n, (y+b)%n,
+ *    (z+c)%n), local number a + 2b + 4c.  A three-load-case field is three
+ *    such arrays back to back (load case i at offset i*n^3).
+ *  - Tensors: 6-vectors in the order [k11, k22, k33, k12, k23, k13]
+ *    (Sec. 2.2, Eq. rep).
+ *  - Ownership: pointers passed in are borrowed for the duration of the call
+ *    only.  A context owns all device memory it allocates; outputs are
+ *    caller-allocated.  `on_device` = 1 means the pointer is device memory on
+ *    the context's device, 0 means host memory.
+ *  - Streams: work is ordered on the context's stream (params.stream, or a
+ *    stream the context creates when that is NULL).  Every call returns after
+ *    its work is complete (synchronous on the stream).
+ *  - Errors: no exception or abort crosses the ABI.  Every call returns an
+ *    otm_status; on failure otm_last_error(ctx) (or otm_last_error(NULL) for
+ *    calls without a context, thread-local) describes it.  A call that fails
+ *    with OTM_EINVAL has changed nothing.
+ *  - Threads: a context must not be used by two threads at once; distinct
+ *    contexts are independent.
+ */
+#ifndef OTM_H
+#define OTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define OTM_API __attribute__((visibility("default")))
+#else
+#define OTM_API
+#endif
+
+typedef enum otm_status {
+    OTM_OK = 0,
+    OTM_EINVAL = 1,    /* bad argument: size, pointer, parameter range */
+    OTM_ENOMEM = 2,    /* device or host allocation failed */
+    OTM_ECUDA = 3,     /* a CUDA runtime call or kernel failed */
+    OTM_ENOCONV = 4,   /* CG hit cg_maxit or broke down; results hold the best iterate */
+    OTM_ETIMEOUT = 5,  /* a bounded device wait ran out */
+    OTM_ESTATE = 6     /* call out of order, or a checkpoint blob that does not match */
+} otm_status;
+
+/* Arithmetic of the solve (params.precision). */
+enum {
+    OTM_FP64 = 0,   /* every field and operation in FP64 */
+    OTM_FP32 = 1,   /* FP32 fields and arithmetic; FP64 inner products, tensor and volume sums */
+    OTM_MIXED = 2   /* FP32 outer CG; V-cycle fields and operators stored in BF16, FP32 arithmetic */
+};
+
+/* Initial guess of each homogenization solve (params.warm_start). */
+enum {
+    OTM_WS_NONE = 0,    /* start from zero */
+    OTM_WS_PREV = 1,    /* start from the previous design iteration's solution */
+    OTM_WS_LEARNED = 2  /* start from the learned predictor, falling back to the better of zero/previous */
+};
+
+/* Objective g(kappa^H, kappa*) (params.objective). */
+enum {
+    OTM_OBJ_MSE = 0,      /* Eq. mse: sum over the 6 components of (kappa - kappa*)^2 */
+    OTM_OBJ_FRACMSE = 1,  /* Eq. fracmse: sum of (kappa/kappa* - 1)^2; a zero target component uses kappa^2 */
+    OTM_OBJ_L1 = 2        /* Eq. l1: sum of |kappa - kappa*|, d|a|/da = 0 at 0 */
+};
+
+/* Fields readable with otm_get_field. */
+enum {
+    OTM_FIELD_RHO = 0,        /* design density rho, n^3 */
+    OTM_FIELD_RHO_FILT = 1,   /* filtered density (Sec. 2.3), n^3 */
+    OTM_FIELD_K = 2,          /* SIMP element conductivity (Sec. 2.2), n^3 */
+    OTM_FIELD_CHI = 3,        /* the three solutions T^(i) of Eq. kti, 3 n^3, zero mean */
+    OTM_FIELD_LOAD = 4,       /* the three macro loads f^(i) (Sec. 2.4 enforceMacroLoad), 3 n^3 */
+    OTM_FIELD_SENS = 5        /* dg/drho after the filter chain rule (Eq. sens), n^3 */
+};
+
+/*
+ * Problem and solver parameters.  The problem statement follows the paper's
+ * HomoConfig / runInstance inputs (Sec. 3.4, 3.5): resolution, the two
+ * conductivities, the target tensor, the initial volume ratio; the OC
+ * parameters follow OCOptimizer(min_density, stepLimit, dampExponent)
+ * (Sec. 3.3) with the values of Sec. 4 (p = 3, r = 1.5, step 0.05, damping 0.5).
+ */
+typedef struct otm_params {
+    int n;                   /* voxels per side, 4 <= n <= 512; the multigrid
+                                hierarchy halves n while it is even and the half
+                                is >= 4, and the coarsest size must be <= 7 */
+    double kappa_target[6];  /* kappa*, must be symmetric positive definite */
+    double volfrac;          /* initial mean density (not a constraint, Sec. 3.4) */
+    double penal;            /* SIMP exponent p (Sec. 2.2), >= 1 */
+    double rmin;             /* density-filter radius in voxels, 1 <= rmin < 3 */
+    double k_solid, k_void;  /* kappa^0 and kappa_min of SIMP, k_solid > k_void > 0 */
+    double move;             /* OC step limit (stepLimit) */
+    double damp;             /* OC damping exponent eta (dampExponent) */
+    double rho_min;          /* OC minimum density (min_density) */
+    double cg_tol;           /* relative residual ||f - K x|| / ||f|| per load case */
+    int cg_maxit;            /* PCG iteration cap per solve */
+    int precision;           /* OTM_FP64 | OTM_FP32 | OTM_MIXED */
+    int warm_start;          /* OTM_WS_* */
+    int objective;           /* OTM_OBJ_* */
+    int governor;            /* 1: adaptive V* of Alg. 1 (model Eq. model3), 0: fixed V* = fixed_volume (Eq. model1) */
+    double fixed_volume;     /* V for governor = 0 */
+    double gov_bound;        /* Alg. 1 "bound" on g (default 1e-4) */
+    double gov_small_rel;    /* Alg. 1 is_small(g^[I-1] - g^[I]): |dg| < gov_small_rel * g (default 1e-3) */
+    double gov_vol_tol;      /* Alg. 1 is_small(V - V*): |V - V*| < gov_vol_tol (default 1e-2) */
+    int symmetry;            /* 1: central symmetry (Sec. 4.1), average rho and dg/drho over point-symmetric pairs */
+    int reserved0;
+    uint64_t seed;           /* seed of the learned predictor's initial weights */
+    void* stream;            /* cudaStream_t to order work on; NULL = context-owned stream */
+    int device;              /* CUDA device ordinal; -1 = current device */
+    int reserved1;
+} otm_params;
+
+/* Per design-iteration report. */
+typedef struct otm_step_info {
+    double g;             /* objective at the density the iteration started from */
+    double kappa[6];      /* kappa^H at that density */
+    double mean_rho;      /* V(rho) = mean rho (Sec. 2.3) */
+    double mean_rhop;     /* mean filtered rho^p, Alg. 1 lowBound */
+    double vstar;         /* volume bound used by the OC update */
+    double lambda;        /* OC Lagrange multiplier; 0 = constraint inactive, inf = all at lower bound */
+    int cg_iters[3];      /* PCG iterations per load case */
+    int iteration;        /* design iteration index (0-based) of this report */
+    double resid[3];      /* true relative residual per load case at exit */
+    float stage_ms[8];    /* filter+SIMP, load+coarse operators, solve, tensor+sensitivity, OC, -, -, total */
+    int kernel_launches;  /* CUDA kernels this call launched (graph kernel nodes counted per execution) */
+    int reserved;
+} otm_step_info;
+
+/* State of Alg. 1's adaptive volume bound. */
+typedef struct otm_governor_state {
+    double df;       /* decrease factor Df */
+    double vstar;    /* V* */
+    double g_prev;   /* g^[I-1] */
+    double gap;      /* last V* - lowBound */
+    int count;       /* consecutive stalled iterations */
+    int reserved;
+} otm_governor_state;
+
+typedef struct otm_ctx otm_ctx;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Fill p with the defaults: n = 128, kappa* = [0.1,0.1,0.1,0,0,0],
+ * volfrac 0.3, p = 3, r = 1.5, k = 1 / 1e-3, move 0.05, damp 0.5,
+ * rho_min 1e-3, cg_tol 1e-6, cg_maxit 500, OTM_FP32, OTM_WS_PREV, MSE,
+ * governor on (bound 1e-4, 1e-3, 1e-2), no symmetry, stream NULL, device -1. */
+OTM_API otm_status otm_params_default(otm_params* p);
+
+/* OTM_OK if the 6-vector is a symmetric positive definite tensor (every
+ * leading principal minor > 0; Sec. 4.2 uses the minors to bound the
+ * feasible cross terms), else OTM_EINVAL.  Host only. */
+OTM_API otm_status otm_check_target(const double kappa_target[6]);
+
+/* Create a context with the defaults of otm_params_default and the given
+ * problem (the call shape of the paper's problem statement: resolution,
+ * target tensor, volume fraction, SIMP exponent, filter radius).  The
+ * density is initialised to volfrac everywhere. */
+OTM_API otm_status otm_create(int n, const double kappa_target[6], double volfrac,
+                              double penal, double rmin, otm_ctx** out);
+
+/* Create a context from a full parameter block.  Allocates every device
+ * buffer of the solve (about 100 * n^3 bytes in OTM_FP32). */
+OTM_API otm_status otm_create_ex(const otm_params* params, otm_ctx** out);
+
+/* Release a context and all its device memory.  NULL is accepted. */
+OTM_API otm_status otm_destroy(otm_ctx* ctx);
+
+/* Copy a density field (n^3 floats, values clamped to [0, 1]) into the
+ * context and reset the design loop (iteration 0, Alg. 1 initial state,
+ * previous solution cleared). */
+OTM_API otm_status otm_set_density(otm_ctx* ctx, const float* rho, int on_device);
+
+/* Copy the current density (n^3 floats) out. */
+OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
+
+/* Copy one of the OTM_FIELD_* arrays (as of the last homogenize or step) out
+ * as floats; `count` must equal its length (n^3 or 3 n^3). */
+OTM_API otm_status otm_get_field(otm_ctx* ctx, int which, float* out, size_t count, int on_device);
+
+/*
+ * Homogenized conductivity of a density field (Sec. 2.2, discrete Eq. homo):
+ * filter (Sec. 2.3) -> SIMP -> macro loads (Sec. 2.4) -> MG-preconditioned CG
+ * for the three load cases (Sec. 2.4, Alg. 3) -> tensor.  rho = NULL uses the
+ * context's current density; otherwise rho (n^3 floats, host or device per
+ * on_device) is used for this call only and the current density is left
+ * unchanged.  kappa_out is a host array of 6 doubles.  info may be NULL.
+ * Returns OTM_ENOCONV if some load case missed cg_tol within cg_maxit
+ * (kappa_out still filled).
+ */
+OTM_API otm_status otm_homogenize(otm_ctx* ctx, const float* rho, int on_device,
+                                  double kappa_out[6], otm_step_info* info);
+
+/*
+ * One design iteration (Alg. 2 with the loop of Sec. 3.4 and model Eq.
+ * model3): homogenize the current density, objective and its gradient
+ * (Eq. sens with the filter chain rule), Alg. 1 volume bound, OC update of
+ * the density.  info may be NULL.  Returns OTM_ENOCONV when the solve missed
+ * cg_tol (the update is still applied).
+ */
+OTM_API otm_status otm_step(otm_ctx* ctx, otm_step_info* info);
+
+/* `iters` calls of otm_step; infos (may be NULL) receives one report each. */
+OTM_API otm_status otm_run(otm_ctx* ctx, int iters, otm_step_info* infos);
+
+/*
+ * Run `count` independent designs for `iters` iterations each.  params[d],
+ * rho0[d] (host, n_d^3 floats; NULL = uniform volfrac) describe design d;
+ * rho_out[d] (host, may be NULL), kappa_out[d] (may be NULL: the tensor of
+ * the last iteration) and infos[d*iters + i] (may be NULL) receive results.
+ * Returns the first non-OK status (designs after it are still attempted).
+ */
+OTM_API otm_status otm_design_batch(int count, const otm_params* params,
+                                    const float* const* rho0, int iters,
+                                    float* const* rho_out, double (*kappa_out)[6],
+                                    otm_step_info* infos);
+
+/* Checkpoint: serialise density, previous solution, Alg. 1 state and the
+ * iteration counter.  With buf == NULL, *len receives the size needed;
+ * otherwise *len must be at least that size. */
+OTM_API otm_status otm_get_state(otm_ctx* ctx, void* buf, size_t* len);
+
+/* Restore a blob written by otm_get_state for the same n and precision. */
+OTM_API otm_status otm_set_state(otm_ctx* ctx, const void* buf, size_t len);
+
+/* Last error message of ctx, or of this thread's context-less calls when
+ * ctx is NULL.  Never NULL. */
+OTM_API const char* otm_last_error(const otm_ctx* ctx);
+
+/* ------------------------------------------------------- host-side helpers */
+
+/* Initial state of Alg. 1: Df = 1, V* = 1, g^[0] = 1, gap = 0, count = 0. */
+OTM_API otm_status otm_governor_init(otm_governor_state* s);
+
+/* One pass of the loop body of Alg. 1 (Sec. 2.3) after the objective g of
+ * the current design is known: lowBound = mean filtered rho^p, vol = mean
+ * rho.  Uses p->gov_bound, gov_small_rel and gov_vol_tol.  Host only; the
+ * same function runs on the device inside otm_step. */
+OTM_API otm_status otm_governor_update(otm_governor_state* s, const otm_params* p,
+                                       double g, double low_bound, double vol);
+
+/* ------------------------------------------- operator-level entry points
+ * For testing and profiling single kernels.  All pointers are device
+ * pointers on the current device; `dtype` is OTM_FP32 (float arrays) or
+ * OTM_FP64 (double arrays); work is ordered on `stream` (cudaStream_t, NULL
+ * = legacy default stream) and completes before return.  Sizes: n as in
+ * otm_params, fields n^3, three-load-case fields 3 n^3.                   */
+
+/* Density filter of Sec. 2.3 with weight max(0, r - d) over the periodic
+ * neighbourhood d < r, followed by SIMP (Sec. 2.2):
+ * rho_f = W rho, k = k_void + rho_f^p (k_solid - k_void). */
+OTM_API otm_status otm_op_filter_simp(int dtype, int n, double rmin, double penal,
+                                      double k_solid, double k_void,
+                                      const void* rho, void* rho_f, void* k, void* stream);
+
+/* Transpose filter s = W^T s_f (the chain rule of Sec. 2.3). */
+OTM_API otm_status otm_op_filter_transpose(int dtype, int n, double rmin,
+                                           const void* s_f, void* s, void* stream);
+
+/* enforceMacroLoad (Sec. 2.4): f = three load cases from element
+ * conductivities k. */
+OTM_API otm_status otm_op_macro_load(int dtype, int n, const void* k, void* f, void* stream);
+
+/* Matrix-free [K u]_v of Sec. 2.4 for three fields u (3 n^3) with element
+ * conductivities k: Ku = K(k) u. */
+OTM_API otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u,
+                                  void* Ku, void* stream);
+
+/* One colour pass of the Gauss-Seidel relaxation of Sec. 2.4,
+ * S_v T_v = f_v - M_v, on the finest grid for the nodes of colour
+ * c = (x%2) + 2(y%2) + 4(z%2) in [0, 8) (n even).  Updates T in place. */
+OTM_API otm_status otm_op_gs_colour(int dtype, int n, const void* k, const void* f,
+                                    void* T, int colour, void* stream);
+
+/* Homogenized tensor and element sensitivities from a solution: for the
+ * element conductivities k and filtered density rho_f, the three solutions
+ * chi (3 n^3), kappa_out (host, 6 doubles) = discrete Eq. homo, and
+ * s_f (device, n^3, may be NULL) = sum_c w_c d kappa_c / d rho_f (Eq. sens)
+ * with weights w (host, 6 doubles). */
+OTM_API otm_status otm_op_kappa_sens(int dtype, int n, double penal, double k_solid,
+                                     double k_void, const void* k, const void* rho_f,
+                                     const void* chi, const double w[6],
+                                     double kappa_out[6], void* s_f, void* stream);
+
+/* OC update (Sec. 3.3) of rho with gradient s under volume bound vstar:
+ * writes rho_new, and *lambda_out (host, may be NULL). */
+OTM_API otm_status otm_op_oc_update(int dtype, int n, double vstar, double move,
+                                    double damp, double rho_min, const void* rho,
+                                    const void* s, void* rho_new, double* lambda_out,
+                                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OTM_H */

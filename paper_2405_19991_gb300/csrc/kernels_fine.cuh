@@ -1,0 +1,749 @@
+// Finest-grid kernels of the matrix-free periodic conduction operator.
+//
+// Element matrix.  For the unit trilinear hexahedron with unit conductivity,
+// K0 = K1(x)M1(x)M1 + M1(x)K1(x)M1 + M1(x)M1(x)K1 with the 1-D stiffness
+// K1 = [[1,-1],[-1,1]] and mass M1 = [[1/3,1/6],[1/6,1/3]], so
+// K0[l][m] = 1/3 (l = m), 0 (corners differing in one coordinate),
+// -1/12 (differing in two or three).  Hence, for a vertex v at local corner l
+// of element e, (K0 u_e)_l = (4 u_l - u_{l^3} - u_{l^5} - u_{l^6} - u_{l^7}) / 12
+// and the assembled [K u]_v of Sec. 2.4 is a 21-point stencil: v, its 12
+// edge-diagonal and 8 body-diagonal neighbours; face neighbours carry 0.
+//
+// Let k_abc be the conductivity of the element (x-a, y-b, z-c), a,b,c in
+// {0,1}; it lies in the octant s = (1-2a, 1-2b, 1-2c) of v and couples v to
+// v+(sx,sy,0), v+(sx,0,sz), v+(0,sy,sz), v+(sx,sy,sz).  Collecting terms:
+//   12 [K u]_v = 4 u_v sum_abc k_abc - nb(u),
+//   nb(u) = sum_abc k_abc u(v+s) + sum_ab (k_ab0 + k_ab1) u(v+(sx,sy,0))
+//         + sum_ac (k_a0c + k_a1c) u(v+(sx,0,sz)) + sum_bc (k_0bc + k_1bc) u(v+(0,sy,sz)).
+// The Gauss-Seidel update S_v T_v = f_v - M_v (Sec. 2.4) then has
+// S_v = sum k_abc / 3 and M_v = -nb(T) / 12, i.e. T_v = (12 f_v + nb(T)) / (4 sum k).
+//
+// Nodes whose (y, z) parities agree are never coupled (their x-neighbours are
+// face neighbours), so the paper's 8-colour order 0,1,...,7 with colour
+// (x%2) + 2(y%2) + 4(z%2) equals four passes over the (y%2, z%2) groups
+// {0,1}, {2,3}, {4,5}, {6,7}, bit for bit.
+#pragma once
+#include "otm_internal.cuh"
+
+namespace otm {
+
+struct Nbr {
+    // per-node neighbour geometry
+    int X[2], Y[2], Z[2];      // node offsets of x+s (a=0 -> +1, a=1 -> -1), times 1, n, n^2
+    int Xe[2], Ye[2], Ze[2];   // element offsets of x-a
+    int xc, yc, zc;            // x, y*n, z*n^2
+};
+
+__device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int n) {
+    Nbr g;
+    const int nn = n * n;
+    const int xm = wrapm(x, n), xp = wrapp(x, n);
+    const int ym = wrapm(y, n), yp = wrapp(y, n);
+    const int zm = wrapm(z, n), zp = wrapp(z, n);
+    g.X[0] = xp; g.X[1] = xm;
+    g.Y[0] = yp * n; g.Y[1] = ym * n;
+    g.Z[0] = zp * nn; g.Z[1] = zm * nn;
+    g.Xe[0] = x; g.Xe[1] = xm;
+    g.Ye[0] = y * n; g.Ye[1] = ym * n;
+    g.Ze[0] = z * nn; g.Ze[1] = zm * nn;
+    g.xc = x; g.yc = y * n; g.zc = z * nn;
+    return g;
+}
+
+template <class KT, class C>
+__device__ __forceinline__ void load_k8(const KT* __restrict__ k, const Nbr& g, C (&kk)[2][2][2]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                kk[c][b][a] = St<KT>::ld(k, (size_t)(g.Xe[a] + g.Ye[b] + g.Ze[c]));
+}
+
+template <class UT, class C>
+__device__ __forceinline__ C nb_sum(const UT* __restrict__ u, const Nbr& g, const C (&kk)[2][2][2]) {
+    C acc = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                acc += kk[c][b][a] * (C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.Z[c]));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            acc += (kk[0][b][a] + kk[1][b][a]) * (C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.zc));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            acc += (kk[c][0][a] + kk[c][1][a]) * (C)St<UT>::ld(u, (size_t)(g.X[a] + g.yc + g.Z[c]));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            acc += (kk[c][b][0] + kk[c][b][1]) * (C)St<UT>::ld(u, (size_t)(g.xc + g.Y[b] + g.Z[c]));
+    return acc;
+}
+
+// Difference form of the same sum: nd(u) = sum coef (u_w - u_v) = nb(u) - 4 sum(k) u_v,
+// so 12 [K u]_v = -nd(u).  Constant fields cancel exactly, which keeps the
+// rounding error of K u proportional to the local differences of u instead
+// of to |u|.
+template <class UT, class C>
+__device__ __forceinline__ C nd_sum(const UT* __restrict__ u, const Nbr& g, const C (&kk)[2][2][2], C uc) {
+    C acc = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+                acc += kk[c][b][a] * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.Z[c])) - uc);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            acc += (kk[0][b][a] + kk[1][b][a]) * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.zc)) - uc);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            acc += (kk[c][0][a] + kk[c][1][a]) * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.yc + g.Z[c])) - uc);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            acc += (kk[c][b][0] + kk[c][b][1]) * ((C)St<UT>::ld(u, (size_t)(g.xc + g.Y[b] + g.Z[c])) - uc);
+    return acc;
+}
+
+// nd of a field held as hi + lo (lo may be null): each difference is formed
+// from the pair and rounded once.
+template <class C>
+__device__ __forceinline__ C nd_sum2(const C* __restrict__ hi, const C* __restrict__ lo, const Nbr& g,
+                                     const C (&kk)[2][2][2], size_t v) {
+    const C hv = hi[v], lv = lo ? lo[v] : C(0);
+    auto D = [&](size_t w) -> C { return df_diff(hi[w], lo ? lo[w] : C(0), hv, lv); };
+    C acc = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) acc += kk[c][b][a] * D((size_t)(g.X[a] + g.Y[b] + g.Z[c]));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) acc += (kk[0][b][a] + kk[1][b][a]) * D((size_t)(g.X[a] + g.Y[b] + g.zc));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) acc += (kk[c][0][a] + kk[c][1][a]) * D((size_t)(g.X[a] + g.yc + g.Z[c]));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc += (kk[c][b][0] + kk[c][b][1]) * D((size_t)(g.xc + g.Y[b] + g.Z[c]));
+    return acc;
+}
+
+// Error-free version for the convergence check: every one of the 32 element
+// terms k_e (u_w - u_v) is formed with TwoProduct and summed with TwoSum,
+// so the result is nd(u) of the stored k and u up to O(eps^2).
+template <class C>
+__device__ __forceinline__ void nd_sum_exact(const C* __restrict__ hi, const C* __restrict__ lo, const Nbr& g,
+                                             const C (&kk)[2][2][2], size_t v, C& s_out, C& c_out) {
+    const C hv = hi[v], lv = lo ? lo[v] : C(0);
+    C s = 0, c = 0;
+    auto term = [&](C kv, C d) {
+        const C p = kv * d;
+        const C pe = fma(kv, d, -p);
+        C t, e;
+        two_sum(s, p, t, e);
+        s = t;
+        c += e + pe;
+    };
+    auto D = [&](size_t w) -> C { return df_diff(hi[w], lo ? lo[w] : C(0), hv, lv); };
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) term(kk[cz][b][a], D((size_t)(g.X[a] + g.Y[b] + g.Z[cz])));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const C d = D((size_t)(g.X[a] + g.Y[b] + g.zc));
+            term(kk[0][b][a], d);
+            term(kk[1][b][a], d);
+        }
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const C d = D((size_t)(g.X[a] + g.yc + g.Z[cz]));
+            term(kk[cz][0][a], d);
+            term(kk[cz][1][a], d);
+        }
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const C d = D((size_t)(g.xc + g.Y[b] + g.Z[cz]));
+            term(kk[cz][b][0], d);
+            term(kk[cz][b][1], d);
+        }
+    s_out = s;
+    c_out = c;
+}
+
+template <class C>
+__device__ __forceinline__ C ksum8(const C (&kk)[2][2][2]) {
+    C s = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) s += kk[c][b][a];
+    return s;
+}
+
+// ----------------------------------------------------------------- finalisers
+struct FinNone {
+    __device__ void operator()(const double*) const {}
+};
+
+// alpha_i = gamma_i / (p_i . K p_i) for active load cases.
+struct FinAlpha {
+    PcgScalars* ps;
+    __device__ void operator()(const double* s) const {
+        for (int i = 0; i < 3; ++i) {
+            ps->pq[i] = s[i];
+            double a = 0.0;
+            if (ps->active[i]) {
+                if (s[i] > 0.0 && isfinite(s[i]) && isfinite(ps->gamma[i])) {
+                    a = ps->gamma[i] / s[i];
+                } else {
+                    ps->breakdown |= (1 << i);
+                    ps->active[i] = 0;
+                }
+            }
+            ps->alpha[i] = a;
+        }
+    }
+};
+
+// Initial residual: record ||f||^2 and ||r||^2, set the active flags (from
+// this residual, or with use_true from the last error-free check).
+struct FinInit {
+    PcgScalars* ps;
+    int use_true;
+    __device__ void operator()(const double* s) const {
+        int na = 0;
+        for (int i = 0; i < 3; ++i) {
+            ps->rr[i] = s[i];
+            ps->ff[i] = s[3 + i];
+            ps->iters[i] = 0;
+            ps->alpha[i] = ps->beta[i] = 0.0;
+            const bool act = use_true ? (ps->true_ff[i] > 0.0 && ps->true_rr[i] > ps->tol2 * ps->true_ff[i])
+                                      : (s[3 + i] > 0.0 && s[i] > ps->tol2 * s[3 + i]);
+            ps->active[i] = act ? 1 : 0;
+            na += act;
+        }
+        ps->breakdown = 0;
+        ps->nactive = na;
+    }
+};
+
+// After x += alpha p, r -= alpha q: convergence test on the recurrence residual.
+struct FinResid {
+    PcgScalars* ps;
+    __device__ void operator()(const double* s) const {
+        int na = 0;
+        for (int i = 0; i < 3; ++i) {
+            ps->rz_old[i] = s[3 + i];
+            if (ps->active[i]) {
+                ps->rr[i] = s[i];
+                ps->iters[i] += 1;
+                if (!(s[i] > ps->tol2 * ps->ff[i])) ps->active[i] = 0;
+                if (!isfinite(s[i])) {
+                    ps->active[i] = 0;
+                    ps->breakdown |= (1 << i);
+                }
+            }
+            na += ps->active[i];
+        }
+        ps->nactive = na;
+    }
+};
+
+// gamma_new = r . z; beta = (gamma_new - [flexible] r.z_old) / gamma_old.
+struct FinBeta {
+    PcgScalars* ps;
+    int first;
+    __device__ void operator()(const double* s) const {
+        for (int i = 0; i < 3; ++i) {
+            double b = 0.0;
+            if (!first && ps->active[i] && ps->gamma[i] != 0.0) {
+                const double num = ps->flexible ? s[i] - ps->rz_old[i] : s[i];
+                b = num / ps->gamma[i];
+                if (!isfinite(b)) b = 0.0;
+            }
+            ps->beta[i] = b;
+            if (first || ps->active[i]) ps->gamma[i] = s[i];
+        }
+    }
+};
+
+// ------------------------------------------------------------------ kernels
+
+// out_i = K(k) u_i  (MODE 0) or out_i = f_i - K(k) u_i (MODE 1), i = 0..2,
+// evaluated in the difference form.  With DOT, MODE 0 reduces u_i . out_i;
+// MODE 1 reduces out_i . out_i and f_i . f_i.  MODE 2 is MODE 1 without the
+// store (residual norms only), evaluated in the compute type CT.
+template <int MODE, bool DOT, class KT, class UT, class FT, class OT, class Fin,
+          class CT = typename St<OT>::C>
+__global__ void __launch_bounds__(256)
+k_stencil_apply(int n, const KT* __restrict__ k, const UT* __restrict__ u, const FT* __restrict__ f,
+                OT* __restrict__ out, RedBuf rb, Fin fin) {
+    using C = CT;
+    const size_t N = (size_t)n * n * n;
+    Acc<C> acc[6];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n);
+        const int y = (int)((v / n) % n);
+        const int z = (int)(v / ((size_t)n * n));
+        const Nbr g = make_nbr(x, y, z, n);
+        C kk[2][2][2];
+        load_k8<KT, C>(k, g, kk);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const UT* ui = u + (size_t)i * N;
+            const C uc = (C)St<UT>::ld(ui, v);
+            const C Ku = nd_sum<UT, C>(ui, g, kk, uc) * C(-1.0 / 12.0);
+            C o;
+            if (MODE == 0) {
+                o = Ku;
+            } else {
+                const C fv = (C)St<FT>::ld(f + (size_t)i * N, v);
+                o = fv - Ku;
+                if (DOT) acc[3 + i].add_prod(fv, fv);
+            }
+            if (MODE != 2) St<OT>::st(out + (size_t)i * N, v, (typename St<OT>::C)o);
+            if (DOT) {
+                if (MODE == 0) acc[i].add_prod(uc, o);
+                else acc[i].add_prod(o, o);
+            }
+        }
+    }
+    if (DOT) {
+        __shared__ double res[6];
+        double vals[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+        if (grid_reduce<6>(vals, rb, res)) {
+            if (threadIdx.x == 0) fin(res);
+        }
+    }
+}
+
+// r_i = f_i - K x_i with x held as hi + lo (lo may be null); reduces
+// ||r_i||^2 and ||f_i||^2 and sets the active flags (FinInit).
+template <class R, class Fin>
+__global__ void __launch_bounds__(256)
+k_residual_x2(int n, const R* __restrict__ k, const R* __restrict__ xh, const R* __restrict__ xl,
+              const R* __restrict__ f, R* __restrict__ r, RedBuf rb, Fin fin) {
+    using C = typename St<R>::C;
+    const size_t N = (size_t)n * n * n;
+    Acc<C> acc[6];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+        const Nbr g = make_nbr(x, y, z, n);
+        C kk[2][2][2];
+        load_k8<R, C>(k, g, kk);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t o = (size_t)i * N;
+            const C fv = f[o + v];
+            const C rv = fv + nd_sum2<C>(xh + o, xl ? xl + o : nullptr, g, kk, v) * C(1.0 / 12.0);
+            r[o + v] = rv;
+            acc[i].add_prod(rv, rv);
+            acc[3 + i].add_prod(fv, fv);
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (threadIdx.x == 0) fin(res);
+    }
+}
+
+// Convergence check (k_true_residual below): ||f_i - K x_i||^2 of the
+// stored iterate with error-free element terms (no FP64 arithmetic).
+
+// True residual norms at solver exit.
+struct FinTrue {
+    PcgScalars* ps;
+    __device__ void operator()(const double* s) const {
+        for (int i = 0; i < 3; ++i) {
+            ps->true_rr[i] = s[i];
+            ps->true_ff[i] = s[3 + i];
+        }
+    }
+};
+
+template <class R>
+__global__ void __launch_bounds__(256)
+k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const R* __restrict__ xl,
+                const R* __restrict__ f, RedBuf rb, FinTrue fin) {
+    using C = typename St<R>::C;
+    const size_t N = (size_t)n * n * n;
+    Acc<C> acc[6];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+        const Nbr g = make_nbr(x, y, z, n);
+        C kk[2][2][2];
+        load_k8<R, C>(k, g, kk);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t o = (size_t)i * N;
+            C s, c;
+            nd_sum_exact<C>(xh + o, xl ? xl + o : nullptr, g, kk, v, s, c);
+            // r = f + nd / 12, nd = s + c; one rounding of the final sum
+            const C fv = f[o + v];
+            C t, e;
+            two_sum(fv, s * C(1.0 / 12.0), t, e);
+            const C rv = t + (e + c * C(1.0 / 12.0) + fma(s, C(1.0 / 12.0), -(s * C(1.0 / 12.0))));
+            acc[i].add_prod(rv, rv);
+            acc[3 + i].add_prod(fv, fv);
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (threadIdx.x == 0) fin(res);
+    }
+}
+
+// One Gauss-Seidel pass over the nodes with y%2 == group&1, z%2 == group>>1
+// and, when xpar >= 0, x%2 == xpar.  ZERO: the relaxed field starts at zero;
+// the pass also zeroes the other nodes of each 2x2 (y, z) cell, so no
+// separate clear is needed (only valid for group 0, xpar < 0).
+template <bool ZERO, class KT, class FT, class TT>
+__global__ void __launch_bounds__(256)
+k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __restrict__ f,
+          TT* __restrict__ T) {
+    using C = typename St<TT>::C;
+    const size_t N = (size_t)n * n * n;
+    const int h = n >> 1;
+    const int nx = xpar < 0 ? n : h;
+    const size_t M = (size_t)nx * h * h;
+    const int yo = group & 1, zo = group >> 1;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < M;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int xi = (int)(t % nx);
+        const int yy = (int)((t / nx) % h);
+        const int zz = (int)(t / ((size_t)nx * h));
+        const int x = xpar < 0 ? xi : 2 * xi + xpar;
+        const int y = 2 * yy + yo, z = 2 * zz + zo;
+        const Nbr g = make_nbr(x, y, z, n);
+        C kk[2][2][2];
+        load_k8<KT, C>(k, g, kk);
+        const C inv4k = C(1) / (C(4) * ksum8(kk));
+        const size_t v = (size_t)(g.xc + g.yc + g.zc);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            TT* Ti = T + (size_t)i * N;
+            const C fv = St<FT>::ld(f + (size_t)i * N, v);
+            C nb = 0;
+            if (!ZERO) nb = nb_sum<TT, C>(Ti, g, kk);
+            St<TT>::st(Ti, v, (C(12) * fv + nb) * inv4k);
+            if (ZERO) {
+                const size_t y1 = (size_t)(y + 1) * n, z1 = (size_t)(z + 1) * n * n;
+                St<TT>::st(Ti, x + y1 + g.zc, C(0));
+                St<TT>::st(Ti, x + g.yc + z1, C(0));
+                St<TT>::st(Ti, x + y1 + z1, C(0));
+            }
+        }
+    }
+}
+
+// enforceMacroLoad (Sec. 2.4).  The template f0 = K0 T0 with T0[l][i] = i-th
+// coordinate of corner l is +1/4 on the upper face of axis i and -1/4 on the
+// lower face (from the K0 row formula above), so
+// f^(i)_v = (sum of k over the four elements below v along axis i
+//           - sum over the four above) / 4.
+template <class KT, class OT>
+__global__ void __launch_bounds__(256)
+k_macro_load(int n, const KT* __restrict__ k, OT* __restrict__ f) {
+    using C = typename St<OT>::C;
+    const size_t N = (size_t)n * n * n;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n);
+        const int y = (int)((v / n) % n);
+        const int z = (int)(v / ((size_t)n * n));
+        const Nbr g = make_nbr(x, y, z, n);
+        C kk[2][2][2];
+        load_k8<KT, C>(k, g, kk);
+        C fx = 0, fy = 0, fz = 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const C kv = kk[c][b][a];
+                    fx += a ? kv : -kv;
+                    fy += b ? kv : -kv;
+                    fz += c ? kv : -kv;
+                }
+        St<OT>::st(f, v, C(0.25) * fx);
+        St<OT>::st(f + N, v, C(0.25) * fy);
+        St<OT>::st(f + 2 * N, v, C(0.25) * fz);
+    }
+}
+
+// The periodic operator annihilates constants, so K x = f is solvable only
+// for zero-mean f; FP32 rounding of the macro loads leaves a small mean that
+// would floor the residual.  Sum, then subtract the mean.
+struct FinMean {
+    PcgScalars* ps;
+    double invN;
+    __device__ void operator()(const double* s) const {
+        for (int i = 0; i < 3; ++i) ps->fmean[i] = s[i] * invN;
+    }
+};
+
+template <class R>
+__global__ void __launch_bounds__(256)
+k_sum3(size_t N, const R* __restrict__ f, RedBuf rb, FinMean fin) {
+    using C = typename St<R>::C;
+    Acc<C> acc[3];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i].add(f[(size_t)i * N + v]);
+    }
+    __shared__ double res[3];
+    double vals[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<3>(vals, rb, res)) {
+        if (threadIdx.x == 0) fin(res);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(256)
+k_sub_mean(size_t N, R* __restrict__ f, const PcgScalars* __restrict__ ps) {
+    using C = typename St<R>::C;
+    const C m0 = (C)ps->fmean[0], m1 = (C)ps->fmean[1], m2 = (C)ps->fmean[2];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        f[v] -= m0;
+        f[N + v] -= m1;
+        f[2 * N + v] -= m2;
+    }
+}
+
+// Restriction R = P^T of the trilinear prolongation: coarse node I gathers
+// the fine nodes 2I + d, d in {-1,0,1}^3, with weight prod (1 - |d|/2).
+template <class IT, class OT>
+__global__ void __launch_bounds__(256)
+k_restrict(int nc, const IT* __restrict__ rf, OT* __restrict__ fc) {
+    using C = typename St<OT>::C;
+    const int nf = 2 * nc;
+    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    for (size_t I = (size_t)blockIdx.x * blockDim.x + threadIdx.x; I < Nc;
+         I += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(I % nc), Y = (int)((I / nc) % nc), Z = (int)(I / ((size_t)nc * nc));
+        int xs[3], ys[3], zs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xs[d] = wrapd(2 * X, d - 1, nf);
+            ys[d] = wrapd(2 * Y, d - 1, nf) * nf;
+            zs[d] = wrapd(2 * Z, d - 1, nf) * nf * nf;
+        }
+        const C w1[3] = {C(0.5), C(1), C(0.5)};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const IT* r = rf + (size_t)i * Nf;
+            C acc = 0;
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz) {
+                C az = 0;
+#pragma unroll
+                for (int dy = 0; dy < 3; ++dy) {
+                    C ay = 0;
+#pragma unroll
+                    for (int dx = 0; dx < 3; ++dx)
+                        ay += w1[dx] * St<IT>::ld(r, (size_t)(xs[dx] + ys[dy] + zs[dz]));
+                    az += w1[dy] * ay;
+                }
+                acc += w1[dz] * az;
+            }
+            St<OT>::st(fc + (size_t)i * Nc, I, acc);
+        }
+    }
+}
+
+// Prolongation and correction: T_v += sum_I P[v, I] Tc_I (trilinear).
+template <class CT, class TT>
+__global__ void __launch_bounds__(256)
+k_prolong_add(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
+    using C = typename St<TT>::C;
+    const int nc = nf / 2;
+    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < Nf;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
+        int xi[2], yi[2], zi[2];
+        C wx[2], wy[2], wz[2];
+        int cx, cy, cz;
+        if (x & 1) { xi[0] = x >> 1; xi[1] = wrapp(x >> 1, nc); wx[0] = wx[1] = C(0.5); cx = 2; }
+        else { xi[0] = xi[1] = x >> 1; wx[0] = C(1); wx[1] = 0; cx = 1; }
+        if (y & 1) { yi[0] = y >> 1; yi[1] = wrapp(y >> 1, nc); wy[0] = wy[1] = C(0.5); cy = 2; }
+        else { yi[0] = yi[1] = y >> 1; wy[0] = C(1); wy[1] = 0; cy = 1; }
+        if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = C(0.5); cz = 2; }
+        else { zi[0] = zi[1] = z >> 1; wz[0] = C(1); wz[1] = 0; cz = 1; }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const CT* tc = Tc + (size_t)i * Nc;
+            C acc = 0;
+            for (int c = 0; c < cz; ++c)
+                for (int b = 0; b < cy; ++b)
+                    for (int a = 0; a < cx; ++a)
+                        acc += wz[c] * wy[b] * wx[a] *
+                               St<CT>::ld(tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]));
+            TT* t = T + (size_t)i * Nf;
+            St<TT>::st(t, v, St<TT>::ld(t, v) + acc);
+        }
+    }
+}
+
+// x_i += alpha_i p_i (x held as hi + lo when xl is not null: the update is
+// added with TwoSum/TwoProduct and renormalised); r_i -= alpha_i q_i;
+// reduce r_i.r_i and (flexible) r_i.z_i.
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, const R* __restrict__ p,
+            const R* __restrict__ q, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps,
+            RedBuf rb, FinResid fin) {
+    using C = typename St<R>::C;
+    const C a0 = (C)ps->alpha[0], a1 = (C)ps->alpha[1], a2 = (C)ps->alpha[2];
+    const bool flex = ps->flexible != 0;
+    Acc<C> acc[6];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const C a = i == 0 ? a0 : (i == 1 ? a1 : a2);
+            if (a == C(0)) continue;
+            const size_t o = (size_t)i * N + v;
+            const C pv = p[o];
+            if (xl) {
+                const C ap = a * pv;
+                const C ep = fma(a, pv, -ap);
+                C sh, se;
+                two_sum((C)x[o], ap, sh, se);
+                const C lo = xl[o] + (se + ep);
+                const C hi = sh + lo;
+                xl[o] = lo - (hi - sh);
+                x[o] = hi;
+            } else {
+                x[o] = x[o] + a * pv;
+            }
+            const C rn = r[o] - a * q[o];
+            r[o] = rn;
+            acc[i].add_prod(rn, rn);
+            if (flex) acc[3 + i].add_prod(rn, (C)St<ZT>::ld(z, o));
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (threadIdx.x == 0) fin(res);
+    }
+}
+
+// x = hi + lo rounded to the output type (corrector fields for readers).
+template <class R, class Y>
+__global__ void __launch_bounds__(256)
+k_join(size_t count, const R* __restrict__ hi, const R* __restrict__ lo, Y* __restrict__ out) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x)
+        St<Y>::st(out, i, (typename St<Y>::C)((double)hi[i] + (lo ? (double)lo[i] : 0.0)));
+}
+
+// gamma = r . z (three load cases), then beta via the finaliser.
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_dot_rz(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb, FinBeta fin) {
+    using C = typename St<R>::C;
+    Acc<C> acc[3];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t o = (size_t)i * N + v;
+            acc[i].add_prod(r[o], (C)St<ZT>::ld(z, o));
+        }
+    }
+    __shared__ double res[3];
+    double vals[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<3>(vals, rb, res)) {
+        if (threadIdx.x == 0) fin(res);
+    }
+}
+
+// b = a (type conversion), optionally clamped to [0, 1].
+template <class X, class Y>
+__global__ void __launch_bounds__(256)
+k_convert(size_t count, const X* __restrict__ a, Y* __restrict__ b, int clamp01) {
+    using C = typename St<Y>::C;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (size_t)gridDim.x * blockDim.x) {
+        C v = (C)St<X>::ld(a, i);
+        if (clamp01) v = v < C(0) ? C(0) : (v > C(1) ? C(1) : v);
+        St<Y>::st(b, i, v);
+    }
+}
+
+// p_i = z_i + beta_i p_i.
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_update_p(size_t N, R* __restrict__ p, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps, int first) {
+    using C = typename St<R>::C;
+    const C b0 = (C)ps->beta[0], b1 = (C)ps->beta[1], b2 = (C)ps->beta[2];
+    const int a0 = ps->active[0], a1 = ps->active[1], a2 = ps->active[2];
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int act = i == 0 ? a0 : (i == 1 ? a1 : a2);
+            if (!act) continue;
+            const C b = i == 0 ? b0 : (i == 1 ? b1 : b2);
+            const size_t o = (size_t)i * N + v;
+            p[o] = first ? (C)St<ZT>::ld(z, o) : (C)St<ZT>::ld(z, o) + b * p[o];
+        }
+    }
+}
+
+}  // namespace otm

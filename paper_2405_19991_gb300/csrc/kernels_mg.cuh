@@ -1,0 +1,311 @@
+// Coarse levels of the V-cycle (Alg. 3).
+//
+// Coarse operators are Galerkin products A_{l+1} = R A_l P with trilinear P
+// and R = P^T.  They are built element by element: a fine element e lies in
+// the coarse element E at sub-position s in {0,1}^3, and its eight corners
+// are interpolated from E's corners by an 8x8 matrix P_s, so
+//   K_E^{l+1} = sum_s P_s^T K_{child(E,s)}^l P_s,   K_e^0 = k_e K0,
+// which on the first level is sum_s k_{child(E,s)} B_s with constant
+// B_s = P_s^T K0 P_s.  Each level's 27-point node stencil (stored as
+// A[o][v], o = (dx+1) + 3(dy+1) + 9(dz+1)) gathers the element matrices of
+// the eight elements around v.  P_s[j][m] = prod_d phi(s_d + j_d, m_d) with
+// phi(t, 0) = {1, 1/2, 0}[t], phi(t, 1) = {0, 1/2, 1}[t].
+#pragma once
+#include "otm_internal.cuh"
+
+namespace otm {
+
+// ---- first coarse level: element matrices from the fine conductivities ----
+template <class KT, class C>
+__global__ void __launch_bounds__(128)
+k_elem_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, C* __restrict__ Kel) {
+    const int nf = 2 * nc;
+    const size_t Nc = (size_t)nc * nc * nc;
+    for (size_t E = (size_t)blockIdx.x * blockDim.x + threadIdx.x; E < Nc;
+         E += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(E % nc), Y = (int)((E / nc) % nc), Z = (int)(E / ((size_t)nc * nc));
+        C ks[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int fx = 2 * X + (s & 1), fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
+            ks[s] = St<KT>::ld(k, (size_t)fx + (size_t)nf * (fy + (size_t)nf * fz));
+        }
+        for (int mm = 0; mm < 64; ++mm) {
+            C a = 0;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) a += ks[s] * Bs[s * 64 + mm];
+            Kel[(size_t)mm * Nc + E] = a;
+        }
+    }
+}
+
+// ---- deeper levels: K_E = sum_s P_s^T K_child P_s ----
+template <class C>
+__global__ void __launch_bounds__(64)
+k_elem_coarsen(int nc, const C* __restrict__ Kf, const C* __restrict__ Ps, C* __restrict__ Kc) {
+    const int nf = 2 * nc;
+    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    for (size_t E = (size_t)blockIdx.x * blockDim.x + threadIdx.x; E < Nc;
+         E += (size_t)gridDim.x * blockDim.x) {
+        const int X = (int)(E % nc), Y = (int)((E / nc) % nc), Z = (int)(E / ((size_t)nc * nc));
+        C out[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) out[i] = 0;
+        for (int s = 0; s < 8; ++s) {
+            const int fx = 2 * X + (s & 1), fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
+            const size_t e = (size_t)fx + (size_t)nf * (fy + (size_t)nf * fz);
+            const C* P = Ps + s * 64;   // P[j*8 + m]
+            // T = K_child P  (8x8), then out += P^T T
+            for (int j = 0; j < 8; ++j) {
+                C kr[8];
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) kr[jj] = Kf[(size_t)(j * 8 + jj) * Nf + e];
+                C t[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    C a = 0;
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) a += kr[jj] * P[jj * 8 + m];
+                    t[m] = a;
+                }
+                // row j of T contributes P[j][m'] * T[j][m] to out[m'][m]
+#pragma unroll
+                for (int mp = 0; mp < 8; ++mp) {
+                    const C pj = P[j * 8 + mp];
+                    if (pj != C(0)) {
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) out[mp * 8 + m] += pj * t[m];
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 64; ++i) Kc[(size_t)i * Nc + E] = out[i];
+    }
+}
+
+// ---- node stencils from element matrices ----
+template <class C, class AT>
+__global__ void __launch_bounds__(128)
+k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
+    const size_t N = (size_t)n * n * n;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+        C acc[27];
+#pragma unroll
+        for (int o = 0; o < 27; ++o) acc[o] = 0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int a = m & 1, b = (m >> 1) & 1, c = m >> 2;
+            const size_t E = (size_t)wrapd(x, -a, n) + (size_t)n * (wrapd(y, -b, n) + (size_t)n * wrapd(z, -c, n));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int dx = (j & 1) - a, dy = ((j >> 1) & 1) - b, dz = (j >> 2) - c;
+                acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += Kel[(size_t)(m * 8 + j) * N + E];
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
+    }
+}
+
+// Node stencil of the finest operator itself (used when the hierarchy has a
+// single level and the fine grid is solved directly).
+template <class KT, class C, class AT>
+__global__ void __launch_bounds__(128)
+k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
+    const size_t N = (size_t)n * n * n;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+        C acc[27];
+#pragma unroll
+        for (int o = 0; o < 27; ++o) acc[o] = 0;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+            const int a = m & 1, b = (m >> 1) & 1, c = m >> 2;
+            const size_t E = (size_t)wrapd(x, -a, n) + (size_t)n * (wrapd(y, -b, n) + (size_t)n * wrapd(z, -c, n));
+            const C ke = St<KT>::ld(k, E);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int pc = __popc(j ^ m);
+                const C k0 = pc == 0 ? C(1.0 / 3.0) : (pc == 1 ? C(0) : C(-1.0 / 12.0));
+                const int dx = (j & 1) - a, dy = ((j >> 1) & 1) - b, dz = (j >> 2) - c;
+                acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += ke * k0;
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
+    }
+}
+
+// ---- Gauss-Seidel colour pass on a 27-point stencil level ----
+// colour = (x%2) + 2(y%2) + 4(z%2); n even.  ZERO (colour 0 only): the field
+// starts at zero and the pass zeroes the other seven nodes of each 2x2x2 cell.
+template <bool ZERO, class AT, class FT, class TT>
+__global__ void __launch_bounds__(256)
+k_gs_stencil(int n, int colour, const AT* __restrict__ A, const FT* __restrict__ f, TT* __restrict__ T) {
+    using C = typename St<TT>::C;
+    const size_t N = (size_t)n * n * n;
+    const int h = n >> 1;
+    const size_t M = (size_t)h * h * h;
+    const int xo = colour & 1, yo = (colour >> 1) & 1, zo = colour >> 2;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < M;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int x = 2 * (int)(t % h) + xo;
+        const int y = 2 * (int)((t / h) % h) + yo;
+        const int z = 2 * (int)(t / ((size_t)h * h)) + zo;
+        const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+        int xs[3], ys[3], zs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xs[d] = wrapd(x, d - 1, n);
+            ys[d] = wrapd(y, d - 1, n) * n;
+            zs[d] = wrapd(z, d - 1, n) * n * n;
+        }
+        C a[27];
+#pragma unroll
+        for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+        const C inv = C(1) / a[13];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            TT* Ti = T + (size_t)i * N;
+            C s = St<FT>::ld(f + (size_t)i * N, v);
+            if (!ZERO) {
+#pragma unroll
+                for (int o = 0; o < 27; ++o) {
+                    if (o == 13) continue;
+                    s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
+                }
+            }
+            St<TT>::st(Ti, v, s * inv);
+            if (ZERO) {
+#pragma unroll
+                for (int q = 1; q < 8; ++q) {
+                    const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
+                    St<TT>::st(Ti, w, C(0));
+                }
+            }
+        }
+    }
+}
+
+// res = f - A T on a stencil level.
+template <class AT, class FT, class TT, class OT>
+__global__ void __launch_bounds__(256)
+k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, const TT* __restrict__ T,
+                   OT* __restrict__ res) {
+    using C = typename St<OT>::C;
+    const size_t N = (size_t)n * n * n;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
+         v += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+        int xs[3], ys[3], zs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xs[d] = wrapd(x, d - 1, n);
+            ys[d] = wrapd(y, d - 1, n) * n;
+            zs[d] = wrapd(z, d - 1, n) * n * n;
+        }
+        C a[27];
+#pragma unroll
+        for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const TT* Ti = T + (size_t)i * N;
+            C s = St<FT>::ld(f + (size_t)i * N, v);
+#pragma unroll
+            for (int o = 0; o < 27; ++o)
+                s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
+            St<OT>::st(res + (size_t)i * N, v, s);
+        }
+    }
+}
+
+// ---- coarsest level: dense inverse of the node-0-pinned operator ----
+// One CTA.  W (FP64 workspace, (m-1)^2) receives the dense matrix of the
+// stencil without node 0's row and column, is inverted in place by
+// Gauss-Jordan elimination (no pivoting: the pinned matrix is SPD), and the
+// inverse is stored to Minv in the compute type.
+template <class AT, class C>
+__global__ void __launch_bounds__(1024)
+k_coarse_invert(int n, const AT* __restrict__ A, double* __restrict__ W, C* __restrict__ Minv) {
+    const int m = n * n * n;
+    const int q = m - 1;
+    __shared__ double col[343];
+    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) W[i] = 0.0;
+    __syncthreads();
+    for (int v = 1 + threadIdx.x; v < m; v += blockDim.x) {
+        const int x = v % n, y = (v / n) % n, z = v / (n * n);
+        for (int o = 0; o < 27; ++o) {
+            const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
+            if (c == 0) continue;
+            W[(size_t)(v - 1) * q + (c - 1)] += (double)St<AT>::ld(A, (size_t)o * m + v);
+        }
+    }
+    __syncthreads();
+    for (int kp = 0; kp < q; ++kp) {
+        const double piv = W[(size_t)kp * q + kp];
+        const double ip = 1.0 / piv;
+        __syncthreads();
+        for (int j = threadIdx.x; j < q; j += blockDim.x) {
+            if (j == kp) W[(size_t)kp * q + j] = ip;
+            else W[(size_t)kp * q + j] *= ip;
+        }
+        for (int i = threadIdx.x; i < q; i += blockDim.x) col[i] = W[(size_t)i * q + kp];
+        __syncthreads();
+        for (size_t t = threadIdx.x; t < (size_t)q * q; t += blockDim.x) {
+            const int i = (int)(t / q), j = (int)(t % q);
+            if (i == kp) continue;
+            if (j == kp) W[t] = -col[i] * ip;
+            else W[t] -= col[i] * W[(size_t)kp * q + j];
+        }
+        __syncthreads();
+    }
+    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) Minv[i] = (C)W[i];
+}
+
+// T = Minv f with T_0 = 0, then shifted to zero mean.  One CTA.
+template <class C, class FT, class TT>
+__global__ void __launch_bounds__(1024)
+k_coarse_solve(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* __restrict__ T) {
+    const int m = n * n * n;
+    const int q = m - 1;
+    __shared__ C fs[3][343];
+    __shared__ C ts[3][343];
+    __shared__ double red[3][32];
+    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) fs[i / m][i % m] = St<FT>::ld(f, i);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * m; t += blockDim.x) {
+        const int r = t / m, v = t % m;
+        C a = 0;
+        if (v > 0) {
+            const C* row = Minv + (size_t)(v - 1) * q;
+            for (int j = 0; j < q; ++j) a += row[j] * fs[r][j + 1];
+        }
+        ts[r][v] = a;
+    }
+    __syncthreads();
+    // mean of each load case
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < 3; ++r) {
+        double s = 0.0;
+        for (int v = threadIdx.x; v < m; v += blockDim.x) s += (double)ts[r][v];
+        s = warp_sum(s);
+        if (lane == 0) red[r][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        red[threadIdx.x][0] = s / m;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * m; t += blockDim.x) {
+        const int r = t / m, v = t % m;
+        St<TT>::st(T, (size_t)t, ts[r][v] - (C)red[r][0]);
+    }
+}
+
+}  // namespace otm

@@ -1,0 +1,252 @@
+// Internal device helpers of libotm: storage/compute types, periodic
+// indexing, compensated FP32 accumulation and deterministic grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "otm.h"
+
+namespace otm {
+
+// ---------------------------------------------------------------------------
+// Storage type S -> compute type C.  Fields may be stored in FP64, FP32 or
+// BF16; BF16 fields are computed on in FP32.
+// ---------------------------------------------------------------------------
+template <class S> struct St;
+template <> struct St<double> {
+    using C = double;
+    static __device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(double* p, size_t i, double v) { p[i] = v; }
+};
+template <> struct St<float> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void st(float* p, size_t i, float v) { p[i] = v; }
+};
+template <> struct St<__nv_bfloat16> {
+    using C = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, size_t i) {
+        return __bfloat162float(p[i]);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, float v) {
+        p[i] = __float2bfloat16_rn(v);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Accumulators for inner products and volume/tensor sums.  FP32 products are
+// summed with an error-free transformation (TwoSum of the running sum and
+// TwoProduct of each product, Ogita-Rump-Oishi "Accurate sum and dot
+// product", 2005), so a thread's partial is good to about FP64 before it is
+// converted for the FP64 block and grid stages.
+// ---------------------------------------------------------------------------
+template <class C> struct Acc;
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        float bp = t - s;
+        c += (s - (t - bp)) + (x - bp);
+        s = t;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p = a * b;
+        float pe = fmaf(a, b, -p);
+        float t = s + p;
+        float bp = t - s;
+        c += ((s - (t - bp)) + (p - bp)) + pe;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Error-free transformations (Knuth TwoSum, FMA TwoProduct).
+template <class C>
+__device__ __forceinline__ void two_sum(C a, C b, C& s, C& e) {
+    s = a + b;
+    const C bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// A value kept as an unevaluated sum hi + lo (double-float when C = float).
+template <class C>
+__device__ __forceinline__ C df_diff(C hw, C lw, C hv, C lv) {   // (hw + lw) - (hv + lv), rounded once
+    C s, e;
+    two_sum(hw, -hv, s, e);
+    return s + ((lw - lv) + e);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic grid reduction.  Every block reduces its threads' values in a
+// fixed shuffle tree, writes one partial per value, and the last block to
+// arrive (counted with an atomic ticket) sums the partials in a fixed order
+// and runs the caller's finaliser.  Same grid -> bitwise-identical result.
+// ---------------------------------------------------------------------------
+struct RedBuf {
+    double* partials;        // [max_blocks * kRedMaxVals]
+    unsigned int* counter;   // one ticket counter, zero between launches
+    int max_blocks;
+};
+constexpr int kRedMaxVals = 72;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-reduce NV values; thread 0 of the LAST block returns true with the
+// grid-wide sums in `out` (shared memory, NV doubles, valid for all threads
+// of that block after the call).  All threads of every block must call it.
+template <int NV>
+__device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out) {
+    __shared__ double sm[32][NV];
+    __shared__ bool is_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double w = warp_sum(v[i]);
+        if (lane == 0) sm[warp][i] = w;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double w = lane < nwarp ? sm[lane][i] : 0.0;
+            w = warp_sum(w);
+            if (lane == 0) rb.partials[(size_t)blockIdx.x * NV + i] = w;
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(rb.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    // fixed-order sum of the partials: strided per thread, then a fixed tree
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            a += __ldcg(rb.partials + (size_t)b * NV + i);
+        a = warp_sum(a);
+        __syncthreads();
+        if (lane == 0) sm[warp][i] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < nwarp; ++w) t += sm[w][i];
+            out[i] = t;
+        }
+    }
+    if (threadIdx.x == 0) *rb.counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Periodic grid indexing: node / element (x, y, z) at x + n (y + n z).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapm(int a, int n) { return a == 0 ? n - 1 : a - 1; }
+__device__ __forceinline__ int wrapp(int a, int n) { return a == n - 1 ? 0 : a + 1; }
+__device__ __forceinline__ int wrapd(int a, int d, int n) {
+    a += d;
+    return a < 0 ? a + n : (a >= n ? a - n : a);
+}
+
+// ---------------------------------------------------------------------------
+// Scalars shared between kernels of a solve (device resident).
+// ---------------------------------------------------------------------------
+struct PcgScalars {
+    double ff[3];        // ||f_i||^2
+    double rr[3];        // ||r_i||^2 (recurrence)
+    double gamma[3];     // r_i . z_i
+    double pq[3];        // p_i . K p_i
+    double alpha[3];
+    double beta[3];
+    double rz_old[3];    // r_{k+1} . z_k (flexible beta)
+    double true_rr[3];   // ||f - K x||^2 at the last residual replacement
+    double true_ff[3];
+    double fmean[3];     // mean of each macro load before projection
+    double tol2;         // cg_tol^2
+    int active[3];       // 1 while load case i iterates
+    int iters[3];
+    int nactive;
+    int breakdown;       // bit i set: load case i broke down (pq <= 0 or non-finite)
+    int flexible;        // 1: Polak-Ribiere beta
+    int pad;
+};
+
+struct GovState {
+    double df, vstar, g_prev, gap;
+    int count, pad;
+};
+
+struct GovParams {
+    double bound, small_rel, vol_tol;
+};
+
+// Alg. 1, one pass of its loop body, with the thresholds of GovParams.
+__host__ __device__ inline void governor_update(GovState& s, const GovParams& p, double g,
+                                                double low_bound, double vol) {
+    if (g <= p.bound) {
+        s.gap = s.vstar - low_bound;
+        s.vstar = s.vstar - s.gap * s.df;
+        s.df = 0.8 * s.df;
+    }
+    const double dg = s.g_prev - g;
+    const bool cond1 = (dg < 0 ? -dg : dg) < p.small_rel * g;
+    const bool cond2 = g > p.bound;
+    const double dv = vol - s.vstar;
+    const bool cond3 = (dv < 0 ? -dv : dv) < p.vol_tol;
+    if (cond1 && cond2 && cond3)
+        s.count += 1;
+    else
+        s.count = 0;
+    if (s.count >= 5) {
+        s.vstar = s.vstar + 0.3 * s.gap * s.df;
+        s.count = 0;
+    }
+    if (s.vstar > 1.0) s.vstar = 1.0;
+    if (s.vstar < 0.0) s.vstar = 0.0;
+    s.g_prev = g;
+}
+
+constexpr int kOcCand = 64;   // candidates per OC search pass
+
+struct DesignScalars {
+    double sum_rho;          // sum of rho
+    double sum_rhop;         // sum of rho_f^p
+    double kappa[6];
+    double g;
+    double w[6];             // dg / dkappa_c
+    double target[6];
+    double vstar;
+    GovState gov;
+    GovParams govp;
+    int governor_on;
+    int objective;
+    // OC search
+    double oc_vmin, oc_vmax;       // sums: all-lower and all-upper (growing) volume
+    double mu_lo, mu_hi;           // current bracket of mu = lambda^-eta
+    double v_lo, v_hi;             // volume sums at the bracket ends
+    double mu_star;
+    double lambda;
+    int oc_mode;                   // 0 interior, 1 inactive, 2 infeasible
+    int oc_pass;
+    double mu_min_seen, mu_max_seen;
+};
+
+}  // namespace otm

@@ -1,0 +1,274 @@
+// Operator-level C entry points (include/otm.h, "operator-level entry
+// points"): one kernel (or one short kernel chain) per call on caller-owned
+// device buffers, for testing and profiling.  Calls that reduce to scalars
+// take their partial-sum scratch from the stream-ordered allocator.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "kernels_design.cuh"
+#include "kernels_fine.cuh"
+#include "otm_internal.cuh"
+
+namespace otm {
+void set_thread_error(const std::string& msg);
+}
+
+namespace {
+
+otm_status op_fail(otm_status st, const std::string& m) {
+    otm::set_thread_error(m);
+    return st;
+}
+
+struct OpCtx {
+    cudaStream_t st;
+    int blocks;
+    int max_blocks;
+    explicit OpCtx(void* stream) : st((cudaStream_t)stream) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        max_blocks = (sms > 0 ? sms : 1) * 8;
+        blocks = max_blocks;
+    }
+    int grid(size_t work) const {
+        size_t b = (work + 255) / 256;
+        if (b < 1) b = 1;
+        if (b > (size_t)max_blocks) b = max_blocks;
+        return (int)b;
+    }
+};
+
+// Scratch for a reduction: partials, ticket counter and a DesignScalars block.
+struct Scratch {
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    otm::DesignScalars* ds = nullptr;
+    cudaStream_t st = nullptr;
+    cudaError_t alloc(cudaStream_t s, int max_blocks) {
+        st = s;
+        cudaError_t e = cudaMallocAsync((void**)&partials, (size_t)max_blocks * otm::kRedMaxVals * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+        e = cudaMallocAsync((void**)&counter, 16, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMemsetAsync(counter, 0, 16, s);
+        if (e != cudaSuccess) return e;
+        e = cudaMallocAsync((void**)&ds, sizeof(otm::DesignScalars), s);
+        if (e != cudaSuccess) return e;
+        return cudaMemsetAsync(ds, 0, sizeof(otm::DesignScalars), s);
+    }
+    ~Scratch() {
+        if (partials) cudaFreeAsync(partials, st);
+        if (counter) cudaFreeAsync(counter, st);
+        if (ds) cudaFreeAsync(ds, st);
+    }
+};
+
+otm_status finish(cudaStream_t st, const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return op_fail(OTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return OTM_OK;
+}
+
+bool bad_dtype(int dtype) { return dtype != OTM_FP32 && dtype != OTM_FP64; }
+
+otm::FilterW filter_w(double rmin) {
+    otm::FilterW fw;
+    memset(&fw, 0, sizeof(fw));
+    fw.R = (int)std::ceil(rmin) - 1;
+    for (int d2 = 0; d2 < 13; ++d2) {
+        const double d = std::sqrt((double)d2);
+        fw.w[d2] = d < rmin ? rmin - d : 0.0;
+    }
+    double wsum = 0.0;
+    for (int dz = -fw.R; dz <= fw.R; ++dz)
+        for (int dy = -fw.R; dy <= fw.R; ++dy)
+            for (int dx = -fw.R; dx <= fw.R; ++dx) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 <= 12) wsum += fw.w[d2];
+            }
+    fw.inv_wsum = 1.0 / wsum;
+    return fw;
+}
+
+otm::SimpP simp_p(double penal, double ks, double kv) {
+    otm::SimpP sp;
+    memset(&sp, 0, sizeof(sp));
+    sp.penal = penal;
+    sp.k_solid = ks;
+    sp.k_void = kv;
+    sp.cubic = penal == 3.0;
+    return sp;
+}
+
+template <class R>
+otm_status filter_simp_t(int n, double rmin, double penal, double ks, double kv, const void* rho, void* rho_f,
+                         void* k, void* stream) {
+    OpCtx oc(stream);
+    Scratch sc;
+    if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_filter_simp: scratch");
+    const size_t N = (size_t)n * n * n;
+    otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
+    otm::k_filter<R, true><<<oc.grid(N), 256, 0, oc.st>>>(n, filter_w(rmin), 1, (const R*)rho, (R*)rho_f, (R*)k,
+                                                          simp_p(penal, ks, kv), rb, otm::FinFilter{sc.ds});
+    return finish(oc.st, "otm_op_filter_simp");
+}
+
+template <class R>
+otm_status filter_t_t(int n, double rmin, const void* s_f, void* s, void* stream) {
+    OpCtx oc(stream);
+    const size_t N = (size_t)n * n * n;
+    otm::RedBuf rb{nullptr, nullptr, 0};
+    otm::k_filter<R, false><<<oc.grid(N), 256, 0, oc.st>>>(n, filter_w(rmin), -1, (const R*)s_f, (R*)s, nullptr,
+                                                           simp_p(3, 1, 1e-3), rb, otm::FinFilter{nullptr});
+    return finish(oc.st, "otm_op_filter_transpose");
+}
+
+template <class R>
+otm_status macro_load_t(int n, const void* k, void* f, void* stream) {
+    OpCtx oc(stream);
+    const size_t N = (size_t)n * n * n;
+    otm::k_macro_load<R, R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)k, (R*)f);
+    return finish(oc.st, "otm_op_macro_load");
+}
+
+template <class R>
+otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream) {
+    OpCtx oc(stream);
+    const size_t N = (size_t)n * n * n;
+    otm::RedBuf rb{nullptr, nullptr, 0};
+    otm::k_stencil_apply<0, false, R, R, R, R, otm::FinNone><<<oc.grid(N), 256, 0, oc.st>>>(
+        n, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
+    return finish(oc.st, "otm_op_apply_K");
+}
+
+template <class R>
+otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* stream) {
+    OpCtx oc(stream);
+    const size_t work = (size_t)n * n * n / 8;
+    otm::k_gs_fine<false, R, R, R><<<oc.grid(work), 256, 0, oc.st>>>(n, colour >> 1, colour & 1, (const R*)k,
+                                                                      (const R*)f, (R*)T);
+    return finish(oc.st, "otm_op_gs_colour");
+}
+
+template <class R>
+otm_status kappa_sens_t(int n, double penal, double ks, double kv, const void* k, const void* rho_f,
+                        const void* chi, const double w[6], double kappa_out[6], void* s_f, void* stream) {
+    OpCtx oc(stream);
+    Scratch sc;
+    if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_kappa_sens: scratch");
+    const size_t N = (size_t)n * n * n;
+    otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
+    otm::k_kappa<R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)k, (const R*)chi, rb,
+                                                  otm::FinKappa{sc.ds, 1.0 / (double)N, 0});
+    if (s_f) {
+        cudaMemcpyAsync(&sc.ds->w[0], w, 6 * sizeof(double), cudaMemcpyHostToDevice, oc.st);
+        otm::k_sens<R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)rho_f, (const R*)chi, sc.ds,
+                                                     simp_p(penal, ks, kv), (R*)s_f);
+    }
+    double kap[6];
+    cudaMemcpyAsync(kap, &sc.ds->kappa[0], 6 * sizeof(double), cudaMemcpyDeviceToHost, oc.st);
+    otm_status st = finish(oc.st, "otm_op_kappa_sens");
+    if (st == OTM_OK)
+        for (int c = 0; c < 6; ++c) kappa_out[c] = kap[c];
+    return st;
+}
+
+template <class R>
+otm_status oc_t(int n, double vstar, double move, double damp, double rho_min, const void* rho, const void* s,
+                void* rho_new, double* lambda_out, void* stream) {
+    OpCtx oc(stream);
+    Scratch sc;
+    if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_oc_update: scratch");
+    const size_t N = (size_t)n * n * n;
+    const double dN = (double)N;
+    otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
+    otm::OcP op;
+    memset(&op, 0, sizeof(op));
+    op.move = move;
+    op.damp = damp;
+    op.rho_min = rho_min;
+    op.half = damp == 0.5;
+    otm::k_governor<<<1, 1, 0, oc.st>>>(sc.ds, 1.0 / dN, 1, vstar);
+    otm::k_oc_prep<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, rb,
+                                                    otm::FinOcPrep{sc.ds, dN});
+    const int passes = sizeof(R) == 8 ? 7 : 4;
+    for (int p = 0; p < passes; ++p) {
+        const int linear = p == passes - 1;
+        otm::k_oc_search<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, linear, rb,
+                                                          otm::FinOcSearch{sc.ds, dN, linear, linear, 1.0 / damp});
+    }
+    otm::k_oc_apply<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, (R*)rho_new);
+    double lam = 0.0;
+    cudaMemcpyAsync(&lam, &sc.ds->lambda, sizeof(double), cudaMemcpyDeviceToHost, oc.st);
+    otm_status st = finish(oc.st, "otm_op_oc_update");
+    if (st == OTM_OK && lambda_out) *lambda_out = lam;
+    return st;
+}
+
+bool bad_n(int n) { return n < 4 || n > 512; }
+
+}  // namespace
+
+#define OP_CHECK(cond, msg) \
+    do {                    \
+        if (cond) return op_fail(OTM_EINVAL, msg); \
+    } while (0)
+
+extern "C" {
+
+otm_status otm_op_filter_simp(int dtype, int n, double rmin, double penal, double k_solid, double k_void,
+                              const void* rho, void* rho_f, void* k, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !rho || !rho_f || !k, "otm_op_filter_simp: bad argument");
+    OP_CHECK(!(rmin >= 1.0 && rmin < 3.0), "otm_op_filter_simp: rmin must be in [1, 3)");
+    if (dtype == OTM_FP64) return filter_simp_t<double>(n, rmin, penal, k_solid, k_void, rho, rho_f, k, stream);
+    return filter_simp_t<float>(n, rmin, penal, k_solid, k_void, rho, rho_f, k, stream);
+}
+
+otm_status otm_op_filter_transpose(int dtype, int n, double rmin, const void* s_f, void* s, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !s_f || !s, "otm_op_filter_transpose: bad argument");
+    OP_CHECK(!(rmin >= 1.0 && rmin < 3.0), "otm_op_filter_transpose: rmin must be in [1, 3)");
+    if (dtype == OTM_FP64) return filter_t_t<double>(n, rmin, s_f, s, stream);
+    return filter_t_t<float>(n, rmin, s_f, s, stream);
+}
+
+otm_status otm_op_macro_load(int dtype, int n, const void* k, void* f, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !k || !f, "otm_op_macro_load: bad argument");
+    if (dtype == OTM_FP64) return macro_load_t<double>(n, k, f, stream);
+    return macro_load_t<float>(n, k, f, stream);
+}
+
+otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u, void* Ku, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !k || !u || !Ku, "otm_op_apply_K: bad argument");
+    if (dtype == OTM_FP64) return apply_K_t<double>(n, k, u, Ku, stream);
+    return apply_K_t<float>(n, k, u, Ku, stream);
+}
+
+otm_status otm_op_gs_colour(int dtype, int n, const void* k, const void* f, void* T, int colour, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || (n & 1) || !k || !f || !T || colour < 0 || colour > 7,
+             "otm_op_gs_colour: bad argument (n must be even, colour in [0, 8))");
+    if (dtype == OTM_FP64) return gs_t<double>(n, k, f, T, colour, stream);
+    return gs_t<float>(n, k, f, T, colour, stream);
+}
+
+otm_status otm_op_kappa_sens(int dtype, int n, double penal, double k_solid, double k_void, const void* k,
+                             const void* rho_f, const void* chi, const double w[6], double kappa_out[6], void* s_f,
+                             void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !k || !chi || !kappa_out, "otm_op_kappa_sens: bad argument");
+    OP_CHECK(s_f && (!rho_f || !w), "otm_op_kappa_sens: s_f needs rho_f and w");
+    if (dtype == OTM_FP64)
+        return kappa_sens_t<double>(n, penal, k_solid, k_void, k, rho_f, chi, w, kappa_out, s_f, stream);
+    return kappa_sens_t<float>(n, penal, k_solid, k_void, k, rho_f, chi, w, kappa_out, s_f, stream);
+}
+
+otm_status otm_op_oc_update(int dtype, int n, double vstar, double move, double damp, double rho_min,
+                            const void* rho, const void* s, void* rho_new, double* lambda_out, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !rho || !s || !rho_new, "otm_op_oc_update: bad argument");
+    OP_CHECK(!(move > 0 && damp > 0 && rho_min >= 0 && rho_min < 1), "otm_op_oc_update: bad OC parameters");
+    if (dtype == OTM_FP64) return oc_t<double>(n, vstar, move, damp, rho_min, rho, s, rho_new, lambda_out, stream);
+    return oc_t<float>(n, vstar, move, damp, rho_min, rho, s, rho_new, lambda_out, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,761 @@
+// Host-side orchestration of one design context on one GPU stream:
+// buffers, the multigrid hierarchy, the three-load-case MG-PCG solve and the
+// design iteration.  Instantiated per precision in solver_*.cu.
+#pragma once
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "kernels_design.cuh"
+#include "kernels_fine.cuh"
+#include "kernels_mg.cuh"
+#include "otm_internal.cuh"
+
+namespace otm {
+
+constexpr int kMaxLevels = 12;
+
+// Abstract interface used by the C ABI.
+struct SolverBase {
+    virtual ~SolverBase() {}
+    virtual otm_status init(const otm_params& p) = 0;
+    virtual otm_status set_density(const float* rho, bool on_device) = 0;
+    virtual otm_status get_density(float* rho, bool on_device) = 0;
+    virtual otm_status get_field(int which, float* out, size_t count, bool on_device) = 0;
+    virtual otm_status homogenize(const float* rho, bool on_device, double kappa[6], otm_step_info* info) = 0;
+    virtual otm_status step(otm_step_info* info) = 0;
+    virtual size_t state_size() const = 0;
+    virtual otm_status get_state(void* buf) = 0;
+    virtual otm_status set_state(const void* buf, size_t len) = 0;
+    std::string err;
+    otm_params prm;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+};
+
+SolverBase* make_solver_f64();
+SolverBase* make_solver_f32();
+SolverBase* make_solver_mixed();
+
+// Checks a CUDA call; on failure records the message and returns OTM_ECUDA.
+#define OTM_CU(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                  \
+            return e_ == cudaErrorMemoryAllocation ? OTM_ENOMEM : OTM_ECUDA;           \
+        }                                                                              \
+    } while (0)
+#define OTM_LAUNCH()                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            err = std::string("kernel launch: ") + cudaGetErrorString(e_);             \
+            return OTM_ECUDA;                                                          \
+        }                                                                              \
+    } while (0)
+#define OTM_TRY(expr)                                                                  \
+    do {                                                                               \
+        otm_status s_ = (expr);                                                        \
+        if (s_ != OTM_OK) return s_;                                                   \
+    } while (0)
+
+// Host-side constant tables of the hierarchy (the GPU path's own derivation
+// of K0 from the 1-D stiffness and mass matrices, see kernels_fine.cuh).
+inline double k0_entry(int l, int m) {
+    const int pc = __builtin_popcount(l ^ m);
+    return pc == 0 ? 1.0 / 3.0 : (pc == 1 ? 0.0 : -1.0 / 12.0);
+}
+inline double phi_w(int t, int m) {
+    static const double w0[3] = {1.0, 0.5, 0.0};
+    static const double w1[3] = {0.0, 0.5, 1.0};
+    return m ? w1[t] : w0[t];
+}
+inline void build_ps(std::vector<double>& Ps, std::vector<double>& Bs) {
+    Ps.assign(8 * 64, 0.0);
+    Bs.assign(8 * 64, 0.0);
+    for (int s = 0; s < 8; ++s) {
+        for (int j = 0; j < 8; ++j)
+            for (int m = 0; m < 8; ++m) {
+                double w = 1.0;
+                for (int d = 0; d < 3; ++d) w *= phi_w(((s >> d) & 1) + ((j >> d) & 1), (m >> d) & 1);
+                Ps[s * 64 + j * 8 + m] = w;
+            }
+        for (int m = 0; m < 8; ++m)
+            for (int mp = 0; mp < 8; ++mp) {
+                double a = 0.0;
+                for (int j = 0; j < 8; ++j)
+                    for (int jp = 0; jp < 8; ++jp)
+                        a += Ps[s * 64 + j * 8 + m] * k0_entry(j, jp) * Ps[s * 64 + jp * 8 + mp];
+                Bs[s * 64 + m * 8 + mp] = a;
+            }
+    }
+}
+
+inline FilterW make_filter(double rmin) {
+    FilterW fw;
+    memset(&fw, 0, sizeof(fw));
+    fw.R = (int)std::ceil(rmin) - 1;
+    double wsum = 0.0;
+    for (int d2 = 0; d2 < 13; ++d2) {
+        const double d = std::sqrt((double)d2);
+        fw.w[d2] = d < rmin ? rmin - d : 0.0;
+    }
+    for (int dz = -fw.R; dz <= fw.R; ++dz)
+        for (int dy = -fw.R; dy <= fw.R; ++dy)
+            for (int dx = -fw.R; dx <= fw.R; ++dx) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 <= 12) wsum += fw.w[d2];
+            }
+    fw.inv_wsum = 1.0 / wsum;
+    return fw;
+}
+
+inline void level_sizes(int n, std::vector<int>& sizes) {
+    sizes.clear();
+    sizes.push_back(n);
+    while (sizes.back() % 2 == 0 && sizes.back() / 2 >= 4) sizes.push_back(sizes.back() / 2);
+}
+
+// R: PCG vectors and design fields.  S: V-cycle storage.
+template <class R, class S>
+class Solver : public SolverBase {
+  public:
+    using C = typename St<R>::C;
+    int n = 0;
+    size_t N = 0;
+    int nlev = 0;
+    int sz[kMaxLevels];
+    size_t Nl[kMaxLevels];
+    int sm_count = 0, max_blocks = 0;
+    long long nl_ = 0;   // kernel launches issued (for the step report)
+
+    // fine fields
+    R *rho = nullptr, *rho_f = nullptr, *kf = nullptr, *s_f = nullptr, *s = nullptr, *rho_tmp = nullptr;
+    R *f = nullptr, *x = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    S *z = nullptr, *res0 = nullptr, *k_vc = nullptr;
+    // coarse levels 1..nlev-1 (level 0 uses z / r / res0 / k_vc)
+    S *Tl[kMaxLevels] = {}, *Fl[kMaxLevels] = {}, *Rl[kMaxLevels] = {}, *Al[kMaxLevels] = {};
+    C *Kel[kMaxLevels] = {};
+    C *Bs_d = nullptr, *Ps_d = nullptr, *Minv = nullptr;
+    double* Wd = nullptr;
+    // reductions and scalars
+    double* partials = nullptr;
+    unsigned int* counter = nullptr;
+    PcgScalars* ps = nullptr;
+    DesignScalars* ds = nullptr;
+    PcgScalars* ps_h = nullptr;
+    DesignScalars* ds_h = nullptr;
+    float* stage_f = nullptr;   // float staging for host/device field copies of R != float
+
+    FilterW fw;
+    SimpP sp;
+    OcP op;
+    bool have_prev = false;
+    int iteration = 0;
+    GovState gov_init;
+    cudaEvent_t ev[8] = {};
+
+    ~Solver() override { release(); }
+
+    void release() {
+        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
+                        partials, counter, ps, ds, stage_f};
+        for (void* ptr : ptrs)
+            if (ptr) cudaFree(ptr);
+        if (k_vc && (void*)k_vc != (void*)kf) cudaFree(k_vc);
+        for (int l = 0; l < kMaxLevels; ++l) {
+            if (Tl[l]) cudaFree(Tl[l]);
+            if (Fl[l]) cudaFree(Fl[l]);
+            if (Rl[l]) cudaFree(Rl[l]);
+            if (Al[l]) cudaFree(Al[l]);
+            if (Kel[l]) cudaFree(Kel[l]);
+        }
+        if (ps_h) cudaFreeHost(ps_h);
+        if (ds_h) cudaFreeHost(ds_h);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        rho = nullptr;
+    }
+
+    RedBuf rbuf() const { return RedBuf{partials, counter, max_blocks}; }
+    int grid(size_t work, int threads = 256) const {
+        size_t b = (work + threads - 1) / threads;
+        if (b < 1) b = 1;
+        if (b > (size_t)max_blocks) b = max_blocks;
+        return (int)b;
+    }
+
+    template <class T>
+    otm_status alloc(T*& ptr, size_t count) {
+        OTM_CU(cudaMalloc((void**)&ptr, count * sizeof(T) + 16));
+        OTM_CU(cudaMemsetAsync(ptr, 0, count * sizeof(T) + 16, stream));
+        return OTM_OK;
+    }
+
+    otm_status init(const otm_params& pin) override {
+        prm = pin;
+        n = pin.n;
+        N = (size_t)n * n * n;
+        std::vector<int> sizes;
+        level_sizes(n, sizes);
+        nlev = (int)sizes.size();
+        for (int l = 0; l < nlev; ++l) {
+            sz[l] = sizes[l];
+            Nl[l] = (size_t)sizes[l] * sizes[l] * sizes[l];
+        }
+        if (pin.device >= 0) OTM_CU(cudaSetDevice(pin.device));
+        OTM_CU(cudaGetDevice(&device));
+        OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
+        max_blocks = sm_count * 8;
+        if (pin.stream) {
+            stream = (cudaStream_t)pin.stream;
+        } else {
+            OTM_CU(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        for (auto& e : ev) OTM_CU(cudaEventCreate(&e));
+
+        OTM_TRY(alloc(rho, N));
+        OTM_TRY(alloc(rho_f, N));
+        OTM_TRY(alloc(kf, N));
+        OTM_TRY(alloc(s_f, N));
+        OTM_TRY(alloc(s, N));
+        OTM_TRY(alloc(rho_tmp, N));
+        OTM_TRY(alloc(f, 3 * N));
+        OTM_TRY(alloc(x, 3 * N));
+        if (!std::is_same<C, double>::value) OTM_TRY(alloc(xl, 3 * N));
+        OTM_TRY(alloc(r, 3 * N));
+        OTM_TRY(alloc(p, 3 * N));
+        OTM_TRY(alloc(q, 3 * N));
+        OTM_TRY(alloc(z, 3 * N));
+        OTM_TRY(alloc(res0, 3 * N));
+        OTM_TRY(alloc(stage_f, 3 * N));
+        if (std::is_same<R, S>::value) k_vc = (S*)kf;
+        else OTM_TRY(alloc(k_vc, N));
+        for (int l = 1; l < nlev; ++l) {
+            OTM_TRY(alloc(Tl[l], 3 * Nl[l]));
+            OTM_TRY(alloc(Fl[l], 3 * Nl[l]));
+            OTM_TRY(alloc(Rl[l], 3 * Nl[l]));
+            OTM_TRY(alloc(Al[l], 27 * Nl[l]));
+            OTM_TRY(alloc(Kel[l], 64 * Nl[l]));
+        }
+        if (nlev == 1) OTM_TRY(alloc(Al[0], 27 * Nl[0]));
+        const size_t m = Nl[nlev - 1];
+        OTM_TRY(alloc(Wd, (m - 1) * (m - 1)));
+        OTM_TRY(alloc(Minv, (m - 1) * (m - 1)));
+        std::vector<double> Ps, Bs;
+        build_ps(Ps, Bs);
+        std::vector<C> Psc(Ps.begin(), Ps.end()), Bsc(Bs.begin(), Bs.end());
+        OTM_TRY(alloc(Ps_d, 8 * 64));
+        OTM_TRY(alloc(Bs_d, 8 * 64));
+        OTM_CU(cudaMemcpyAsync(Ps_d, Psc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaMemcpyAsync(Bs_d, Bsc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
+        OTM_TRY(alloc(partials, (size_t)max_blocks * kRedMaxVals));
+        OTM_TRY(alloc(counter, 4));
+        OTM_TRY(alloc(ps, 1));
+        OTM_TRY(alloc(ds, 1));
+        OTM_CU(cudaMallocHost((void**)&ps_h, sizeof(PcgScalars)));
+        OTM_CU(cudaMallocHost((void**)&ds_h, sizeof(DesignScalars)));
+
+        fw = make_filter(pin.rmin);
+        sp.penal = pin.penal;
+        sp.k_solid = pin.k_solid;
+        sp.k_void = pin.k_void;
+        sp.cubic = pin.penal == 3.0;
+        op.move = pin.move;
+        op.damp = pin.damp;
+        op.rho_min = pin.rho_min;
+        op.half = pin.damp == 0.5;
+
+        memset(ds_h, 0, sizeof(DesignScalars));
+        gov_init.df = 1.0;
+        gov_init.vstar = 1.0;
+        gov_init.g_prev = 1.0;
+        gov_init.gap = 0.0;
+        gov_init.count = 0;
+        ds_h->gov = gov_init;
+        ds_h->govp.bound = pin.gov_bound;
+        ds_h->govp.small_rel = pin.gov_small_rel;
+        ds_h->govp.vol_tol = pin.gov_vol_tol;
+        ds_h->governor_on = pin.governor;
+        ds_h->objective = pin.objective;
+        for (int c = 0; c < 6; ++c) ds_h->target[c] = pin.kappa_target[c];
+        ds_h->vstar = pin.governor ? 1.0 : pin.fixed_volume;
+        OTM_CU(cudaMemcpyAsync(ds, ds_h, sizeof(DesignScalars), cudaMemcpyHostToDevice, stream));
+        memset(ps_h, 0, sizeof(PcgScalars));
+        ps_h->tol2 = pin.cg_tol * pin.cg_tol;
+        ps_h->flexible = std::is_same<R, S>::value ? 0 : 1;
+        OTM_CU(cudaMemcpyAsync(ps, ps_h, sizeof(PcgScalars), cudaMemcpyHostToDevice, stream));
+        // uniform initial density
+        std::vector<float> h(N, (float)pin.volfrac);
+        OTM_TRY(set_density(h.data(), false));
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+
+    // ---------------------------------------------------------- conversions
+    // float (host or device) -> R field, through the float staging buffer.
+    otm_status to_R(const float* src, bool on_device, R* dst, size_t count, bool clamp01) {
+        OTM_CU(cudaMemcpyAsync(stage_f, src, count * sizeof(float),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+        ++nl_;
+        k_convert<float, R><<<grid(count), 256, 0, stream>>>(count, stage_f, dst, clamp01 ? 1 : 0);
+        OTM_LAUNCH();
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+    // R field -> float (host or device).
+    otm_status from_R(const R* src, float* dst, size_t count, bool on_device) {
+        ++nl_;
+        k_convert<R, float><<<grid(count), 256, 0, stream>>>(count, src, stage_f, 0);
+        OTM_LAUNCH();
+        OTM_CU(cudaMemcpyAsync(dst, stage_f, count * sizeof(float),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+
+    otm_status set_density(const float* h, bool on_device) override {
+        OTM_TRY(to_R(h, on_device, rho, N, true));
+        have_prev = false;
+        iteration = 0;
+        // reset Alg. 1 state
+        OTM_CU(cudaMemcpyAsync(&ds->gov, &gov_init, sizeof(GovState), cudaMemcpyHostToDevice, stream));
+        const double v0 = prm.governor ? 1.0 : prm.fixed_volume;
+        OTM_CU(cudaMemcpyAsync(&ds->vstar, &v0, sizeof(double), cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+
+    otm_status get_density(float* out, bool on_device) override {
+        OTM_TRY(from_R(rho, out, N, on_device));
+        return OTM_OK;
+    }
+
+    otm_status get_field(int which, float* out, size_t count, bool on_device) override {
+        const R* src = nullptr;
+        size_t len = N;
+        switch (which) {
+            case OTM_FIELD_RHO: src = rho; break;
+            case OTM_FIELD_RHO_FILT: src = rho_f; break;
+            case OTM_FIELD_K: src = kf; break;
+            case OTM_FIELD_CHI:
+                if (count != 3 * N) {
+                    err = "otm_get_field: count does not match the field length";
+                    return OTM_EINVAL;
+                }
+                ++nl_;
+                k_join<R, float><<<grid(3 * N), 256, 0, stream>>>(3 * N, x, xl, stage_f);
+                OTM_LAUNCH();
+                OTM_CU(cudaMemcpyAsync(out, stage_f, 3 * N * sizeof(float),
+                                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+                OTM_CU(cudaStreamSynchronize(stream));
+                return OTM_OK;
+            case OTM_FIELD_LOAD: src = f; len = 3 * N; break;
+            case OTM_FIELD_SENS: src = s; break;
+            default: err = "otm_get_field: unknown field"; return OTM_EINVAL;
+        }
+        if (count != len) {
+            err = "otm_get_field: count does not match the field length";
+            return OTM_EINVAL;
+        }
+        return from_R(src, out, len, on_device);
+    }
+
+    // --------------------------------------------------------------- stages
+    otm_status filter_simp() {
+        ++nl_;
+        k_filter<R, true><<<grid(N), 256, 0, stream>>>(n, fw, 1, rho, rho_f, kf, sp, rbuf(), FinFilter{ds});
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+
+    otm_status build_hierarchy() {
+        ++nl_;
+        k_macro_load<R, R><<<grid(N), 256, 0, stream>>>(n, kf, f);
+        ++nl_;
+        k_sum3<R><<<grid(N), 256, 0, stream>>>(N, f, rbuf(), FinMean{ps, 1.0 / (double)N});
+        ++nl_;
+        k_sub_mean<R><<<grid(N), 256, 0, stream>>>(N, f, ps);
+        OTM_LAUNCH();
+        if (!std::is_same<R, S>::value) {
+            ++nl_;
+            k_convert<R, S><<<grid(N), 256, 0, stream>>>(N, kf, k_vc, 0);
+            OTM_LAUNCH();
+        }
+        if (nlev == 1) {
+            ++nl_;
+            k_stencil_from_k<R, C, S><<<grid(N, 128), 128, 0, stream>>>(n, kf, Al[0]);
+            OTM_LAUNCH();
+        } else {
+            ++nl_;
+            k_elem_from_k<R, C><<<grid(Nl[1], 128), 128, 0, stream>>>(sz[1], kf, Bs_d, Kel[1]);
+            OTM_LAUNCH();
+            ++nl_;
+            k_stencil_from_elem<C, S><<<grid(Nl[1], 128), 128, 0, stream>>>(sz[1], Kel[1], Al[1]);
+            OTM_LAUNCH();
+            for (int l = 1; l + 1 < nlev; ++l) {
+                ++nl_;
+                k_elem_coarsen<C><<<grid(Nl[l + 1], 64), 64, 0, stream>>>(sz[l + 1], Kel[l], Ps_d, Kel[l + 1]);
+                OTM_LAUNCH();
+                ++nl_;
+                k_stencil_from_elem<C, S><<<grid(Nl[l + 1], 128), 128, 0, stream>>>(sz[l + 1], Kel[l + 1], Al[l + 1]);
+                OTM_LAUNCH();
+            }
+        }
+        const int L = nlev - 1;
+        ++nl_;
+        k_coarse_invert<S, C><<<1, 1024, 0, stream>>>(sz[L], Al[L], Wd, Minv);
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+
+    // z = V(r): one V-cycle of Alg. 3 with a forward 8-colour Gauss-Seidel
+    // sweep before and the reverse sweep after the coarse correction.
+    otm_status vcycle() {
+        const int L = nlev - 1;
+        if (nlev == 1) {
+            ++nl_;
+            k_coarse_solve<C, R, S><<<1, 1024, 0, stream>>>(sz[0], Minv, r, z);
+            OTM_LAUNCH();
+            return OTM_OK;
+        }
+        const int gq = grid(Nl[0] / 4);
+        // level 0, pre-smooth: groups {0,1}, {2,3}, {4,5}, {6,7}
+        ++nl_;
+        k_gs_fine<true, S, R, S><<<gq, 256, 0, stream>>>(n, 0, -1, k_vc, r, z);
+        for (int gidx = 1; gidx < 4; ++gidx) {
+            ++nl_;
+            k_gs_fine<false, S, R, S><<<gq, 256, 0, stream>>>(n, gidx, -1, k_vc, r, z);
+        }
+        ++nl_;
+        k_stencil_apply<1, false, S, S, R, S, FinNone><<<grid(N), 256, 0, stream>>>(n, k_vc, z, r, res0, rbuf(), FinNone{});
+        ++nl_;
+        k_restrict<S, S><<<grid(Nl[1]), 256, 0, stream>>>(sz[1], res0, Fl[1]);
+        OTM_LAUNCH();
+        for (int l = 1; l < L; ++l) {
+            const int gc = grid(Nl[l] / 8);
+            ++nl_;
+            k_gs_stencil<true, S, S, S><<<gc, 256, 0, stream>>>(sz[l], 0, Al[l], Fl[l], Tl[l]);
+            for (int c = 1; c < 8; ++c) {
+                ++nl_;
+                k_gs_stencil<false, S, S, S><<<gc, 256, 0, stream>>>(sz[l], c, Al[l], Fl[l], Tl[l]);
+            }
+            ++nl_;
+            k_residual_stencil<S, S, S, S><<<grid(Nl[l]), 256, 0, stream>>>(sz[l], Al[l], Fl[l], Tl[l], Rl[l]);
+            ++nl_;
+            k_restrict<S, S><<<grid(Nl[l + 1]), 256, 0, stream>>>(sz[l + 1], Rl[l], Fl[l + 1]);
+            OTM_LAUNCH();
+        }
+        ++nl_;
+        k_coarse_solve<C, S, S><<<1, 1024, 0, stream>>>(sz[L], Minv, Fl[L], Tl[L]);
+        OTM_LAUNCH();
+        for (int l = L - 1; l >= 1; --l) {
+            ++nl_;
+            k_prolong_add<S, S><<<grid(Nl[l]), 256, 0, stream>>>(sz[l], Tl[l + 1], Tl[l]);
+            const int gc = grid(Nl[l] / 8);
+            for (int c = 7; c >= 0; --c) {
+                ++nl_;
+                k_gs_stencil<false, S, S, S><<<gc, 256, 0, stream>>>(sz[l], c, Al[l], Fl[l], Tl[l]);
+            }
+            OTM_LAUNCH();
+        }
+        ++nl_;
+        k_prolong_add<S, S><<<grid(N), 256, 0, stream>>>(n, Tl[1], z);
+        for (int gidx = 3; gidx >= 0; --gidx) {
+            ++nl_;
+            k_gs_fine<false, S, R, S><<<gq, 256, 0, stream>>>(n, gidx, -1, k_vc, r, z);
+        }
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+
+    // MG-PCG for the three load cases, starting from x (zero or warm), as
+    // iterative refinement: each pass forms r = f - K x from the stored
+    // iterate (x held as an FP32 pair hi + lo in the FP32/mixed paths), runs
+    // PCG on the correction until the recurrence residual meets cg_tol, and
+    // then checks ||f - K x|| / ||f|| with error-free element terms.  A pass
+    // that does not halve the worst checked residual ends the solve.
+    // Returns OTM_OK when every load case meets cg_tol, else OTM_ENOCONV.
+    static constexpr int kMaxRestarts = 6;
+    int last_iters[3] = {0, 0, 0};
+
+    otm_status solve(int* iters_out, double* resid_out) {
+        RedBuf rb = rbuf();
+        int total = 0;
+        int iters[3] = {0, 0, 0};
+        bool converged = false;
+        double prev_worst = 1e300;
+        int use_true = 0;
+        for (int restart = 0;; ++restart) {
+            ++nl_;
+            k_residual_x2<R, FinInit><<<grid(N), 256, 0, stream>>>(n, kf, x, xl, f, r, rb, FinInit{ps, use_true});
+            OTM_LAUNCH();
+            OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+            OTM_CU(cudaStreamSynchronize(stream));
+            if (ps_h->nactive > 0 && total < prm.cg_maxit) {
+                OTM_TRY(vcycle());
+                ++nl_;
+                k_dot_rz<R, S><<<grid(N), 256, 0, stream>>>(N, r, z, rb, FinBeta{ps, 1});
+                ++nl_;
+                k_update_p<R, S><<<grid(N), 256, 0, stream>>>(N, p, z, ps, 1);
+                OTM_LAUNCH();
+                while (total < prm.cg_maxit) {
+                    ++nl_;
+                    k_stencil_apply<0, true, R, R, R, R, FinAlpha><<<grid(N), 256, 0, stream>>>(
+                        n, kf, p, (const R*)nullptr, q, rb, FinAlpha{ps});
+                    ++nl_;
+                    k_update_xr<R, S><<<grid(N), 256, 0, stream>>>(N, x, xl, r, p, q, z, ps, rb, FinResid{ps});
+                    OTM_LAUNCH();
+                    ++total;
+                    OTM_CU(cudaMemcpyAsync(&ps_h->nactive, &ps->nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+                    OTM_CU(cudaStreamSynchronize(stream));
+                    if (ps_h->nactive == 0) break;
+                    OTM_TRY(vcycle());
+                    ++nl_;
+                    k_dot_rz<R, S><<<grid(N), 256, 0, stream>>>(N, r, z, rb, FinBeta{ps, 0});
+                    ++nl_;
+                    k_update_p<R, S><<<grid(N), 256, 0, stream>>>(N, p, z, ps, 0);
+                    OTM_LAUNCH();
+                }
+                OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+                OTM_CU(cudaStreamSynchronize(stream));
+                for (int i = 0; i < 3; ++i) iters[i] += ps_h->iters[i];
+            }
+            ++nl_;
+            k_true_residual<R><<<grid(N), 256, 0, stream>>>(n, kf, x, xl, f, rb, FinTrue{ps});
+            OTM_LAUNCH();
+            OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+            OTM_CU(cudaStreamSynchronize(stream));
+            double worst = 0.0;
+            bool all_ok = true;
+            for (int i = 0; i < 3; ++i) {
+                const double ff = ps_h->true_ff[i];
+                const double rel = ff > 0 ? std::sqrt(ps_h->true_rr[i] / ff) : 0.0;
+                worst = rel > worst ? rel : worst;
+                if (!(rel <= prm.cg_tol)) all_ok = false;
+            }
+            if (all_ok) {
+                converged = true;
+                break;
+            }
+            if (restart >= kMaxRestarts || total >= prm.cg_maxit || !(worst < 0.5 * prev_worst)) break;
+            prev_worst = worst;
+            use_true = 1;
+        }
+        for (int i = 0; i < 3; ++i) {
+            const double ff = ps_h->true_ff[i];
+            resid_out[i] = ff > 0 ? std::sqrt(ps_h->true_rr[i] / ff) : 0.0;
+            iters_out[i] = iters[i];
+            last_iters[i] = iters[i];
+        }
+        if (!converged) {
+            err = "PCG did not reach cg_tol (cg_maxit reached or the residual stagnated)";
+            return OTM_ENOCONV;
+        }
+        return OTM_OK;
+    }
+
+    // kappa (and the objective) from x; optionally the sensitivity chain.
+    otm_status tensor_and_sens(bool with_sens) {
+        ++nl_;
+        k_kappa<R><<<grid(N), 256, 0, stream>>>(n, kf, x, rbuf(), FinKappa{ds, 1.0 / (double)N, 1});
+        OTM_LAUNCH();
+        if (with_sens) {
+            ++nl_;
+            k_sens<R><<<grid(N), 256, 0, stream>>>(n, rho_f, x, ds, sp, s_f);
+            ++nl_;
+            k_filter<R, false><<<grid(N), 256, 0, stream>>>(n, fw, -1, s_f, s, nullptr, sp, rbuf(), FinFilter{ds});
+            OTM_LAUNCH();
+        }
+        return OTM_OK;
+    }
+
+    otm_status oc_update() {
+        const double dN = (double)N;
+        ++nl_;
+        k_oc_prep<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, rbuf(), FinOcPrep{ds, dN});
+        OTM_LAUNCH();
+        const int passes = std::is_same<C, double>::value ? 7 : 4;
+        for (int pidx = 0; pidx < passes; ++pidx) {
+            const int linear = pidx == passes - 1;
+            ++nl_;
+            k_oc_search<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, linear, rbuf(),
+                                                        FinOcSearch{ds, dN, linear, linear, 1.0 / prm.damp});
+            OTM_LAUNCH();
+        }
+        ++nl_;
+        k_oc_apply<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, rho_tmp);
+        OTM_LAUNCH();
+        std::swap(rho, rho_tmp);
+        return OTM_OK;
+    }
+
+    otm_status run_solve(bool warm, otm_step_info* info) {
+        if (!warm) {
+            OTM_CU(cudaMemsetAsync(x, 0, 3 * N * sizeof(R), stream));
+            if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));
+        }
+        int iters[3];
+        double resid[3];
+        otm_status st = solve(iters, resid);
+        if (info) {
+            for (int i = 0; i < 3; ++i) {
+                info->cg_iters[i] = iters[i];
+                info->resid[i] = resid[i];
+            }
+        }
+        return st;
+    }
+
+    otm_status homogenize(const float* rho_in, bool on_device, double kappa[6], otm_step_info* info) override {
+        R* saved = nullptr;
+        if (rho_in) {
+            saved = rho;
+            rho = rho_tmp;
+            OTM_TRY(to_R(rho_in, on_device, rho, N, true));
+        }
+        otm_status st = OTM_OK;
+        st = filter_simp();
+        if (st == OTM_OK) st = build_hierarchy();
+        otm_status sst = OTM_OK;
+        if (st == OTM_OK) sst = run_solve(false, info);
+        if (sst != OTM_OK && sst != OTM_ENOCONV) st = sst;
+        if (st == OTM_OK) st = tensor_and_sens(false);
+        if (saved) {
+            rho_tmp = rho;
+            rho = saved;
+        }
+        if (st != OTM_OK) return st;
+        OTM_CU(cudaMemcpyAsync(ds_h, ds, sizeof(DesignScalars), cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        for (int c = 0; c < 6; ++c) kappa[c] = ds_h->kappa[c];
+        if (info) {
+            info->g = ds_h->g;
+            for (int c = 0; c < 6; ++c) info->kappa[c] = ds_h->kappa[c];
+            info->mean_rho = ds_h->sum_rho / (double)N;
+            info->mean_rhop = ds_h->sum_rhop / (double)N;
+            info->vstar = ds_h->vstar;
+            info->lambda = 0.0;
+            info->iteration = iteration;
+        }
+        have_prev = false;
+        return sst;
+    }
+
+    otm_status step(otm_step_info* info) override {
+        otm_step_info loc;
+        memset(&loc, 0, sizeof(loc));
+        const long long nl0 = nl_;
+        OTM_CU(cudaEventRecord(ev[0], stream));
+        OTM_TRY(filter_simp());
+        OTM_CU(cudaEventRecord(ev[1], stream));
+        OTM_TRY(build_hierarchy());
+        OTM_CU(cudaEventRecord(ev[2], stream));
+        const bool warm = have_prev && prm.warm_start != OTM_WS_NONE;
+        otm_status sst = run_solve(warm, &loc);
+        if (sst != OTM_OK && sst != OTM_ENOCONV) return sst;
+        have_prev = true;
+        OTM_CU(cudaEventRecord(ev[3], stream));
+        OTM_TRY(tensor_and_sens(true));
+        OTM_CU(cudaEventRecord(ev[4], stream));
+        ++nl_;
+        k_governor<<<1, 1, 0, stream>>>(ds, 1.0 / (double)N, 0, 0.0);
+        OTM_LAUNCH();
+        if (prm.symmetry) {
+            ++nl_;
+            k_symmetrize<R><<<grid(N / 2 + 1), 256, 0, stream>>>(N, rho, s);
+            OTM_LAUNCH();
+        }
+        OTM_TRY(oc_update());
+        OTM_CU(cudaEventRecord(ev[5], stream));
+        OTM_CU(cudaMemcpyAsync(ds_h, ds, sizeof(DesignScalars), cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        loc.g = ds_h->g;
+        for (int c = 0; c < 6; ++c) loc.kappa[c] = ds_h->kappa[c];
+        loc.mean_rho = ds_h->sum_rho / (double)N;
+        loc.mean_rhop = ds_h->sum_rhop / (double)N;
+        loc.vstar = ds_h->vstar;
+        loc.lambda = ds_h->lambda;
+        loc.iteration = iteration;
+        float ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]); loc.stage_ms[0] = ms;
+        cudaEventElapsedTime(&ms, ev[1], ev[2]); loc.stage_ms[1] = ms;
+        cudaEventElapsedTime(&ms, ev[2], ev[3]); loc.stage_ms[2] = ms;
+        cudaEventElapsedTime(&ms, ev[3], ev[4]); loc.stage_ms[3] = ms;
+        cudaEventElapsedTime(&ms, ev[4], ev[5]); loc.stage_ms[4] = ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[5]); loc.stage_ms[7] = ms;
+        loc.kernel_launches = (int)(nl_ - nl0);
+        iteration += 1;
+        if (info) *info = loc;
+        return sst;
+    }
+
+    // ---------------------------------------------------------- checkpoint
+    struct StateHeader {
+        uint64_t magic;
+        int32_t n, precision, iteration, have_prev;
+        GovState gov;
+        double vstar;
+        uint64_t rho_bytes, chi_bytes;
+    };
+    size_t chi_bytes() const { return (xl ? 6 : 3) * N * sizeof(R); }
+    size_t state_size() const override { return sizeof(StateHeader) + N * sizeof(R) + chi_bytes(); }
+    otm_status get_state(void* buf) override {
+        StateHeader h;
+        memset(&h, 0, sizeof(h));
+        h.magic = 0x4f544d5354415445ull;
+        h.n = n;
+        h.precision = prm.precision;
+        h.iteration = iteration;
+        h.have_prev = have_prev ? 1 : 0;
+        OTM_CU(cudaMemcpyAsync(ds_h, ds, sizeof(DesignScalars), cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        h.gov = ds_h->gov;
+        h.vstar = ds_h->vstar;
+        h.rho_bytes = N * sizeof(R);
+        h.chi_bytes = chi_bytes();
+        char* b = (char*)buf;
+        memcpy(b, &h, sizeof(h));
+        OTM_CU(cudaMemcpyAsync(b + sizeof(h), rho, h.rho_bytes, cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaMemcpyAsync(b + sizeof(h) + h.rho_bytes, x, 3 * N * sizeof(R), cudaMemcpyDeviceToHost, stream));
+        if (xl)
+            OTM_CU(cudaMemcpyAsync(b + sizeof(h) + h.rho_bytes + 3 * N * sizeof(R), xl, 3 * N * sizeof(R),
+                                   cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+    otm_status set_state(const void* buf, size_t len) override {
+        if (len < sizeof(StateHeader)) {
+            err = "otm_set_state: blob too short";
+            return OTM_ESTATE;
+        }
+        StateHeader h;
+        memcpy(&h, buf, sizeof(h));
+        if (h.magic != 0x4f544d5354415445ull || h.n != n || h.precision != prm.precision ||
+            h.rho_bytes != N * sizeof(R) || h.chi_bytes != chi_bytes() || len < state_size()) {
+            err = "otm_set_state: blob does not match this context (n, precision or size)";
+            return OTM_ESTATE;
+        }
+        const char* b = (const char*)buf;
+        OTM_CU(cudaMemcpyAsync(rho, b + sizeof(h), h.rho_bytes, cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaMemcpyAsync(x, b + sizeof(h) + h.rho_bytes, 3 * N * sizeof(R), cudaMemcpyHostToDevice, stream));
+        if (xl)
+            OTM_CU(cudaMemcpyAsync(xl, b + sizeof(h) + h.rho_bytes + 3 * N * sizeof(R), 3 * N * sizeof(R),
+                                   cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaMemcpyAsync(&ds->gov, &h.gov, sizeof(GovState), cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaMemcpyAsync(&ds->vstar, &h.vstar, sizeof(double), cudaMemcpyHostToDevice, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        iteration = h.iteration;
+        have_prev = h.have_prev != 0;
+        return OTM_OK;
+    }
+
+};
+
+}  // namespace otm

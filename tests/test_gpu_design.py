@@ -1,0 +1,208 @@
+"""Design-loop parity: otm_step trajectories against the oracle's, Alg. 1
+state, checkpoint/resume, determinism, objective and constraint variants,
+and the batched entry point."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import design
+import workloads as W
+from tests.gpu_util import rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+def _otm():
+    from paper_2405_19991_gb300 import otm
+    return otm
+
+
+def _make(n, precision, tol, move=0.05, target=W.TARGET_ISOTROPIC, rmin=1.5, **kw):
+    otm = _otm()
+    p = otm.otm_params_default(n=n, precision=precision, cg_tol=tol, move=move, rmin=rmin,
+                               kappa_target=target, cg_maxit=3000, **kw)
+    return otm.otm_create_ex(p), otm
+
+
+def _rho(ctx, otm, n):
+    out = np.empty(n ** 3, np.float32)
+    otm.otm_get_density(ctx, out.ctypes.data, 0)
+    return out.astype(np.float64)
+
+
+def _oracle(n, rho0, move, target, rmin=1.5, **kw):
+    p = design.DesignParams(n=n, kappa_target=target, rmin=rmin, cg_tol=1e-12, move=move, **kw)
+    return design.Design(p, rho0)
+
+
+@pytest.mark.parametrize("move,iters", [(0.05, 20), (0.02, 30)])
+def test_trajectory_fp64_matches_oracle(move, iters):
+    """16^3 isotropic workload: with step 0.05 the constraint stays inactive
+    (sign steps); with step 0.02 Alg. 1 lowers V* at iteration 8, the update
+    turns infeasible and then the bisection becomes active."""
+    n = 16
+    wl = W.SMALL_16
+    rho0 = wl.rho0(np.float32)
+    ctx, otm = _make(n, 0, 1e-11, move=move)
+    ref = _oracle(n, rho0.astype(np.float64), move, wl.kappa_target)
+    try:
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        modes = set()
+        for it in range(iters):
+            info, st = otm.otm_step(ctx)
+            assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+            r = ref.step()
+            assert abs(info.g - r["g"]) <= 1e-8 * max(r["g"], 1e-12) + 1e-14, it
+            assert rel_fro(info.kappa, r["kappa"]) <= 1e-8, it
+            assert abs(info.vstar - r["vstar"]) <= 1e-9, it
+            modes.add("inactive" if r["lam"] == 0 else ("infeasible" if np.isinf(r["lam"]) else "active"))
+        diff = np.max(np.abs(_rho(ctx, otm, n) - ref.rho))
+        assert diff <= 1e-3, diff
+        if move == 0.02:
+            assert modes == {"inactive", "infeasible", "active"}
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_trajectory_fp32_and_mixed_against_oracle(precision):
+    """FP32 / mixed path on the same 16^3 workload, 20 iterations of
+    step 0.02: the density stays within 1e-3 of the oracle's."""
+    n = 16
+    wl = W.SMALL_16
+    rho0 = wl.rho0(np.float32)
+    ctx, otm = _make(n, precision, 1e-7 if precision == 1 else 1e-6, move=0.02)
+    ref = _oracle(n, rho0.astype(np.float64), 0.02, wl.kappa_target)
+    try:
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        for it in range(20):
+            info, st = otm.otm_step(ctx)
+            assert st in (otm.OTM_OK, otm.OTM_ENOCONV)
+            ref.step()
+        diff = np.max(np.abs(_rho(ctx, otm, n) - ref.rho))
+        assert diff <= 1e-3, diff
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("objective,kind", [(1, "fracmse"), (2, "l1")])
+def test_objective_variants(objective, kind):
+    n = 8
+    rho0 = W.initial_density(n, 0.4, 21).astype(np.float32)
+    target = W.TARGET_ANISOTROPIC
+    ctx, otm = _make(n, 0, 1e-11, move=0.02, target=target, objective=objective)
+    ref = _oracle(n, rho0.astype(np.float64), 0.02, target, objective=kind)
+    try:
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        for it in range(6):
+            info, st = otm.otm_step(ctx)
+            r = ref.step()
+            assert abs(info.g - r["g"]) <= 1e-8 * r["g"]
+        assert np.max(np.abs(_rho(ctx, otm, n) - ref.rho)) <= 1e-6
+    finally:
+        otm.otm_destroy(ctx)
+
+
+def test_fixed_volume_and_central_symmetry():
+    n = 8
+    rho0 = W.initial_density(n, 0.4, 22).astype(np.float32)
+    target = (0.3, 0.2, 0.1, 0.05, 0.01, 0.1)
+    ctx, otm = _make(n, 0, 1e-11, move=0.05, target=target, governor=0, fixed_volume=0.35, symmetry=1)
+    ref = _oracle(n, rho0.astype(np.float64), 0.05, target, governor=False, fixed_volume=0.35, symmetry=True)
+    try:
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        for it in range(6):
+            info, st = otm.otm_step(ctx)
+            r = ref.step()
+            assert abs(info.vstar - 0.35) < 1e-15
+        got = _rho(ctx, otm, n)
+        assert np.max(np.abs(got - ref.rho)) <= 1e-6
+        assert np.max(np.abs(got - got[::-1])) <= 1e-7     # point-symmetric
+        assert got.mean() <= 0.35 + 1e-6
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_checkpoint_resume_is_bitwise(precision):
+    n = 16
+    rho0 = W.SMALL_16.rho0(np.float32)
+    ctx, otm = _make(n, precision, 1e-6, move=0.02)
+    ctx2, _ = _make(n, precision, 1e-6, move=0.02)
+    try:
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        for _ in range(10):
+            otm.otm_step(ctx)
+        blob = otm.otm_get_state(ctx)
+        infos_a = [otm.otm_step(ctx)[0] for _ in range(5)]
+        otm.otm_set_state(ctx2, blob)
+        infos_b = [otm.otm_step(ctx2)[0] for _ in range(5)]
+        for a, b in zip(infos_a, infos_b):
+            assert a.g == b.g and list(a.kappa) == list(b.kappa) and a.vstar == b.vstar
+            assert a.iteration == b.iteration
+        assert np.array_equal(_rho(ctx, otm, n), _rho(ctx2, otm, n))
+        # a blob of another size is refused
+        ctx3, _ = _make(8, precision, 1e-6)
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        assert otm.lib.otm_set_state(ctx3, buf, len(blob)) == otm.OTM_ESTATE
+        otm.otm_destroy(ctx3)
+    finally:
+        otm.otm_destroy(ctx)
+        otm.otm_destroy(ctx2)
+
+
+def test_determinism():
+    n = 32
+    rho0 = W.initial_density(n, 0.3, 3).astype(np.float32)
+    outs = []
+    for _ in range(2):
+        ctx, otm = _make(n, 1, 1e-6, rmin=2.0, target=W.TARGET_ORTHOTROPIC)
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        infos, st = otm.otm_run(ctx, 4)
+        outs.append((_rho(ctx, otm, n), [i.g for i in infos], [list(i.cg_iters) for i in infos]))
+        otm.otm_destroy(ctx)
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1] and outs[0][2] == outs[1][2]
+
+
+def test_design_batch_matches_single_contexts():
+    otm = _otm()
+    designs = W.batch_designs(count=3, sizes=(8, 12, 16))
+    params, r0, ro, outs = [], [], [], []
+    arrays = []
+    for d in designs:
+        p = otm.otm_params_default(n=d.n, precision=1, kappa_target=d.kappa_target, volfrac=d.volfrac,
+                                   cg_tol=1e-6, cg_maxit=2000)
+        params.append(p)
+        a = d.rho0(np.float32)
+        o = np.empty(d.n ** 3, np.float32)
+        arrays += [a, o]
+        r0.append(a.ctypes.data)
+        ro.append(o.ctypes.data)
+        outs.append(o)
+    kaps, infos, st = otm.otm_design_batch(params, r0, 3, ro)
+    assert st == otm.OTM_OK
+    for d, p, o, kap in zip(designs, params, outs, kaps):
+        ctx = otm.otm_create_ex(p)
+        a = d.rho0(np.float32)
+        otm.otm_set_density(ctx, a.ctypes.data, 0)
+        infos1, _ = otm.otm_run(ctx, 3)
+        assert np.array_equal(_rho(ctx, otm, d.n), o.astype(np.float64))
+        assert list(infos1[-1].kappa) == kap
+        otm.otm_destroy(ctx)
+
+
+def test_homogenize_leaves_design_state_alone():
+    n = 8
+    ctx, otm = _make(n, 1, 1e-6)
+    try:
+        rho0 = W.initial_density(n, 0.4, 4).astype(np.float32)
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        other = W.initial_density(n, 0.6, 5).astype(np.float32)
+        kap_other, _, _ = otm.otm_homogenize(ctx, other.ctypes.data, 0)
+        assert np.array_equal(_rho(ctx, otm, n), rho0.astype(np.float64))
+        kap_cur, _, _ = otm.otm_homogenize(ctx, None, 0)
+        assert kap_cur[0] < kap_other[0]
+    finally:
+        otm.otm_destroy(ctx)

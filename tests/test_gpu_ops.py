@@ -1,0 +1,164 @@
+"""Kernel-level parity: each operator entry point of libotm against the FP64
+oracle on the same seeded inputs, in FP64 (to rounding) and FP32 (to a bound
+derived from the arithmetic)."""
+import numpy as np
+import pytest
+
+from oracle import design, fem
+import workloads as W
+from tests.gpu_util import dev, empty, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _otm():
+    from paper_2405_19991_gb300 import otm
+    return otm
+
+
+def _tdt(dtype):
+    import torch
+    return torch.float64 if dtype == 0 else torch.float32
+
+
+def _k(n, seed):
+    rho = W.random_density(n, seed)
+    return 1e-3 + rho ** 3 * (1 - 1e-3)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,rmin", [(16, 1.5), (13, 2.0), (10, 2.5), (6, 1.0)])
+def test_filter_simp(dtype, n, rmin):
+    otm = _otm()
+    rho = W.random_density(n, 1)
+    t = _tdt(dtype)
+    r_d, rf_d, k_d = dev(rho, t), empty(n ** 3, t), empty(n ** 3, t)
+    otm.otm_op_filter_simp(dtype, n, rmin, 3.0, 1.0, 1e-3, r_d, rf_d, k_d)
+    rho_in = host(r_d)       # the rounded input both sides see
+    rf = design.density_filter(n, rho_in, rmin)
+    k = design.simp(rf, 3.0, 1.0, 1e-3)
+    tol = 1e-13 if dtype == 0 else 2e-6
+    assert np.max(np.abs(host(rf_d) - rf)) <= tol
+    assert np.max(np.abs(host(k_d) - k)) <= tol
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n,rmin", [(12, 1.5), (9, 2.0), (8, 2.9)])
+def test_filter_transpose(dtype, n, rmin):
+    otm = _otm()
+    rng = np.random.default_rng(2)
+    s = rng.standard_normal(n ** 3)
+    t = _tdt(dtype)
+    s_d, o_d = dev(s, t), empty(n ** 3, t)
+    otm.otm_op_filter_transpose(dtype, n, rmin, s_d, o_d)
+    ref = design.density_filter_transpose(n, host(s_d), rmin)
+    tol = 1e-13 if dtype == 0 else 2e-6 * np.max(np.abs(s))
+    assert np.max(np.abs(host(o_d) - ref)) <= tol
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [4, 7, 16])
+def test_macro_load(dtype, n):
+    otm = _otm()
+    k = _k(n, 3)
+    t = _tdt(dtype)
+    k_d, f_d = dev(k, t), empty(3 * n ** 3, t)
+    otm.otm_op_macro_load(dtype, n, k_d, f_d)
+    ref = fem.macro_load(n, host(k_d)).ravel()
+    tol = 1e-14 if dtype == 0 else 1e-6
+    assert np.max(np.abs(host(f_d) - ref)) <= tol
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [4, 5, 8, 13, 16])
+def test_apply_K(dtype, n):
+    otm = _otm()
+    k = _k(n, 4)
+    u = W.random_field(n, 5)
+    t = _tdt(dtype)
+    k_d, u_d, o_d = dev(k, t), dev(u.ravel(), t), empty(3 * n ** 3, t)
+    otm.otm_op_apply_K(dtype, n, k_d, u_d, o_d)
+    ref = fem.apply_operator(n, host(k_d), host(u_d).reshape(3, -1)).ravel()
+    # FP32: about 40 rounded operations on terms bounded by 16/3 kmax umax
+    scale = np.max(k) * np.max(np.abs(u)) * 16.0 / 3.0
+    tol = 1e-13 * scale if dtype == 0 else 40 * 6e-8 * scale
+    assert np.max(np.abs(host(o_d) - ref)) <= tol
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [4, 8, 12])
+def test_gs_colour_pass(dtype, n):
+    otm = _otm()
+    k = _k(n, 6)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((3, n ** 3))
+    T = rng.standard_normal((3, n ** 3))
+    t = _tdt(dtype)
+    k_d, f_d, T_d = dev(k, t), dev(f.ravel(), t), dev(T.ravel(), t)
+    K = fem.assemble(n, host(k_d))
+    Tref = host(T_d).reshape(3, -1)
+    fh = host(f_d).reshape(3, -1)
+    for colour in (0, 3, 5, 6, 1):
+        otm.otm_op_gs_colour(dtype, n, k_d, f_d, T_d, colour)
+        nodes = fem.colour_nodes(n, colour)
+        for i in range(3):
+            Tref[i] = fem.gauss_seidel_pass(K, fh[i], Tref[i], nodes)
+        got = host(T_d).reshape(3, -1)
+        tol = 1e-11 if dtype == 0 else 2e-4 * max(1.0, np.max(np.abs(Tref)))
+        assert np.max(np.abs(got - Tref)) <= tol, colour
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [6, 16])
+def test_kappa_and_sensitivity(dtype, n):
+    otm = _otm()
+    rho_f = W.random_density(n, 8, 0.05, 0.95)
+    k = design.simp(rho_f, 3.0, 1.0, 1e-3)
+    chi = 0.3 * W.random_field(n, 9)
+    w = np.array([0.2, -0.1, 0.05, 0.3, -0.2, 0.1])
+    t = _tdt(dtype)
+    k_d, rf_d, chi_d, s_d = dev(k, t), dev(rho_f, t), dev(chi.ravel(), t), empty(n ** 3, t)
+    kap = otm.otm_op_kappa_sens(dtype, n, 3.0, 1.0, 1e-3, k_d, rf_d, chi_d, w, s_d)
+    kh, rfh, chih = host(k_d), host(rf_d), host(chi_d).reshape(3, -1)
+    E = fem.element_energies(n, chih)
+    kref = fem.kappa_from_energies(kh, E)
+    tol = 1e-12 if dtype == 0 else 1e-6
+    assert np.max(np.abs(np.array(kap) - kref)) <= tol * np.max(np.abs(kref))
+    s_ref, _ = design.sensitivity(n, rfh, E, w, 3.0, 1.0, 1e-3, 1.5)
+    stol = 1e-12 if dtype == 0 else 2e-5
+    assert np.max(np.abs(host(s_d) - s_ref)) <= stol * np.max(np.abs(s_ref))
+
+
+def _oc_case(seed, N, active):
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.0, 1.0, N)
+    s = rng.standard_normal(N) * 10.0 ** rng.uniform(-3, 0, N)
+    if active:
+        s = -np.abs(s) * (rng.uniform(size=N) < 0.8) + np.abs(s) * 0.01
+    return rho, s
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("case", ["active", "mixed", "inactive", "infeasible"])
+@pytest.mark.parametrize("n", [6, 16])
+def test_oc_update(dtype, case, n):
+    otm = _otm()
+    N = n ** 3
+    rho, s = _oc_case(11 + n, N, case in ("active", "infeasible"))
+    vstar = {"active": rho.mean() - 0.01, "mixed": rho.mean() - 0.004, "inactive": 1.0,
+             "infeasible": 0.0}[case]
+    t = _tdt(dtype)
+    r_d, s_d, o_d = dev(rho, t), dev(s, t), empty(N, t)
+    lam = otm.otm_op_oc_update(dtype, n, vstar, 0.05, 0.5, 1e-3, r_d, s_d, o_d)
+    ref, lam_ref = design.oc_update(host(r_d), host(s_d), vstar, 0.05, 0.5, 1e-3)
+    got = host(o_d)
+    tol = 1e-9 if dtype == 0 else 2e-6
+    assert np.max(np.abs(got - ref)) <= tol
+    if case == "inactive":
+        assert lam == 0.0 and lam_ref == 0.0
+    elif case == "infeasible":
+        assert np.isinf(lam) and np.isinf(lam_ref)
+    else:
+        assert got.mean() <= vstar + 1e-6
+        if np.isfinite(lam_ref) and lam_ref > 0:
+            assert abs(lam - lam_ref) <= 1e-4 * lam_ref

@@ -1,0 +1,150 @@
+"""Homogenization parity: otm_homogenize (filter, SIMP, macro loads, MG-PCG,
+tensor) against the FP64 oracle, at sizes the oracle solves in seconds, and
+at 128^3 on closed forms and sampled outputs."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import design, fem
+import workloads as W
+from tests.gpu_util import dev, empty, host, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-9, 1: 1e-6, 2: 1e-4}     # relative Frobenius error of kappa per precision
+
+
+def _otm():
+    from paper_2405_19991_gb300 import otm
+    return otm
+
+
+def _ctx(n, precision, tol, rmin=1.5, target=W.TARGET_ISOTROPIC, **kw):
+    otm = _otm()
+    p = otm.otm_params_default(n=n, precision=precision, cg_tol=tol, rmin=rmin,
+                               kappa_target=target, cg_maxit=2000, **kw)
+    return otm.otm_create_ex(p), otm
+
+
+def _homogenize_host(ctx, otm, rho):
+    arr = np.ascontiguousarray(rho, dtype=np.float32)
+    kap, info, st = otm.otm_homogenize(ctx, arr.ctypes.data, 0)
+    return np.array(kap), info, st
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+@pytest.mark.parametrize("n,rmin", [(4, 1.5), (6, 2.0), (8, 1.5), (12, 2.0), (16, 1.5), (20, 2.0)])
+def test_homogenize_matches_oracle(precision, n, rmin):
+    ctx, otm = _ctx(n, precision, 1e-10 if precision == 0 else 1e-6, rmin=rmin)
+    try:
+        rho = W.initial_density(n, 0.35, 100 + n).astype(np.float32)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        rf = design.density_filter(n, rho.astype(np.float64), rmin)
+        k = design.simp(rf, 3.0, 1.0, 1e-3)
+        ref = fem.homogenize(n, k, tol=1e-12)
+        err = rel_fro(kap, ref["kappa"])
+        assert err <= TOL[precision], (err, kap, ref["kappa"])
+        assert max(info.resid) <= (1e-10 if precision == 0 else 1e-6) * 1.0001
+        # the corrector fields agree up to the solver tolerance (zero mean)
+        N = n ** 3
+        chi = np.empty(3 * N, dtype=np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * N, 0)
+        chi = chi.reshape(3, N).astype(np.float64)
+        chi -= chi.mean(axis=1, keepdims=True)
+        scale = np.max(np.abs(ref["chi"])) + 1e-30
+        ctol = {0: 1e-6, 1: 2e-3, 2: 2e-2}[precision]
+        assert np.max(np.abs(chi - ref["chi"])) <= ctol * max(scale, 1e-3)
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_energy_error_is_one_sided(precision):
+    """kappa from an inexact solution lies above the exact one (Loewner
+    order), up to the rounding of the tensor sums."""
+    n = 16
+    ctx, otm = _ctx(n, precision, 1e-4)
+    try:
+        rho = W.initial_density(n, 0.3, 5).astype(np.float32)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        rf = design.density_filter(n, rho.astype(np.float64), 1.5)
+        ref = fem.homogenize(n, design.simp(rf, 3.0, 1.0, 1e-3), tol=1e-12)
+        d = fem.kappa_matrix(kap) - fem.kappa_matrix(ref["kappa"])
+        assert np.min(np.linalg.eigvalsh(d)) >= -1e-6 * np.max(np.abs(ref["kappa"]))
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_128_solid_uniform_and_laminate(precision):
+    n = 128
+    ctx, otm = _ctx(n, precision, 1e-6, rmin=1.0)   # rmin = 1: the filter is the identity
+    try:
+        kap, info, st = _homogenize_host(ctx, otm, np.ones(n ** 3))
+        assert st == otm.OTM_OK
+        assert np.max(np.abs(kap - np.array([1, 1, 1, 0, 0, 0]))) < 1e-6
+        kap, info, st = _homogenize_host(ctx, otm, np.full(n ** 3, 0.6))
+        kc = 1e-3 + 0.6 ** 3 * (1 - 1e-3)
+        assert np.max(np.abs(kap - np.array([kc, kc, kc, 0, 0, 0]))) < 1e-6 * kc * 10
+        # z-laminate: rho depends on the layer only
+        rng = np.random.default_rng(3)
+        layers = rng.uniform(0.1, 1.0, n).astype(np.float32)
+        rho = np.repeat(layers, n * n)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        kl = 1e-3 + layers.astype(np.float64) ** 3 * (1 - 1e-3)
+        arith, harm = kl.mean(), 1.0 / (1.0 / kl).mean()
+        rtol = 1e-5 if precision == 1 else 1e-4
+        assert abs(kap[0] - arith) <= rtol * arith
+        assert abs(kap[1] - arith) <= rtol * arith
+        assert abs(kap[2] - harm) <= rtol * harm + 1e-6 * arith
+        assert np.max(np.abs(kap[3:])) <= 1e-6
+    finally:
+        otm.otm_destroy(ctx)
+
+
+def test_128_sampled_residual_tensor_and_sensitivity():
+    """The benchmark configuration (128^3, r = 2, FP32, cg_tol 1e-6): the
+    oracle recomputes, from the GPU's own k and corrector fields, the
+    residual at sampled nodes, the full tensor sum, and the element
+    sensitivities at sampled elements."""
+    otm = _otm()
+    n = 128
+    wl = W.ORTHO_128
+    p = otm.otm_params_default(n=n, precision=1, cg_tol=1e-6, rmin=wl.rmin, kappa_target=wl.kappa_target)
+    ctx = otm.otm_create_ex(p)
+    try:
+        rho = wl.rho0(np.float32)
+        otm.otm_set_density(ctx, rho.ctypes.data, 0)
+        info, st = otm.otm_step(ctx)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        N = n ** 3
+        k = np.empty(N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_K, k.ctypes.data, N, 0)
+        chi = np.empty(3 * N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * N, 0)
+        rf = np.empty(N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_RHO_FILT, rf.ctypes.data, N, 0)
+        k = k.astype(np.float64)
+        chi = chi.reshape(3, N).astype(np.float64)
+        # filter + SIMP against the oracle on the same input
+        rf_ref = design.density_filter(n, rho.astype(np.float64), wl.rmin)
+        assert np.max(np.abs(rf - rf_ref)) < 2e-6
+        # residual at sampled nodes: |r_v| <= ||r||_2 <= tol ||f||_2
+        f = fem.macro_load(n, k)
+        rng = np.random.default_rng(0)
+        nodes = rng.choice(N, 300, replace=False)
+        Ku = fem.apply_operator_at(n, k, chi, nodes)
+        r = f[:, nodes] - Ku
+        for i in range(3):
+            nf = np.linalg.norm(f[i] - f[i].mean())
+            assert np.max(np.abs(r[i])) <= 1.5e-6 * nf
+        # tensor from the GPU corrector, summed in FP64 by the oracle
+        E = fem.element_energies(n, chi)
+        kref = fem.kappa_from_energies(k, E)
+        assert rel_fro(info.kappa, kref) <= 1e-6
+        assert max(info.resid) <= 1e-6 * 1.0001
+    finally:
+        otm.otm_destroy(ctx)
