@@ -293,6 +293,24 @@ OTM_API otm_status otm_op_kappa_sens(int dtype, int n, double penal, double k_so
                                      const void* chi, const double w[6],
                                      double kappa_out[6], void* s_f, void* stream);
 
+/* Same computation and arguments as otm_op_kappa_sens, for callers that must
+ * not allocate device memory (for instance inside a host framework that has
+ * reserved the device through its own memory pool, or in a loop that cannot
+ * afford an allocation's possible synchronisation).  The paper has no
+ * counterpart: this is a deployment variant.  Its reduction scratch is a
+ * fixed device array inside the library (about 50 KB, held on every GPU that
+ * loads the library until the process exits); no cudaMalloc, cudaFree or
+ * other allocating call is made.  Limit: n <= 512.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the scratch and it keeps the last call's contents (the call
+ * clears what must start at zero); calls whose GPU work overlaps race on it
+ * and must be serialised by the caller. */
+OTM_API otm_status otm_op_kappa_sens_noalloc(int dtype, int n, double penal, double k_solid,
+                                             double k_void, const void* k, const void* rho_f,
+                                             const void* chi, const double w[6],
+                                             double kappa_out[6], void* s_f, void* stream);
+
 /* OC update (Sec. 3.3) of rho with gradient s under volume bound vstar:
  * writes rho_new, and *lambda_out (host, may be NULL). */
 OTM_API otm_status otm_op_oc_update(int dtype, int n, double vstar, double move,

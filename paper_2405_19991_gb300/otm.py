@@ -117,6 +117,7 @@ def _load():
         "otm_op_gs_colour": [i, i, vp, vp, vp, i, vp],
         "otm_op_kappa_sens": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_op_oc_update": [i, i, d, d, d, d, vp, vp, vp, P(C.c_double), vp],
+        "otm_op_kappa_sens_noalloc": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -136,7 +137,7 @@ EXPORTED = [
     "otm_run", "otm_design_batch", "otm_get_state", "otm_set_state", "otm_last_error",
     "otm_governor_init", "otm_governor_update", "otm_op_filter_simp", "otm_op_filter_transpose",
     "otm_op_macro_load", "otm_op_apply_K", "otm_op_gs_colour", "otm_op_kappa_sens",
-    "otm_op_oc_update",
+    "otm_op_oc_update", "otm_op_kappa_sens_noalloc",
 ]
 
 
@@ -287,6 +288,15 @@ def otm_op_kappa_sens(dtype, n, penal, k_solid, k_void, k, rho_f, chi, w, s_f, s
     warr = (C.c_double * 6)(*[float(v) for v in w]) if w is not None else None
     check(lib.otm_op_kappa_sens(dtype, n, penal, k_solid, k_void, _p(k), _p(rho_f), _p(chi), warr, kap,
                                 _p(s_f), stream))
+    return list(kap)
+
+
+def otm_op_kappa_sens_noalloc(dtype, n, penal, k_solid, k_void, k, rho_f, chi, w, s_f, stream=None):
+    """otm_op_kappa_sens without device allocations (fixed scratch inside the library)."""
+    kap = (C.c_double * 6)()
+    warr = (C.c_double * 6)(*[float(v) for v in w]) if w is not None else None
+    check(lib.otm_op_kappa_sens_noalloc(dtype, n, penal, k_solid, k_void, _p(k), _p(rho_f), _p(chi), warr, kap,
+                                        _p(s_f), stream))
     return list(kap)
 
 
