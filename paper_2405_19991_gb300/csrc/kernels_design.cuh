@@ -41,35 +41,44 @@ struct FinFilter {
 };
 
 // out_e = sum_o w(o) in_{e + sgn*o} / sum w.  sgn = -1 is the transpose
-// (scatter of each element to the neighbours it gathered from).
-template <class R, bool SIMP>
+// (scatter of each element to the neighbours it gathered from).  RR is the
+// offset range (|o_d| <= RR), fixed at compile time so the loops unroll and
+// the weights stay in registers.
+template <class R, bool SIMP, int RR>
 __global__ void __launch_bounds__(256)
 k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ out, R* __restrict__ kout,
          SimpP sp, RedBuf rb, FinFilter fin) {
+    pdl_enter();
     using C = typename St<R>::C;
-    const size_t N = (size_t)n * n * n;
     C w[13];
 #pragma unroll
     for (int i = 0; i < 13; ++i) w[i] = (C)fw.w[i];
     const C inv = (C)fw.inv_wsum;
     Acc<C> a_rho, a_rhop;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row_, n * n) {
+    const int y = row_ % n, z = row_ / n;
+    size_t zo[2 * RR + 1], yo[2 * RR + 1];
+#pragma unroll
+    for (int d = -RR; d <= RR; ++d) {
+        zo[d + RR] = (size_t)wrapd(z, sgn * d, n) * n * n;
+        yo[d + RR] = (size_t)wrapd(y, sgn * d, n) * n;
+    }
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row_ * n + x;
+        int xo[2 * RR + 1];
+#pragma unroll
+        for (int d = -RR; d <= RR; ++d) xo[d + RR] = wrapd(x, sgn * d, n);
         C acc = 0;
-        for (int dz = -fw.R; dz <= fw.R; ++dz) {
-            const size_t zo = (size_t)wrapd(z, sgn * dz, n) * n * n;
-            for (int dy = -fw.R; dy <= fw.R; ++dy) {
-                const size_t yo = (size_t)wrapd(y, sgn * dy, n) * n;
-                for (int dx = -fw.R; dx <= fw.R; ++dx) {
+#pragma unroll
+        for (int dz = -RR; dz <= RR; ++dz)
+#pragma unroll
+            for (int dy = -RR; dy <= RR; ++dy)
+#pragma unroll
+                for (int dx = -RR; dx <= RR; ++dx) {
                     const int d2 = dx * dx + dy * dy + dz * dz;
                     if (d2 > 12) continue;
-                    const C ww = w[d2];
-                    if (ww == C(0)) continue;
-                    acc += ww * in[(size_t)wrapd(x, sgn * dx, n) + yo + zo];
+                    acc += w[d2] * (C)in[(size_t)xo[dx + RR] + yo[dy + RR] + zo[dz + RR]];
                 }
-            }
-        }
         const C rf = acc * inv;
         out[v] = rf;
         if (SIMP) {
@@ -79,13 +88,23 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
             a_rhop.add(rp);
         }
     }
+    }
     if (SIMP) {
         __shared__ double res[2];
         double vals[2] = {a_rho.value(), a_rhop.value()};
         if (grid_reduce<2>(vals, rb, res)) {
-            if (threadIdx.x == 0) fin(res);
+            if (is_thread0()) fin(res);
         }
     }
+}
+
+// Dispatch on the filter's offset range.
+template <class R, bool SIMP>
+inline cudaError_t launch_filter(RowLaunch L, cudaStream_t st, int n, const FilterW& fw, int sgn, const R* in, R* out,
+                                 R* kout, const SimpP& sp, RedBuf rb, FinFilter fin) {
+    if (fw.R <= 0) return launch_pdl(k_filter<R, SIMP, 0>, L.grid, L.block, st, n, fw, sgn, in, out, kout, sp, rb, fin);
+    if (fw.R == 1) return launch_pdl(k_filter<R, SIMP, 1>, L.grid, L.block, st, n, fw, sgn, in, out, kout, sp, rb, fin);
+    return launch_pdl(k_filter<R, SIMP, 2>, L.grid, L.block, st, n, fw, sgn, in, out, kout, sp, rb, fin);
 }
 
 // Element energies E_c = d^i . K0 d^j, d^i_l = t^i_l - chi^i(corner l) with
@@ -162,24 +181,27 @@ struct FinKappa {
 template <class R>
 __global__ void __launch_bounds__(256)
 k_kappa(int n, const R* __restrict__ k, const R* __restrict__ chi, RedBuf rb, FinKappa fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     const size_t N = (size_t)n * n * n;
     Acc<C> acc[6];
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(e % n), y = (int)((e / n) % n), z = (int)(e / ((size_t)n * n));
+    OTM_FOR_ROWS(row_, n * n) {
+    const int y = row_ % n, z = row_ / n;
+    OTM_FOR_X(x, n) {
+        const size_t e = (size_t)row_ * n + x;
         C E[6];
         element_energies<R, C>(n, N, x, y, z, chi, E);
         const C ke = k[e];
 #pragma unroll
         for (int c = 0; c < 6; ++c) acc[c].add_prod(ke, E[c]);
     }
+    }
     __shared__ double res[6];
     double vals[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) vals[c] = acc[c].value();
     if (grid_reduce<6>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
@@ -188,21 +210,24 @@ template <class R>
 __global__ void __launch_bounds__(256)
 k_sens(int n, const R* __restrict__ rho_f, const R* __restrict__ chi, const DesignScalars* __restrict__ ds,
        SimpP sp, R* __restrict__ s_f) {
+    pdl_enter();
     using C = typename St<R>::C;
     const size_t N = (size_t)n * n * n;
     C w[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) w[c] = (C)ds->w[c];
     const C scale = (C)((sp.k_solid - sp.k_void) / (double)N);
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(e % n), y = (int)((e / n) % n), z = (int)(e / ((size_t)n * n));
+    OTM_FOR_ROWS(row_, n * n) {
+    const int y = row_ % n, z = row_ / n;
+    OTM_FOR_X(x, n) {
+        const size_t e = (size_t)row_ * n + x;
         C E[6];
         element_energies<R, C>(n, N, x, y, z, chi, E);
         C a = 0;
 #pragma unroll
         for (int c = 0; c < 6; ++c) a += w[c] * E[c];
         s_f[e] = a * simp_dpow((C)rho_f[e], sp) * scale;
+    }
     }
 }
 
@@ -211,6 +236,7 @@ k_sens(int n, const R* __restrict__ rho_f, const R* __restrict__ chi, const Desi
 template <class R>
 __global__ void __launch_bounds__(256)
 k_symmetrize(size_t N, R* __restrict__ rho, R* __restrict__ s) {
+    pdl_enter();
     using C = typename St<R>::C;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N / 2;
          e += (size_t)gridDim.x * blockDim.x) {
@@ -284,6 +310,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
 k_oc_prep(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, DesignScalars* ds,
           RedBuf rb, FinOcPrep fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     Acc<C> vmin, vmax;
     double mumin = 1e300, mumax = 0.0;
@@ -294,7 +321,8 @@ k_oc_prep(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, 
         vmin.add(lo);
         if (c > C(0)) {
             vmax.add(hi);
-            const double a = (double)lo / (double)c, b = (double)hi / (double)c;
+            const C ic = C(1) / c;
+            const double a = (double)(lo * ic), b = (double)(hi * ic);
             mumin = a < mumin ? a : mumin;
             mumax = b > mumax ? b : mumax;
         } else {
@@ -316,7 +344,7 @@ k_oc_prep(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, 
     __shared__ double res[2];
     double vals[2] = {vmin.value(), vmax.value()};
     if (grid_reduce<2>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
@@ -365,6 +393,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
 k_oc_search(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, DesignScalars* ds,
             int linear, RedBuf rb, FinOcSearch fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     if (ds->oc_mode != 0) return;   // uniform across the grid: no reduction needed
     __shared__ C cand[kOcCand];
@@ -389,7 +418,7 @@ k_oc_search(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op
 #pragma unroll
     for (int j = 0; j < kOcCand; ++j) vals[j] = (double)sum[j];
     if (grid_reduce<kOcCand>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
@@ -397,6 +426,7 @@ template <class R>
 __global__ void __launch_bounds__(256)
 k_oc_apply(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op,
            const DesignScalars* __restrict__ ds, R* __restrict__ rho_new) {
+    pdl_enter();
     using C = typename St<R>::C;
     const int mode = ds->oc_mode;
     const C mu = (C)ds->mu_star;
@@ -417,6 +447,7 @@ k_oc_apply(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op,
 
 // One thread: Alg. 1 (or the fixed bound), then reset the OC min/max slots.
 static __global__ void k_governor(DesignScalars* ds, double invN, int use_fixed, double fixed_vstar) {
+    pdl_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (use_fixed) {
         ds->vstar = fixed_vstar;

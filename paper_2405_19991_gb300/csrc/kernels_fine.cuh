@@ -257,6 +257,7 @@ struct FinInit {
         }
         ps->breakdown = 0;
         ps->nactive = na;
+        ps->first = 1;
     }
 };
 
@@ -279,14 +280,18 @@ struct FinResid {
             na += ps->active[i];
         }
         ps->nactive = na;
+        ps->total += 1;
     }
 };
 
 // gamma_new = r . z; beta = (gamma_new - [flexible] r.z_old) / gamma_old.
+// The first beta after a pass's residual is 0 (p = z).
 struct FinBeta {
     PcgScalars* ps;
-    int first;
     __device__ void operator()(const double* s) const {
+        const int first = ps->first;
+        ps->pfirst = first;
+        ps->first = 0;
         for (int i = 0; i < 3; ++i) {
             double b = 0.0;
             if (!first && ps->active[i] && ps->gamma[i] != 0.0) {
@@ -311,14 +316,14 @@ template <int MODE, bool DOT, class KT, class UT, class FT, class OT, class Fin,
 __global__ void __launch_bounds__(256)
 k_stencil_apply(int n, const KT* __restrict__ k, const UT* __restrict__ u, const FT* __restrict__ f,
                 OT* __restrict__ out, RedBuf rb, Fin fin) {
+    pdl_enter();
     using C = CT;
     const size_t N = (size_t)n * n * n;
     Acc<C> acc[6];
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n);
-        const int y = (int)((v / n) % n);
-        const int z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row, n * n) {
+    const int y = row % n, z = row / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row * n + x;
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<KT, C>(k, g, kk);
@@ -342,13 +347,14 @@ k_stencil_apply(int n, const KT* __restrict__ k, const UT* __restrict__ u, const
             }
         }
     }
+    }
     if (DOT) {
         __shared__ double res[6];
         double vals[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
         if (grid_reduce<6>(vals, rb, res)) {
-            if (threadIdx.x == 0) fin(res);
+            if (is_thread0()) fin(res);
         }
     }
 }
@@ -359,12 +365,14 @@ template <class R, class Fin>
 __global__ void __launch_bounds__(256)
 k_residual_x2(int n, const R* __restrict__ k, const R* __restrict__ xh, const R* __restrict__ xl,
               const R* __restrict__ f, R* __restrict__ r, RedBuf rb, Fin fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     const size_t N = (size_t)n * n * n;
     Acc<C> acc[6];
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row, n * n) {
+    const int y = row % n, z = row / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row * n + x;
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<R, C>(k, g, kk);
@@ -378,12 +386,13 @@ k_residual_x2(int n, const R* __restrict__ k, const R* __restrict__ xh, const R*
             acc[3 + i].add_prod(fv, fv);
         }
     }
+    }
     __shared__ double res[6];
     double vals[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
     if (grid_reduce<6>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
@@ -405,12 +414,14 @@ template <class R>
 __global__ void __launch_bounds__(256)
 k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const R* __restrict__ xl,
                 const R* __restrict__ f, RedBuf rb, FinTrue fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     const size_t N = (size_t)n * n * n;
     Acc<C> acc[6];
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row, n * n) {
+    const int y = row % n, z = row / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row * n + x;
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<R, C>(k, g, kk);
@@ -428,12 +439,13 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
             acc[3 + i].add_prod(fv, fv);
         }
     }
+    }
     __shared__ double res[6];
     double vals[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
     if (grid_reduce<6>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
@@ -445,19 +457,16 @@ template <bool ZERO, class KT, class FT, class TT>
 __global__ void __launch_bounds__(256)
 k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __restrict__ f,
           TT* __restrict__ T) {
+    pdl_enter();
     using C = typename St<TT>::C;
     const size_t N = (size_t)n * n * n;
     const int h = n >> 1;
     const int nx = xpar < 0 ? n : h;
-    const size_t M = (size_t)nx * h * h;
     const int yo = group & 1, zo = group >> 1;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < M;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int xi = (int)(t % nx);
-        const int yy = (int)((t / nx) % h);
-        const int zz = (int)(t / ((size_t)nx * h));
+    OTM_FOR_ROWS(grow, h * h) {
+    const int y = 2 * (grow % h) + yo, z = 2 * (grow / h) + zo;
+    OTM_FOR_X(xi, nx) {
         const int x = xpar < 0 ? xi : 2 * xi + xpar;
-        const int y = 2 * yy + yo, z = 2 * zz + zo;
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<KT, C>(k, g, kk);
@@ -478,6 +487,7 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
             }
         }
     }
+    }
 }
 
 // enforceMacroLoad (Sec. 2.4).  The template f0 = K0 T0 with T0[l][i] = i-th
@@ -488,13 +498,13 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
 template <class KT, class OT>
 __global__ void __launch_bounds__(256)
 k_macro_load(int n, const KT* __restrict__ k, OT* __restrict__ f) {
+    pdl_enter();
     using C = typename St<OT>::C;
     const size_t N = (size_t)n * n * n;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n);
-        const int y = (int)((v / n) % n);
-        const int z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row, n * n) {
+    const int y = row % n, z = row / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row * n + x;
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<KT, C>(k, g, kk);
@@ -514,6 +524,7 @@ k_macro_load(int n, const KT* __restrict__ k, OT* __restrict__ f) {
         St<OT>::st(f + N, v, C(0.25) * fy);
         St<OT>::st(f + 2 * N, v, C(0.25) * fz);
     }
+    }
 }
 
 // The periodic operator annihilates constants, so K x = f is solvable only
@@ -530,6 +541,7 @@ struct FinMean {
 template <class R>
 __global__ void __launch_bounds__(256)
 k_sum3(size_t N, const R* __restrict__ f, RedBuf rb, FinMean fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     Acc<C> acc[3];
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
@@ -542,13 +554,14 @@ k_sum3(size_t N, const R* __restrict__ f, RedBuf rb, FinMean fin) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
     if (grid_reduce<3>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256)
 k_sub_mean(size_t N, R* __restrict__ f, const PcgScalars* __restrict__ ps) {
+    pdl_enter();
     using C = typename St<R>::C;
     const C m0 = (C)ps->fmean[0], m1 = (C)ps->fmean[1], m2 = (C)ps->fmean[2];
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
@@ -562,75 +575,88 @@ k_sub_mean(size_t N, R* __restrict__ f, const PcgScalars* __restrict__ ps) {
 // Restriction R = P^T of the trilinear prolongation: coarse node I gathers
 // the fine nodes 2I + d, d in {-1,0,1}^3, with weight prod (1 - |d|/2).
 template <class IT, class OT>
-__global__ void __launch_bounds__(256)
-k_restrict(int nc, const IT* __restrict__ rf, OT* __restrict__ fc) {
+__device__ __forceinline__ void restrict_node(int nc, int X, int Y, int Z, const IT* __restrict__ rf,
+                                              OT* __restrict__ fc) {
     using C = typename St<OT>::C;
     const int nf = 2 * nc;
     const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
-    for (size_t I = (size_t)blockIdx.x * blockDim.x + threadIdx.x; I < Nc;
-         I += (size_t)gridDim.x * blockDim.x) {
-        const int X = (int)(I % nc), Y = (int)((I / nc) % nc), Z = (int)(I / ((size_t)nc * nc));
-        int xs[3], ys[3], zs[3];
+    const size_t I = (size_t)X + (size_t)nc * (Y + (size_t)nc * Z);
+    int xs[3], ys[3], zs[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xs[d] = wrapd(2 * X, d - 1, nf);
-            ys[d] = wrapd(2 * Y, d - 1, nf) * nf;
-            zs[d] = wrapd(2 * Z, d - 1, nf) * nf * nf;
-        }
-        const C w1[3] = {C(0.5), C(1), C(0.5)};
+    for (int d = 0; d < 3; ++d) {
+        xs[d] = wrapd(2 * X, d - 1, nf);
+        ys[d] = wrapd(2 * Y, d - 1, nf) * nf;
+        zs[d] = wrapd(2 * Z, d - 1, nf) * nf * nf;
+    }
+    const C w1[3] = {C(0.5), C(1), C(0.5)};
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const IT* r = rf + (size_t)i * Nf;
-            C acc = 0;
+    for (int i = 0; i < 3; ++i) {
+        const IT* r = rf + (size_t)i * Nf;
+        C acc = 0;
 #pragma unroll
-            for (int dz = 0; dz < 3; ++dz) {
-                C az = 0;
+        for (int dz = 0; dz < 3; ++dz) {
+            C az = 0;
 #pragma unroll
-                for (int dy = 0; dy < 3; ++dy) {
-                    C ay = 0;
+            for (int dy = 0; dy < 3; ++dy) {
+                C ay = 0;
 #pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-                        ay += w1[dx] * St<IT>::ld(r, (size_t)(xs[dx] + ys[dy] + zs[dz]));
-                    az += w1[dy] * ay;
-                }
-                acc += w1[dz] * az;
+                for (int dx = 0; dx < 3; ++dx) ay += w1[dx] * St<IT>::ld(r, (size_t)(xs[dx] + ys[dy] + zs[dz]));
+                az += w1[dy] * ay;
             }
-            St<OT>::st(fc + (size_t)i * Nc, I, acc);
+            acc += w1[dz] * az;
         }
+        St<OT>::st(fc + (size_t)i * Nc, I, acc);
+    }
+}
+
+template <class IT, class OT>
+__global__ void __launch_bounds__(256)
+k_restrict(int nc, const IT* __restrict__ rf, OT* __restrict__ fc) {
+    pdl_enter();
+    OTM_FOR_ROWS(row, nc * nc) {
+        const int Y = row % nc, Z = row / nc;
+        OTM_FOR_X(X, nc) restrict_node<IT, OT>(nc, X, Y, Z, rf, fc);
     }
 }
 
 // Prolongation and correction: T_v += sum_I P[v, I] Tc_I (trilinear).
 template <class CT, class TT>
-__global__ void __launch_bounds__(256)
-k_prolong_add(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
+__device__ __forceinline__ void prolong_node(int nf, int x, int y, int z, const CT* __restrict__ Tc,
+                                             TT* __restrict__ T) {
     using C = typename St<TT>::C;
     const int nc = nf / 2;
     const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < Nf;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
-        int xi[2], yi[2], zi[2];
-        C wx[2], wy[2], wz[2];
-        int cx, cy, cz;
-        if (x & 1) { xi[0] = x >> 1; xi[1] = wrapp(x >> 1, nc); wx[0] = wx[1] = C(0.5); cx = 2; }
-        else { xi[0] = xi[1] = x >> 1; wx[0] = C(1); wx[1] = 0; cx = 1; }
-        if (y & 1) { yi[0] = y >> 1; yi[1] = wrapp(y >> 1, nc); wy[0] = wy[1] = C(0.5); cy = 2; }
-        else { yi[0] = yi[1] = y >> 1; wy[0] = C(1); wy[1] = 0; cy = 1; }
-        if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = C(0.5); cz = 2; }
-        else { zi[0] = zi[1] = z >> 1; wz[0] = C(1); wz[1] = 0; cz = 1; }
+    const size_t v = (size_t)x + (size_t)nf * (y + (size_t)nf * z);
+    int xi[2], yi[2], zi[2];
+    C wx[2], wy[2], wz[2];
+    int cx, cy, cz;
+    if (x & 1) { xi[0] = x >> 1; xi[1] = wrapp(x >> 1, nc); wx[0] = wx[1] = C(0.5); cx = 2; }
+    else { xi[0] = xi[1] = x >> 1; wx[0] = C(1); wx[1] = 0; cx = 1; }
+    if (y & 1) { yi[0] = y >> 1; yi[1] = wrapp(y >> 1, nc); wy[0] = wy[1] = C(0.5); cy = 2; }
+    else { yi[0] = yi[1] = y >> 1; wy[0] = C(1); wy[1] = 0; cy = 1; }
+    if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = C(0.5); cz = 2; }
+    else { zi[0] = zi[1] = z >> 1; wz[0] = C(1); wz[1] = 0; cz = 1; }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const CT* tc = Tc + (size_t)i * Nc;
-            C acc = 0;
-            for (int c = 0; c < cz; ++c)
-                for (int b = 0; b < cy; ++b)
-                    for (int a = 0; a < cx; ++a)
-                        acc += wz[c] * wy[b] * wx[a] *
-                               St<CT>::ld(tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]));
-            TT* t = T + (size_t)i * Nf;
-            St<TT>::st(t, v, St<TT>::ld(t, v) + acc);
-        }
+    for (int i = 0; i < 3; ++i) {
+        const CT* tc = Tc + (size_t)i * Nc;
+        C acc = 0;
+        for (int c = 0; c < cz; ++c)
+            for (int b = 0; b < cy; ++b)
+                for (int a = 0; a < cx; ++a)
+                    acc += wz[c] * wy[b] * wx[a] *
+                           St<CT>::ld(tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]));
+        TT* t = T + (size_t)i * Nf;
+        St<TT>::st(t, v, St<TT>::ld(t, v) + acc);
+    }
+}
+
+template <class CT, class TT>
+__global__ void __launch_bounds__(256)
+k_prolong_add(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
+    pdl_enter();
+    OTM_FOR_ROWS(row, nf * nf) {
+        const int y = row % nf, z = row / nf;
+        OTM_FOR_X(x, nf) prolong_node<CT, TT>(nf, x, y, z, Tc, T);
     }
 }
 
@@ -642,6 +668,7 @@ __global__ void __launch_bounds__(256)
 k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, const R* __restrict__ p,
             const R* __restrict__ q, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps,
             RedBuf rb, FinResid fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     const C a0 = (C)ps->alpha[0], a1 = (C)ps->alpha[1], a2 = (C)ps->alpha[2];
     const bool flex = ps->flexible != 0;
@@ -677,7 +704,124 @@ k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, 
 #pragma unroll
     for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
     if (grid_reduce<6>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
+    }
+}
+
+// Vectorised forms of the three streaming PCG kernels: each thread handles
+// four consecutive nodes per load case (N a multiple of 4).  Same arithmetic
+// per element as the scalar forms.
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_update_xr4(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, const R* __restrict__ p,
+             const R* __restrict__ q, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps,
+             RedBuf rb, FinResid fin) {
+    pdl_enter();
+    using C = typename St<R>::C;
+    const C al[3] = {(C)ps->alpha[0], (C)ps->alpha[1], (C)ps->alpha[2]};
+    const bool flex = ps->flexible != 0;
+    Acc<C> acc[6];
+    const size_t N4 = N / 4;
+    for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < N4; j += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const C a = al[i];
+            if (a == C(0)) continue;
+            const size_t o = (size_t)i * N + 4 * j;
+            const Q4<C> pv = ld4(p, o), qv = ld4(q, o);
+            Q4<C> rv = ld4(r, o), xv = ld4(x, o);
+            if (xl) {
+                Q4<C> lv = ld4(xl, o);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const C ap = a * pv.v[t];
+                    const C ep = fma(a, pv.v[t], -ap);
+                    C sh, se;
+                    two_sum(xv.v[t], ap, sh, se);
+                    const C lo = lv.v[t] + (se + ep);
+                    const C hi = sh + lo;
+                    lv.v[t] = lo - (hi - sh);
+                    xv.v[t] = hi;
+                }
+                st4(xl, o, lv);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) xv.v[t] = xv.v[t] + a * pv.v[t];
+            }
+            st4(x, o, xv);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                rv.v[t] = rv.v[t] - a * qv.v[t];
+                acc[i].add_prod(rv.v[t], rv.v[t]);
+            }
+            st4(r, o, rv);
+            if (flex) {
+                const Q4<C> zv = ld4(z, o);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) acc[3 + i].add_prod(rv.v[t], zv.v[t]);
+            }
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (is_thread0()) fin(res);
+    }
+}
+
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_dot_rz4(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb, FinBeta fin) {
+    pdl_enter();
+    using C = typename St<R>::C;
+    Acc<C> acc[3];
+    const size_t N4 = N / 4;
+    for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < N4; j += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const size_t o = (size_t)i * N + 4 * j;
+            const Q4<C> rv = ld4(r, o);
+            const Q4<C> zv = ld4(z, o);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) acc[i].add_prod(rv.v[t], zv.v[t]);
+        }
+    }
+    __shared__ double res[3];
+    double vals[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<3>(vals, rb, res)) {
+        if (is_thread0()) fin(res);
+    }
+}
+
+template <class R, class ZT>
+__global__ void __launch_bounds__(256)
+k_update_p4(size_t N, R* __restrict__ p, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps) {
+    pdl_enter();
+    using C = typename St<R>::C;
+    const int first = ps->pfirst;
+    const C be[3] = {(C)ps->beta[0], (C)ps->beta[1], (C)ps->beta[2]};
+    const int act[3] = {ps->active[0], ps->active[1], ps->active[2]};
+    const size_t N4 = N / 4;
+    for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < N4; j += (size_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (!act[i]) continue;
+            const size_t o = (size_t)i * N + 4 * j;
+            const Q4<C> zv = ld4(z, o);
+            Q4<C> pv;
+            if (first) {
+                pv = zv;
+            } else {
+                pv = ld4(p, o);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) pv.v[t] = zv.v[t] + be[i] * pv.v[t];
+            }
+            st4(p, o, pv);
+        }
     }
 }
 
@@ -685,6 +829,7 @@ k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, 
 template <class R, class Y>
 __global__ void __launch_bounds__(256)
 k_join(size_t count, const R* __restrict__ hi, const R* __restrict__ lo, Y* __restrict__ out) {
+    pdl_enter();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (size_t)gridDim.x * blockDim.x)
         St<Y>::st(out, i, (typename St<Y>::C)((double)hi[i] + (lo ? (double)lo[i] : 0.0)));
@@ -694,6 +839,7 @@ k_join(size_t count, const R* __restrict__ hi, const R* __restrict__ lo, Y* __re
 template <class R, class ZT>
 __global__ void __launch_bounds__(256)
 k_dot_rz(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb, FinBeta fin) {
+    pdl_enter();
     using C = typename St<R>::C;
     Acc<C> acc[3];
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
@@ -709,14 +855,28 @@ k_dot_rz(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb,
 #pragma unroll
     for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
     if (grid_reduce<3>(vals, rb, res)) {
-        if (threadIdx.x == 0) fin(res);
+        if (is_thread0()) fin(res);
     }
+}
+
+// Device-side loop control of the captured PCG: continue while a load case
+// is active and the iteration cap is not reached.
+static __global__ void k_set_cond(const PcgScalars* __restrict__ ps, cudaGraphConditionalHandle h, int maxit) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0)
+        cudaGraphSetConditional(h, (ps->nactive > 0 && ps->total < maxit) ? 1u : 0u);
+}
+
+static __global__ void k_pcg_reset(PcgScalars* ps) {
+    pdl_enter();
+    if (threadIdx.x == 0 && blockIdx.x == 0) ps->total = 0;
 }
 
 // b = a (type conversion), optionally clamped to [0, 1].
 template <class X, class Y>
 __global__ void __launch_bounds__(256)
 k_convert(size_t count, const X* __restrict__ a, Y* __restrict__ b, int clamp01) {
+    pdl_enter();
     using C = typename St<Y>::C;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (size_t)gridDim.x * blockDim.x) {
@@ -729,8 +889,10 @@ k_convert(size_t count, const X* __restrict__ a, Y* __restrict__ b, int clamp01)
 // p_i = z_i + beta_i p_i.
 template <class R, class ZT>
 __global__ void __launch_bounds__(256)
-k_update_p(size_t N, R* __restrict__ p, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps, int first) {
+k_update_p(size_t N, R* __restrict__ p, const ZT* __restrict__ z, const PcgScalars* __restrict__ ps) {
+    pdl_enter();
     using C = typename St<R>::C;
+    const int first = ps->pfirst;
     const C b0 = (C)ps->beta[0], b1 = (C)ps->beta[1], b2 = (C)ps->beta[2];
     const int a0 = ps->active[0], a1 = ps->active[1], a2 = ps->active[2];
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;

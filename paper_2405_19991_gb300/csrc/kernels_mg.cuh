@@ -19,11 +19,13 @@ namespace otm {
 template <class KT, class C>
 __global__ void __launch_bounds__(128)
 k_elem_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, C* __restrict__ Kel) {
+    pdl_enter();
     const int nf = 2 * nc;
     const size_t Nc = (size_t)nc * nc * nc;
-    for (size_t E = (size_t)blockIdx.x * blockDim.x + threadIdx.x; E < Nc;
-         E += (size_t)gridDim.x * blockDim.x) {
-        const int X = (int)(E % nc), Y = (int)((E / nc) % nc), Z = (int)(E / ((size_t)nc * nc));
+    OTM_FOR_ROWS(row_, nc * nc) {
+    const int Y = row_ % nc, Z = row_ / nc;
+    OTM_FOR_X(X, nc) {
+        const size_t E = (size_t)row_ * nc + X;
         C ks[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
@@ -37,17 +39,20 @@ k_elem_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, C* __r
             Kel[(size_t)mm * Nc + E] = a;
         }
     }
+    }
 }
 
 // ---- deeper levels: K_E = sum_s P_s^T K_child P_s ----
 template <class C>
 __global__ void __launch_bounds__(64)
 k_elem_coarsen(int nc, const C* __restrict__ Kf, const C* __restrict__ Ps, C* __restrict__ Kc) {
+    pdl_enter();
     const int nf = 2 * nc;
     const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
-    for (size_t E = (size_t)blockIdx.x * blockDim.x + threadIdx.x; E < Nc;
-         E += (size_t)gridDim.x * blockDim.x) {
-        const int X = (int)(E % nc), Y = (int)((E / nc) % nc), Z = (int)(E / ((size_t)nc * nc));
+    OTM_FOR_ROWS(row_, nc * nc) {
+    const int Y = row_ % nc, Z = row_ / nc;
+    OTM_FOR_X(X, nc) {
+        const size_t E = (size_t)row_ * nc + X;
         C out[64];
 #pragma unroll
         for (int i = 0; i < 64; ++i) out[i] = 0;
@@ -82,16 +87,19 @@ k_elem_coarsen(int nc, const C* __restrict__ Kf, const C* __restrict__ Ps, C* __
 #pragma unroll
         for (int i = 0; i < 64; ++i) Kc[(size_t)i * Nc + E] = out[i];
     }
+    }
 }
 
 // ---- node stencils from element matrices ----
 template <class C, class AT>
 __global__ void __launch_bounds__(128)
 k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
+    pdl_enter();
     const size_t N = (size_t)n * n * n;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row_, n * n) {
+    const int y = row_ % n, z = row_ / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row_ * n + x;
         C acc[27];
 #pragma unroll
         for (int o = 0; o < 27; ++o) acc[o] = 0;
@@ -108,6 +116,7 @@ k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
 #pragma unroll
         for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
     }
+    }
 }
 
 // Node stencil of the finest operator itself (used when the hierarchy has a
@@ -115,10 +124,12 @@ k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
 template <class KT, class C, class AT>
 __global__ void __launch_bounds__(128)
 k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
+    pdl_enter();
     const size_t N = (size_t)n * n * n;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
+    OTM_FOR_ROWS(row_, n * n) {
+    const int y = row_ % n, z = row_ / n;
+    OTM_FOR_X(x, n) {
+        const size_t v = (size_t)row_ * n + x;
         C acc[27];
 #pragma unroll
         for (int o = 0; o < 27; ++o) acc[o] = 0;
@@ -138,138 +149,165 @@ k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
 #pragma unroll
         for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
     }
+    }
 }
 
 // ---- Gauss-Seidel colour pass on a 27-point stencil level ----
 // colour = (x%2) + 2(y%2) + 4(z%2); n even.  ZERO (colour 0 only): the field
 // starts at zero and the pass zeroes the other seven nodes of each 2x2x2 cell.
+// gs_stencil_node relaxes node (x, y, z): T_v = (f_v - sum_{o != 0} A_o T_{v+o}) / A_0.
+template <bool ZERO, class AT, class FT, class TT>
+__device__ __forceinline__ void gs_stencil_node(int n, size_t N, int x, int y, int z, const AT* __restrict__ A,
+                                                const FT* __restrict__ f, TT* __restrict__ T) {
+    using C = typename St<TT>::C;
+    const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    int xs[3], ys[3], zs[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d] = wrapd(x, d - 1, n);
+        ys[d] = wrapd(y, d - 1, n) * n;
+        zs[d] = wrapd(z, d - 1, n) * n * n;
+    }
+    C a[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+    const C inv = C(1) / a[13];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        TT* Ti = T + (size_t)i * N;
+        C s = St<FT>::ld(f + (size_t)i * N, v);
+        if (!ZERO) {
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                if (o == 13) continue;
+                s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
+            }
+        }
+        St<TT>::st(Ti, v, s * inv);
+        if (ZERO) {
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+                const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
+                St<TT>::st(Ti, w, C(0));
+            }
+        }
+    }
+}
+
 template <bool ZERO, class AT, class FT, class TT>
 __global__ void __launch_bounds__(256)
 k_gs_stencil(int n, int colour, const AT* __restrict__ A, const FT* __restrict__ f, TT* __restrict__ T) {
-    using C = typename St<TT>::C;
+    pdl_enter();
     const size_t N = (size_t)n * n * n;
     const int h = n >> 1;
-    const size_t M = (size_t)h * h * h;
     const int xo = colour & 1, yo = (colour >> 1) & 1, zo = colour >> 2;
-    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < M;
-         t += (size_t)gridDim.x * blockDim.x) {
-        const int x = 2 * (int)(t % h) + xo;
-        const int y = 2 * (int)((t / h) % h) + yo;
-        const int z = 2 * (int)(t / ((size_t)h * h)) + zo;
-        const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
-        int xs[3], ys[3], zs[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xs[d] = wrapd(x, d - 1, n);
-            ys[d] = wrapd(y, d - 1, n) * n;
-            zs[d] = wrapd(z, d - 1, n) * n * n;
-        }
-        C a[27];
-#pragma unroll
-        for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
-        const C inv = C(1) / a[13];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            TT* Ti = T + (size_t)i * N;
-            C s = St<FT>::ld(f + (size_t)i * N, v);
-            if (!ZERO) {
-#pragma unroll
-                for (int o = 0; o < 27; ++o) {
-                    if (o == 13) continue;
-                    s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
-                }
-            }
-            St<TT>::st(Ti, v, s * inv);
-            if (ZERO) {
-#pragma unroll
-                for (int q = 1; q < 8; ++q) {
-                    const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
-                    St<TT>::st(Ti, w, C(0));
-                }
-            }
-        }
+    OTM_FOR_ROWS(row_, h * h) {
+        const int y = 2 * (row_ % h) + yo, z = 2 * (row_ / h) + zo;
+        OTM_FOR_X(xi, h) gs_stencil_node<ZERO, AT, FT, TT>(n, N, 2 * xi + xo, y, z, A, f, T);
     }
 }
 
 // res = f - A T on a stencil level.
 template <class AT, class FT, class TT, class OT>
+__device__ __forceinline__ void residual_stencil_node(int n, size_t N, int x, int y, int z, const AT* __restrict__ A,
+                                                      const FT* __restrict__ f, const TT* __restrict__ T,
+                                                      OT* __restrict__ res) {
+    using C = typename St<OT>::C;
+    const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    int xs[3], ys[3], zs[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d] = wrapd(x, d - 1, n);
+        ys[d] = wrapd(y, d - 1, n) * n;
+        zs[d] = wrapd(z, d - 1, n) * n * n;
+    }
+    C a[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const TT* Ti = T + (size_t)i * N;
+        C s = St<FT>::ld(f + (size_t)i * N, v);
+#pragma unroll
+        for (int o = 0; o < 27; ++o)
+            s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
+        St<OT>::st(res + (size_t)i * N, v, s);
+    }
+}
+
+template <class AT, class FT, class TT, class OT>
 __global__ void __launch_bounds__(256)
 k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, const TT* __restrict__ T,
                    OT* __restrict__ res) {
-    using C = typename St<OT>::C;
+    pdl_enter();
     const size_t N = (size_t)n * n * n;
-    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N;
-         v += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(v % n), y = (int)((v / n) % n), z = (int)(v / ((size_t)n * n));
-        int xs[3], ys[3], zs[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            xs[d] = wrapd(x, d - 1, n);
-            ys[d] = wrapd(y, d - 1, n) * n;
-            zs[d] = wrapd(z, d - 1, n) * n * n;
-        }
-        C a[27];
-#pragma unroll
-        for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const TT* Ti = T + (size_t)i * N;
-            C s = St<FT>::ld(f + (size_t)i * N, v);
-#pragma unroll
-            for (int o = 0; o < 27; ++o)
-                s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
-            St<OT>::st(res + (size_t)i * N, v, s);
-        }
+    OTM_FOR_ROWS(row_, n * n) {
+        const int y = row_ % n, z = row_ / n;
+        OTM_FOR_X(x, n) residual_stencil_node<AT, FT, TT, OT>(n, N, x, y, z, A, f, T, res);
     }
 }
 
 // ---- coarsest level: dense inverse of the node-0-pinned operator ----
-// One CTA.  W (FP64 workspace, (m-1)^2) receives the dense matrix of the
-// stencil without node 0's row and column, is inverted in place by
-// Gauss-Jordan elimination (no pivoting: the pinned matrix is SPD), and the
-// inverse is stored to Minv in the compute type.
+// One CTA.  The dense matrix of the stencil without node 0's row and column
+// is inverted in place by Gauss-Jordan elimination (no pivoting: the pinned
+// matrix is SPD) in the compute type C, in shared memory when it fits, and
+// the result is symmetrised ((M + M^T) / 2) so the coarse correction, and
+// with it the V-cycle, stays a symmetric operator.
 template <class AT, class C>
 __global__ void __launch_bounds__(1024)
-k_coarse_invert(int n, const AT* __restrict__ A, double* __restrict__ W, C* __restrict__ Minv) {
+k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restrict__ Minv, int use_smem) {
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char inv_sm[];
     const int m = n * n * n;
     const int q = m - 1;
-    __shared__ double col[343];
-    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) W[i] = 0.0;
+    C* W = use_smem ? reinterpret_cast<C*>(inv_sm) : Wg;     // the (m-1)^2 working matrix
+    __shared__ C col[343];
+    __shared__ C ipiv;
+    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) W[i] = C(0);
     __syncthreads();
     for (int v = 1 + threadIdx.x; v < m; v += blockDim.x) {
         const int x = v % n, y = (v / n) % n, z = v / (n * n);
         for (int o = 0; o < 27; ++o) {
             const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
             if (c == 0) continue;
-            W[(size_t)(v - 1) * q + (c - 1)] += (double)St<AT>::ld(A, (size_t)o * m + v);
+            W[(size_t)(v - 1) * q + (c - 1)] += (C)St<AT>::ld(A, (size_t)o * m + v);
         }
     }
     __syncthreads();
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int kp = 0; kp < q; ++kp) {
-        const double piv = W[(size_t)kp * q + kp];
-        const double ip = 1.0 / piv;
+        if (threadIdx.x == 0) ipiv = C(1) / W[(size_t)kp * q + kp];
         __syncthreads();
+        const C ip = ipiv;
         for (int j = threadIdx.x; j < q; j += blockDim.x) {
             if (j == kp) W[(size_t)kp * q + j] = ip;
             else W[(size_t)kp * q + j] *= ip;
         }
         for (int i = threadIdx.x; i < q; i += blockDim.x) col[i] = W[(size_t)i * q + kp];
         __syncthreads();
-        for (size_t t = threadIdx.x; t < (size_t)q * q; t += blockDim.x) {
-            const int i = (int)(t / q), j = (int)(t % q);
+        // warps over rows, lanes over columns
+        for (int i = threadIdx.x >> 5; i < q; i += nw) {
             if (i == kp) continue;
-            if (j == kp) W[t] = -col[i] * ip;
-            else W[t] -= col[i] * W[(size_t)kp * q + j];
+            const C ci = col[i];
+            C* Wi = W + (size_t)i * q;
+            const C* Wk = W + (size_t)kp * q;
+            for (int j = lane; j < q; j += 32) {
+                if (j == kp) Wi[j] = -ci * ip;
+                else Wi[j] -= ci * Wk[j];
+            }
         }
         __syncthreads();
     }
-    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) Minv[i] = (C)W[i];
+    for (size_t t = threadIdx.x; t < (size_t)q * q; t += blockDim.x) {
+        const int i = (int)(t / q), j = (int)(t % q);
+        Minv[t] = C(0.5) * (W[t] + W[(size_t)j * q + i]);
+    }
 }
 
-// T = Minv f with T_0 = 0, then shifted to zero mean.  One CTA.
+// T = Minv f with T_0 = 0, then shifted to zero mean.  Executed by every
+// thread of one CTA (block-level synchronisation only).
 template <class C, class FT, class TT>
-__global__ void __launch_bounds__(1024)
-k_coarse_solve(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* __restrict__ T) {
+__device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* __restrict__ T) {
     const int m = n * n * n;
     const int q = m - 1;
     __shared__ C fs[3][343];
@@ -277,17 +315,17 @@ k_coarse_solve(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* 
     __shared__ double red[3][32];
     for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) fs[i / m][i % m] = St<FT>::ld(f, i);
     __syncthreads();
+    // Minv is symmetric, so row v-1 is read as column v-1: consecutive
+    // threads read consecutive words.
     for (int t = threadIdx.x; t < 3 * m; t += blockDim.x) {
         const int r = t / m, v = t % m;
         C a = 0;
         if (v > 0) {
-            const C* row = Minv + (size_t)(v - 1) * q;
-            for (int j = 0; j < q; ++j) a += row[j] * fs[r][j + 1];
+            for (int j = 0; j < q; ++j) a += Minv[(size_t)j * q + (v - 1)] * fs[r][j + 1];
         }
         ts[r][v] = a;
     }
     __syncthreads();
-    // mean of each load case
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = 0; r < 3; ++r) {
         double s = 0.0;
@@ -306,6 +344,25 @@ k_coarse_solve(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* 
         const int r = t / m, v = t % m;
         St<TT>::st(T, (size_t)t, ts[r][v] - (C)red[r][0]);
     }
+}
+
+// Stage Minv in dynamic shared memory when use_smem (blockDim threads copy).
+template <class C>
+__device__ __forceinline__ const C* stage_minv(const C* __restrict__ Minv_g, int q, int use_smem, unsigned char* sm) {
+    if (!use_smem) return Minv_g;
+    C* ms = reinterpret_cast<C*>(sm);
+    for (int i = threadIdx.x; i < q * q; i += blockDim.x) ms[i] = Minv_g[i];
+    __syncthreads();
+    return ms;
+}
+
+template <class C, class FT, class TT>
+__global__ void __launch_bounds__(1024)
+k_coarse_solve(int n, const C* __restrict__ Minv_g, const FT* __restrict__ f, TT* __restrict__ T, int use_smem) {
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char cs_sm[];
+    const C* Minv = stage_minv<C>(Minv_g, n * n * n - 1, use_smem, cs_sm);
+    coarse_solve_block<C, FT, TT>(n, Minv, f, T);
 }
 
 }  // namespace otm

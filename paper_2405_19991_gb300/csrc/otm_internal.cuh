@@ -11,6 +11,51 @@
 
 namespace otm {
 
+constexpr int kMaxLevelsDev = 12;   // multigrid levels a context may have
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel first waits until the kernel
+// it depends on has completed and its writes are visible (griddepcontrol.wait
+// returns at once when the launch carried no programmatic dependency), then
+// allows its own dependent to be launched, so that launch overlaps this
+// kernel's execution instead of following its completion.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch with the programmatic-stream-serialisation attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                   Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // ---------------------------------------------------------------------------
 // Storage type S -> compute type C.  Fields may be stored in FP64, FP32 or
 // BF16; BF16 fields are computed on in FP32.
@@ -35,6 +80,43 @@ template <> struct St<__nv_bfloat16> {
         p[i] = __float2bfloat16_rn(v);
     }
 };
+
+// Four consecutive values, loaded and stored with one vector access where
+// the storage type allows it (16 B for FP32, 8 B for BF16, two 16 B for FP64).
+template <class C>
+struct Q4 {
+    C v[4];
+};
+__device__ __forceinline__ Q4<float> ld4(const float* p, size_t i) {
+    const float4 a = *reinterpret_cast<const float4*>(p + i);
+    return Q4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ void st4(float* p, size_t i, const Q4<float>& q) {
+    *reinterpret_cast<float4*>(p + i) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ Q4<double> ld4(const double* p, size_t i) {
+    const double2 a = *reinterpret_cast<const double2*>(p + i);
+    const double2 b = *reinterpret_cast<const double2*>(p + i + 2);
+    return Q4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(double* p, size_t i, const Q4<double>& q) {
+    *reinterpret_cast<double2*>(p + i) = make_double2(q.v[0], q.v[1]);
+    *reinterpret_cast<double2*>(p + i + 2) = make_double2(q.v[2], q.v[3]);
+}
+__device__ __forceinline__ Q4<float> ld4(const __nv_bfloat16* p, size_t i) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p + i);
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+    return Q4<float>{{__low2float(a), __high2float(a), __low2float(b), __high2float(b)}};
+}
+__device__ __forceinline__ void st4(__nv_bfloat16* p, size_t i, const Q4<float>& q) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(q.v[0], q.v[1]);
+    __nv_bfloat162 b = __floats2bfloat162_rn(q.v[2], q.v[3]);
+    uint2 raw;
+    raw.x = *reinterpret_cast<unsigned int*>(&a);
+    raw.y = *reinterpret_cast<unsigned int*>(&b);
+    *reinterpret_cast<uint2*>(p + i) = raw;
+}
 
 // ---------------------------------------------------------------------------
 // Accumulators for inner products and volume/tensor sums.  FP32 products are
@@ -111,8 +193,10 @@ template <int NV>
 __device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out) {
     __shared__ double sm[32][NV];
     __shared__ bool is_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarp = (blockDim.x + 31) >> 5;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarp = (nthr + 31) >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         double w = warp_sum(v[i]);
@@ -127,7 +211,7 @@ __device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out
             if (lane == 0) rb.partials[(size_t)blockIdx.x * NV + i] = w;
         }
     }
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         __threadfence();
         unsigned int t = atomicAdd(rb.counter, 1u);
         is_last = (t == gridDim.x - 1);
@@ -139,21 +223,51 @@ __device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         double a = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        for (int b = tid; b < (int)gridDim.x; b += nthr)
             a += __ldcg(rb.partials + (size_t)b * NV + i);
         a = warp_sum(a);
         __syncthreads();
         if (lane == 0) sm[warp][i] = a;
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             double t = 0.0;
             for (int w = 0; w < nwarp; ++w) t += sm[w][i];
             out[i] = t;
         }
     }
-    if (threadIdx.x == 0) *rb.counter = 0u;
+    if (tid == 0) *rb.counter = 0u;
     __syncthreads();
     return true;
+}
+
+// Row mapping of a grid kernel: threadIdx.x runs over x, the (y, z) rows
+// (row = y + n z) over blockIdx.x * blockDim.y + threadIdx.y with a grid
+// stride.  One 32-bit division per row, none per element.
+#define OTM_FOR_ROWS(row, nrows)                                                          \
+    for (int row = blockIdx.x * blockDim.y + threadIdx.y; row < (nrows); row += gridDim.x * blockDim.y)
+#define OTM_FOR_X(xv, nx) for (int xv = threadIdx.x; xv < (nx); xv += blockDim.x)
+// Launch shape for a row-mapped kernel: x threads (a multiple of 32, at most
+// `threads`) times rows per block, and a grid over the rows capped at
+// max_blocks (the capacity of the reduction partials).
+struct RowLaunch {
+    int grid;
+    dim3 block;
+};
+inline RowLaunch row_launch(int nx, int nrows, int max_blocks, int threads = 256) {
+    int bx = ((nx + 31) / 32) * 32;
+    if (bx > threads) bx = threads;
+    if (bx < 32) bx = 32;
+    int by = threads / bx;
+    if (by < 1) by = 1;
+    long long g = ((long long)nrows + by - 1) / by;
+    if (g > max_blocks) g = max_blocks;
+    if (g < 1) g = 1;
+    return RowLaunch{(int)g, dim3((unsigned)bx, (unsigned)by, 1)};
+}
+#define OTM_ROWS_CFG(cfg) (cfg).grid, (cfg).block
+
+__device__ __forceinline__ bool is_thread0() {
+    return threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +298,9 @@ struct PcgScalars {
     int active[3];       // 1 while load case i iterates
     int iters[3];
     int nactive;
+    int first;           // set by the residual of a pass: the next beta is the first of the pass
+    int pfirst;          // the p update after that beta sets p = z
+    int total;           // PCG iterations of this solve (all passes)
     int breakdown;       // bit i set: load case i broke down (pq <= 0 or non-finite)
     int flexible;        // 1: Polak-Ribiere beta
     int pad;

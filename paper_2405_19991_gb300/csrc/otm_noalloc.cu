@@ -103,12 +103,14 @@ otm_status run(int n, double penal, double ks, double kv, const void* k, const v
     // the reduction's ticket counter must start at zero
     e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return fail(OTM_ECUDA, std::string("otm_op_kappa_sens_noalloc: ") + cudaGetErrorString(e));
-    otm::k_kappa<R><<<(int)blocks, 256, 0, st>>>(n, (const R*)k, (const R*)chi, rb,
+    const otm::RowLaunch L = otm::row_launch(n, n * n, (int)blocks);
+    rb.max_blocks = L.grid;
+    otm::k_kappa<R><<<OTM_ROWS_CFG(L), 0, st>>>(n, (const R*)k, (const R*)chi, rb,
                                                  otm::FinKappa{ds, 1.0 / (double)N, 0});
     if (s_f) {
         e = cudaMemcpyAsync(&ds->w[0], w, 6 * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return fail(OTM_ECUDA, std::string("otm_op_kappa_sens_noalloc: ") + cudaGetErrorString(e));
-        otm::k_sens<R><<<(int)blocks, 256, 0, st>>>(n, (const R*)rho_f, (const R*)chi, ds, simp_p(penal, ks, kv),
+        otm::k_sens<R><<<OTM_ROWS_CFG(L), 0, st>>>(n, (const R*)rho_f, (const R*)chi, ds, simp_p(penal, ks, kv),
                                                     (R*)s_f);
     }
     double kap[6];

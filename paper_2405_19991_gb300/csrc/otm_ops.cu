@@ -8,6 +8,7 @@
 
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
+#include "kernels_tiled.cuh"
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -32,6 +33,7 @@ struct OpCtx {
         max_blocks = (sms > 0 ? sms : 1) * 8;
         blocks = max_blocks;
     }
+    otm::RowLaunch rows(int nx, int nrows) const { return otm::row_launch(nx, nrows, max_blocks); }
     int grid(size_t work) const {
         size_t b = (work + 255) / 256;
         if (b < 1) b = 1;
@@ -111,8 +113,8 @@ otm_status filter_simp_t(int n, double rmin, double penal, double ks, double kv,
     if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_filter_simp: scratch");
     const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
-    otm::k_filter<R, true><<<oc.grid(N), 256, 0, oc.st>>>(n, filter_w(rmin), 1, (const R*)rho, (R*)rho_f, (R*)k,
-                                                          simp_p(penal, ks, kv), rb, otm::FinFilter{sc.ds});
+    otm::launch_filter<R, true>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), 1, (const R*)rho, (R*)rho_f, (R*)k,
+                                simp_p(penal, ks, kv), rb, otm::FinFilter{sc.ds});
     return finish(oc.st, "otm_op_filter_simp");
 }
 
@@ -121,8 +123,8 @@ otm_status filter_t_t(int n, double rmin, const void* s_f, void* s, void* stream
     OpCtx oc(stream);
     const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{nullptr, nullptr, 0};
-    otm::k_filter<R, false><<<oc.grid(N), 256, 0, oc.st>>>(n, filter_w(rmin), -1, (const R*)s_f, (R*)s, nullptr,
-                                                           simp_p(3, 1, 1e-3), rb, otm::FinFilter{nullptr});
+    otm::launch_filter<R, false>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), -1, (const R*)s_f, (R*)s, (R*)nullptr,
+                                 simp_p(3, 1, 1e-3), rb, otm::FinFilter{nullptr});
     return finish(oc.st, "otm_op_filter_transpose");
 }
 
@@ -130,7 +132,7 @@ template <class R>
 otm_status macro_load_t(int n, const void* k, void* f, void* stream) {
     OpCtx oc(stream);
     const size_t N = (size_t)n * n * n;
-    otm::k_macro_load<R, R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)k, (R*)f);
+    otm::k_macro_load<R, R><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(n, (const R*)k, (R*)f);
     return finish(oc.st, "otm_op_macro_load");
 }
 
@@ -139,16 +141,24 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     OpCtx oc(stream);
     const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{nullptr, nullptr, 0};
-    otm::k_stencil_apply<0, false, R, R, R, R, otm::FinNone><<<oc.grid(N), 256, 0, oc.st>>>(
-        n, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int tz = sizeof(R) == 4 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
+    if (tz > 0)   // the same kernel and launch shape the solver uses at this size
+        otm::k_stencil_tiled<0, false, R, R, R, R, otm::FinNone>
+            <<<(n / otm::kTX) * (n / otm::kTY) * (n / tz), dim3(otm::kTX, otm::kTY), 0, oc.st>>>(
+                n, tz, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
+    else
+        otm::k_stencil_apply<0, false, R, R, R, R, otm::FinNone><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(
+            n, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
     return finish(oc.st, "otm_op_apply_K");
 }
 
 template <class R>
 otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* stream) {
     OpCtx oc(stream);
-    const size_t work = (size_t)n * n * n / 8;
-    otm::k_gs_fine<false, R, R, R><<<oc.grid(work), 256, 0, oc.st>>>(n, colour >> 1, colour & 1, (const R*)k,
+    otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n / 2, (n / 2) * (n / 2))), 0, oc.st>>>(n, colour >> 1, colour & 1, (const R*)k,
                                                                       (const R*)f, (R*)T);
     return finish(oc.st, "otm_op_gs_colour");
 }
@@ -161,11 +171,11 @@ otm_status kappa_sens_t(int n, double penal, double ks, double kv, const void* k
     if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_kappa_sens: scratch");
     const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
-    otm::k_kappa<R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)k, (const R*)chi, rb,
+    otm::k_kappa<R><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(n, (const R*)k, (const R*)chi, rb,
                                                   otm::FinKappa{sc.ds, 1.0 / (double)N, 0});
     if (s_f) {
         cudaMemcpyAsync(&sc.ds->w[0], w, 6 * sizeof(double), cudaMemcpyHostToDevice, oc.st);
-        otm::k_sens<R><<<oc.grid(N), 256, 0, oc.st>>>(n, (const R*)rho_f, (const R*)chi, sc.ds,
+        otm::k_sens<R><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(n, (const R*)rho_f, (const R*)chi, sc.ds,
                                                      simp_p(penal, ks, kv), (R*)s_f);
     }
     double kap[6];

@@ -3,6 +3,7 @@
 // design iteration.  Instantiated per precision in solver_*.cu.
 #pragma once
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -11,6 +12,8 @@
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
 #include "kernels_mg.cuh"
+#include "kernels_tiled.cuh"
+#include "kernels_cluster.cuh"
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -162,7 +165,11 @@ class Solver : public SolverBase {
     ~Solver() override { release(); }
 
     void release() {
-        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
+        if (gx_first) cudaGraphExecDestroy(gx_first);
+        if (gx_pass) cudaGraphExecDestroy(gx_pass);
+        if (gx_tail) cudaGraphExecDestroy(gx_tail);
+        if (cap2) cudaStreamDestroy(cap2);
+        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
                         partials, counter, ps, ds, stage_f};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
@@ -183,6 +190,26 @@ class Solver : public SolverBase {
     }
 
     RedBuf rbuf() const { return RedBuf{partials, counter, max_blocks}; }
+    RowLaunch rl(int nx, int nrows, int thr = 256) const { return row_launch(nx, nrows, max_blocks, thr); }
+    int tz_ = 0;   // z-planes per CTA of the tiled fine stencil (0: gather kernel)
+    // First level of the cluster-run tail of the V-cycle: the first level >= 1
+    // with at most kClusterMaxN nodes per side (L + 1 when the hierarchy has
+    // a single level).  OTM_NO_CLUSTER=1 disables it.
+    bool use_cluster = true;
+    int cluster_maxn = kClusterMaxN;   // OTM_CLUSTER_MAXN overrides
+    int cluster_lc() const {
+        const int L = nlev - 1;
+        if (!use_cluster || nlev < 2) return L + 1;
+        for (int l = 1; l <= L; ++l)
+            if (sz[l] <= cluster_maxn) return l;
+        return L;
+    }
+    size_t minv_smem_bytes(int l) const {
+        const size_t q = Nl[l] - 1;
+        // staged inverse; with the kernel's static arrays this stays within 48 KB
+        return q * q * sizeof(C) <= 24 * 1024 ? q * q * sizeof(C) : 0;
+    }
+    int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
     int grid(size_t work, int threads = 256) const {
         size_t b = (work + threads - 1) / threads;
         if (b < 1) b = 1;
@@ -212,6 +239,7 @@ class Solver : public SolverBase {
         OTM_CU(cudaGetDevice(&device));
         OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
         max_blocks = sm_count * 8;
+        tz_ = tiled_tz(pin.n, sm_count, max_blocks);
         if (pin.stream) {
             stream = (cudaStream_t)pin.stream;
         } else {
@@ -219,6 +247,15 @@ class Solver : public SolverBase {
             own_stream = true;
         }
         for (auto& e : ev) OTM_CU(cudaEventCreate(&e));
+        OTM_CU(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
+        {
+            const char* ng = getenv("OTM_NO_GRAPH");
+            use_graphs = !(ng && ng[0] == '1');
+            const char* nc = getenv("OTM_NO_CLUSTER");
+            use_cluster = !(nc && nc[0] == '1');
+            const char* cm = getenv("OTM_CLUSTER_MAXN");
+            if (cm) cluster_maxn = atoi(cm);
+        }
 
         OTM_TRY(alloc(rho, N));
         OTM_TRY(alloc(rho_f, N));
@@ -226,6 +263,7 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(s_f, N));
         OTM_TRY(alloc(s, N));
         OTM_TRY(alloc(rho_tmp, N));
+        OTM_TRY(alloc(rho_save, N));
         OTM_TRY(alloc(f, 3 * N));
         OTM_TRY(alloc(x, 3 * N));
         if (!std::is_same<C, double>::value) OTM_TRY(alloc(xl, 3 * N));
@@ -304,7 +342,7 @@ class Solver : public SolverBase {
         OTM_CU(cudaMemcpyAsync(stage_f, src, count * sizeof(float),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
         ++nl_;
-        k_convert<float, R><<<grid(count), 256, 0, stream>>>(count, stage_f, dst, clamp01 ? 1 : 0);
+        launch_pdl(k_convert<float, R>, grid(count), 256, stream, count, stage_f, dst, clamp01 ? 1 : 0);
         OTM_LAUNCH();
         OTM_CU(cudaStreamSynchronize(stream));
         return OTM_OK;
@@ -312,7 +350,7 @@ class Solver : public SolverBase {
     // R field -> float (host or device).
     otm_status from_R(const R* src, float* dst, size_t count, bool on_device) {
         ++nl_;
-        k_convert<R, float><<<grid(count), 256, 0, stream>>>(count, src, stage_f, 0);
+        launch_pdl(k_convert<R, float>, grid(count), 256, stream, count, src, stage_f, 0);
         OTM_LAUNCH();
         OTM_CU(cudaMemcpyAsync(dst, stage_f, count * sizeof(float),
                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
@@ -350,7 +388,7 @@ class Solver : public SolverBase {
                     return OTM_EINVAL;
                 }
                 ++nl_;
-                k_join<R, float><<<grid(3 * N), 256, 0, stream>>>(3 * N, x, xl, stage_f);
+                launch_pdl(k_join<R, float>, grid(3 * N), 256, stream, 3 * N, x, xl, stage_f);
                 OTM_LAUNCH();
                 OTM_CU(cudaMemcpyAsync(out, stage_f, 3 * N * sizeof(float),
                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
@@ -370,47 +408,53 @@ class Solver : public SolverBase {
     // --------------------------------------------------------------- stages
     otm_status filter_simp() {
         ++nl_;
-        k_filter<R, true><<<grid(N), 256, 0, stream>>>(n, fw, 1, rho, rho_f, kf, sp, rbuf(), FinFilter{ds});
+        launch_filter<R, true>(rl(n, n * n), stream, n, fw, 1, rho, rho_f, kf, sp, rbuf(), FinFilter{ds});
         OTM_LAUNCH();
         return OTM_OK;
     }
 
     otm_status build_hierarchy() {
         ++nl_;
-        k_macro_load<R, R><<<grid(N), 256, 0, stream>>>(n, kf, f);
+        launch_pdl(k_macro_load<R, R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, f);
         ++nl_;
-        k_sum3<R><<<grid(N), 256, 0, stream>>>(N, f, rbuf(), FinMean{ps, 1.0 / (double)N});
+        launch_pdl(k_sum3<R>, grid(N), 256, stream, N, f, rbuf(), FinMean{ps, 1.0 / (double)N});
         ++nl_;
-        k_sub_mean<R><<<grid(N), 256, 0, stream>>>(N, f, ps);
+        launch_pdl(k_sub_mean<R>, grid(N), 256, stream, N, f, ps);
         OTM_LAUNCH();
         if (!std::is_same<R, S>::value) {
             ++nl_;
-            k_convert<R, S><<<grid(N), 256, 0, stream>>>(N, kf, k_vc, 0);
+            launch_pdl(k_convert<R, S>, grid(N), 256, stream, N, kf, k_vc, 0);
             OTM_LAUNCH();
         }
         if (nlev == 1) {
             ++nl_;
-            k_stencil_from_k<R, C, S><<<grid(N, 128), 128, 0, stream>>>(n, kf, Al[0]);
+            launch_pdl(k_stencil_from_k<R, C, S>, OTM_ROWS_CFG(rl(n, n * n, 128)), stream, n, kf, Al[0]);
             OTM_LAUNCH();
         } else {
             ++nl_;
-            k_elem_from_k<R, C><<<grid(Nl[1], 128), 128, 0, stream>>>(sz[1], kf, Bs_d, Kel[1]);
+            launch_pdl(k_elem_from_k<R, C>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1], 128)), stream, sz[1], kf, Bs_d, Kel[1]);
             OTM_LAUNCH();
             ++nl_;
-            k_stencil_from_elem<C, S><<<grid(Nl[1], 128), 128, 0, stream>>>(sz[1], Kel[1], Al[1]);
+            launch_pdl(k_stencil_from_elem<C, S>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1], 128)), stream, sz[1], Kel[1], Al[1]);
             OTM_LAUNCH();
             for (int l = 1; l + 1 < nlev; ++l) {
                 ++nl_;
-                k_elem_coarsen<C><<<grid(Nl[l + 1], 64), 64, 0, stream>>>(sz[l + 1], Kel[l], Ps_d, Kel[l + 1]);
+                launch_pdl(k_elem_coarsen<C>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1], 64)), stream, sz[l + 1], Kel[l], Ps_d, Kel[l + 1]);
                 OTM_LAUNCH();
                 ++nl_;
-                k_stencil_from_elem<C, S><<<grid(Nl[l + 1], 128), 128, 0, stream>>>(sz[l + 1], Kel[l + 1], Al[l + 1]);
+                launch_pdl(k_stencil_from_elem<C, S>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1], 128)), stream, sz[l + 1], Kel[l + 1], Al[l + 1]);
                 OTM_LAUNCH();
             }
         }
         const int L = nlev - 1;
         ++nl_;
-        k_coarse_invert<S, C><<<1, 1024, 0, stream>>>(sz[L], Al[L], Wd, Minv);
+        {
+            const size_t q = Nl[L] - 1;
+            const size_t wbytes = q * q * sizeof(C);
+            const int use_smem = wbytes <= 48 * 1024 ? 1 : 0;
+            launch_pdl_smem(k_coarse_invert<S, C>, 1, 1024, use_smem ? wbytes : 0, stream, sz[L], Al[L], (C*)Wd, Minv,
+                            use_smem);
+        }
         OTM_LAUNCH();
         return OTM_OK;
     }
@@ -421,117 +465,331 @@ class Solver : public SolverBase {
         const int L = nlev - 1;
         if (nlev == 1) {
             ++nl_;
-            k_coarse_solve<C, R, S><<<1, 1024, 0, stream>>>(sz[0], Minv, r, z);
+            launch_pdl_smem(k_coarse_solve<C, R, S>, 1, 1024, minv_smem_bytes(0), stream, sz[0], Minv, r, z, minv_smem_bytes(0) > 0 ? 1 : 0);
             OTM_LAUNCH();
             return OTM_OK;
         }
-        const int gq = grid(Nl[0] / 4);
         // level 0, pre-smooth: groups {0,1}, {2,3}, {4,5}, {6,7}
         ++nl_;
-        k_gs_fine<true, S, R, S><<<gq, 256, 0, stream>>>(n, 0, -1, k_vc, r, z);
+        launch_pdl(k_gs_fine<true, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, 0, -1, k_vc, r, z);
         for (int gidx = 1; gidx < 4; ++gidx) {
             ++nl_;
-            k_gs_fine<false, S, R, S><<<gq, 256, 0, stream>>>(n, gidx, -1, k_vc, r, z);
+            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc, r, z);
         }
         ++nl_;
-        k_stencil_apply<1, false, S, S, R, S, FinNone><<<grid(N), 256, 0, stream>>>(n, k_vc, z, r, res0, rbuf(), FinNone{});
+        if (tz_ > 0 && !std::is_same<S, double>::value)
+            launch_pdl(k_stencil_tiled<1, false, S, S, R, S, FinNone>, tiled_grid(), dim3(kTX, kTY), stream, n, tz_,
+                       k_vc, z, r, res0, rbuf(), FinNone{});
+        else
+            launch_pdl(k_stencil_apply<1, false, S, S, R, S, FinNone>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, k_vc, z,
+                       r, res0, rbuf(), FinNone{});
         ++nl_;
-        k_restrict<S, S><<<grid(Nl[1]), 256, 0, stream>>>(sz[1], res0, Fl[1]);
+        launch_pdl(k_restrict<S, S>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1])), stream, sz[1], res0, Fl[1]);
         OTM_LAUNCH();
-        for (int l = 1; l < L; ++l) {
-            const int gc = grid(Nl[l] / 8);
+        const int lc = cluster_lc();   // levels lc..L run in one cluster launch (lc > L: none)
+        const int Lsep = lc <= L ? lc : L;
+        for (int l = 1; l < Lsep; ++l) {
             ++nl_;
-            k_gs_stencil<true, S, S, S><<<gc, 256, 0, stream>>>(sz[l], 0, Al[l], Fl[l], Tl[l]);
+            launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
             for (int c = 1; c < 8; ++c) {
                 ++nl_;
-                k_gs_stencil<false, S, S, S><<<gc, 256, 0, stream>>>(sz[l], c, Al[l], Fl[l], Tl[l]);
+                launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
             }
             ++nl_;
-            k_residual_stencil<S, S, S, S><<<grid(Nl[l]), 256, 0, stream>>>(sz[l], Al[l], Fl[l], Tl[l], Rl[l]);
+            launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Al[l], Fl[l], Tl[l], Rl[l]);
             ++nl_;
-            k_restrict<S, S><<<grid(Nl[l + 1]), 256, 0, stream>>>(sz[l + 1], Rl[l], Fl[l + 1]);
+            launch_pdl(k_restrict<S, S>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1])), stream, sz[l + 1], Rl[l], Fl[l + 1]);
             OTM_LAUNCH();
         }
-        ++nl_;
-        k_coarse_solve<C, S, S><<<1, 1024, 0, stream>>>(sz[L], Minv, Fl[L], Tl[L]);
-        OTM_LAUNCH();
-        for (int l = L - 1; l >= 1; --l) {
+        if (lc <= L) {
+            ClusterArgs<S, C> ca;
+            memset(&ca, 0, sizeof(ca));
+            ca.lc = lc;
+            ca.L = L;
+            ca.minv_smem = minv_smem_bytes(L) > 0 ? 1 : 0;
+            for (int l = 0; l <= L; ++l) {
+                ca.n[l] = sz[l];
+                ca.T[l] = Tl[l];
+                ca.F[l] = Fl[l];
+                ca.Rr[l] = Rl[l];
+                ca.A[l] = Al[l];
+            }
+            ca.Minv = Minv;
             ++nl_;
-            k_prolong_add<S, S><<<grid(Nl[l]), 256, 0, stream>>>(sz[l], Tl[l + 1], Tl[l]);
-            const int gc = grid(Nl[l] / 8);
+            launch_pdl_smem(k_coarse_cluster<S, C>, kClusterCTAs, kClusterThreads, minv_smem_bytes(L), stream, ca);
+        } else {
+            ++nl_;
+            launch_pdl_smem(k_coarse_solve<C, S, S>, 1, 1024, minv_smem_bytes(L), stream, sz[L], Minv, Fl[L], Tl[L],
+                            minv_smem_bytes(L) > 0 ? 1 : 0);
+        }
+        OTM_LAUNCH();
+        for (int l = Lsep - 1; l >= 1; --l) {
+            ++nl_;
+            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1], Tl[l]);
             for (int c = 7; c >= 0; --c) {
                 ++nl_;
-                k_gs_stencil<false, S, S, S><<<gc, 256, 0, stream>>>(sz[l], c, Al[l], Fl[l], Tl[l]);
+                launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
             }
             OTM_LAUNCH();
         }
         ++nl_;
-        k_prolong_add<S, S><<<grid(N), 256, 0, stream>>>(n, Tl[1], z);
+        launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
         for (int gidx = 3; gidx >= 0; --gidx) {
             ++nl_;
-            k_gs_fine<false, S, R, S><<<gq, 256, 0, stream>>>(n, gidx, -1, k_vc, r, z);
+            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc, r, z);
         }
         OTM_LAUNCH();
         return OTM_OK;
     }
 
-    // MG-PCG for the three load cases, starting from x (zero or warm), as
-    // iterative refinement: each pass forms r = f - K x from the stored
-    // iterate (x held as an FP32 pair hi + lo in the FP32/mixed paths), runs
-    // PCG on the correction until the recurrence residual meets cg_tol, and
-    // then checks ||f - K x|| / ||f|| with error-free element terms.  A pass
-    // that does not halve the worst checked residual ends the solve.
-    // Returns OTM_OK when every load case meets cg_tol, else OTM_ENOCONV.
+    // ----------------------------------------------------------------------
+    // MG-PCG for the three load cases as iterative refinement.  A pass forms
+    // r = f - K x from the stored iterate (x held as an FP32 pair hi + lo in
+    // the FP32/mixed paths), runs PCG on the correction until the recurrence
+    // residual meets cg_tol (or the iteration cap), and then checks
+    // ||f - K x|| / ||f|| with error-free element terms.  Further passes
+    // start from the checked residual; a pass that does not halve the worst
+    // checked residual ends the solve (OTM_ENOCONV).
+    //
+    // Graph mode (default): the setup and the first pass are one CUDA graph
+    // in which the PCG loop is a device-side conditional while node; later
+    // passes and the design tail are graphs too, so a design iteration costs
+    // two host synchronisations.  OTM_NO_GRAPH=1 selects the host-driven loop.
+    // ----------------------------------------------------------------------
     static constexpr int kMaxRestarts = 6;
     int last_iters[3] = {0, 0, 0};
+    bool use_graphs = true;
+    cudaStream_t cap2 = nullptr;
+    cudaGraphExec_t gx_first = nullptr, gx_pass = nullptr, gx_tail = nullptr;
+    long long nlg_first = 0, nlg_pass = 0, nlg_body = 0, nlg_tail = 0;
+    R* rho_save = nullptr;
 
-    otm_status solve(int* iters_out, double* resid_out) {
+    // one PCG iteration: z = V(r), beta, p, q = K p, alpha, x and r updates
+    otm_status enqueue_body() {
         RedBuf rb = rbuf();
-        int total = 0;
+        OTM_TRY(vcycle());
+        ++nl_;
+        if (N % 4 == 0) launch_pdl(k_dot_rz4<R, S>, grid(N / 4), 256, stream, N, r, z, rb, FinBeta{ps});
+        else launch_pdl(k_dot_rz<R, S>, grid(N), 256, stream, N, r, z, rb, FinBeta{ps});
+        ++nl_;
+        if (N % 4 == 0) launch_pdl(k_update_p4<R, S>, grid(N / 4), 256, stream, N, p, z, ps);
+        else launch_pdl(k_update_p<R, S>, grid(N), 256, stream, N, p, z, ps);
+        ++nl_;
+if (tz_ > 0 && std::is_same<R, float>::value)
+            launch_pdl(k_stencil_tiled<0, true, R, R, R, R, FinAlpha>, tiled_grid(), dim3(kTX, kTY), stream, n, tz_,
+                       kf, p, (const R*)nullptr, q, rb, FinAlpha{ps});
+        else
+            launch_pdl(k_stencil_apply<0, true, R, R, R, R, FinAlpha>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, p,
+                       (const R*)nullptr, q, rb, FinAlpha{ps});
+        ++nl_;
+        if (N % 4 == 0)
+            launch_pdl(k_update_xr4<R, S>, grid(N / 4), 256, stream, N, x, xl, r, p, q, z, ps, rb, FinResid{ps});
+        else
+            launch_pdl(k_update_xr<R, S>, grid(N), 256, stream, N, x, xl, r, p, q, z, ps, rb, FinResid{ps});
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+    otm_status enqueue_pass_head(int use_true) {
+        ++nl_;
+        launch_pdl(k_residual_x2<R, FinInit>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, r, rbuf(), FinInit{ps, use_true});
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+    otm_status enqueue_check() {
+        ++nl_;
+        launch_pdl(k_true_residual<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, rbuf(), FinTrue{ps});
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+    otm_status enqueue_setup() {
+        OTM_TRY(filter_simp());
+        OTM_TRY(build_hierarchy());
+        ++nl_;
+        launch_pdl(k_pcg_reset, 1, 1, stream, ps);
+        OTM_LAUNCH();
+        return OTM_OK;
+    }
+    // design tail: tensor, sensitivity, filter transpose, Alg. 1, OC update
+    otm_status enqueue_tail() {
+        OTM_TRY(tensor_and_sens(true));
+        ++nl_;
+        launch_pdl(k_governor, 1, 1, stream, ds, 1.0 / (double)N, 0, 0.0);
+        OTM_LAUNCH();
+        if (prm.symmetry) {
+            ++nl_;
+            launch_pdl(k_symmetrize<R>, grid(N / 2 + 1), 256, stream, N, rho, s);
+            OTM_LAUNCH();
+        }
+        OTM_TRY(oc_update());
+        return OTM_OK;
+    }
+
+    otm_status read_ps() {
+        OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        return OTM_OK;
+    }
+
+    // host-driven pass
+    otm_status pass_direct(int use_true) {
+        OTM_TRY(enqueue_pass_head(use_true));
+        OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+        OTM_CU(cudaStreamSynchronize(stream));
+        while (ps_h->nactive > 0 && ps_h->total < prm.cg_maxit) {
+            OTM_TRY(enqueue_body());
+            OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
+            OTM_CU(cudaStreamSynchronize(stream));
+        }
+        OTM_TRY(enqueue_check());
+        return read_ps();
+    }
+
+    // Capture [setup] + pass head + while{body} + check into one graph.
+    otm_status capture_pass(bool with_setup, int use_true, cudaGraphExec_t* out, long long* fixed) {
+        cudaGraph_t g = nullptr;
+        OTM_CU(cudaGraphCreate(&g, 0));
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            err = std::string("cudaGraphConditionalHandleCreate: ") + cudaGetErrorString(e);
+            return OTM_ECUDA;
+        }
+        const long long n0 = nl_;
+        cudaStream_t main = stream;
+        otm_status st = OTM_OK;
+        long long body = 0;
+        e = cudaStreamBeginCaptureToGraph(main, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            err = std::string("cudaStreamBeginCaptureToGraph: ") + cudaGetErrorString(e);
+            return OTM_ECUDA;
+        }
+        if (with_setup) st = enqueue_setup();
+        if (st == OTM_OK) st = enqueue_pass_head(use_true);
+        if (st == OTM_OK) {
+            ++nl_;
+            launch_pdl(k_set_cond, 1, 1, stream, ps, h, prm.cg_maxit);
+            cudaStreamCaptureStatus cs;
+            cudaGraph_t cg = nullptr;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(main, &cs, nullptr, &cg, &deps, nullptr, &nd);
+            cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t cn = nullptr;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
+            if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(main, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+            if (e == cudaSuccess) {
+                cudaGraph_t bg = cp.conditional.phGraph_out[0];
+                e = cudaStreamBeginCaptureToGraph(cap2, bg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+                if (e == cudaSuccess) {
+                    stream = cap2;
+                    const long long b0 = nl_;
+                    st = enqueue_body();
+                    ++nl_;
+                    launch_pdl(k_set_cond, 1, 1, stream, ps, h, prm.cg_maxit);
+                    body = nl_ - b0;
+                    stream = main;
+                    cudaGraph_t tmp = nullptr;
+                    cudaError_t e2 = cudaStreamEndCapture(cap2, &tmp);
+                    if (e2 != cudaSuccess) e = e2;
+                }
+            }
+            if (e != cudaSuccess && st == OTM_OK) {
+                err = std::string("graph capture of the PCG loop: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
+        if (st == OTM_OK) st = enqueue_check();
+        cudaGraph_t done = nullptr;
+        e = cudaStreamEndCapture(main, &done);
+        stream = main;
+        if (st == OTM_OK && e != cudaSuccess) {
+            err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
+            st = OTM_ECUDA;
+        }
+        if (st == OTM_OK) {
+            e = cudaGraphInstantiate(out, g, 0);
+            if (e != cudaSuccess) {
+                err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
+        cudaGraphDestroy(g);
+        *fixed = (nl_ - n0) - body;
+        nlg_body = body;
+        nl_ = n0;
+        cudaGetLastError();
+        return st;
+    }
+
+    otm_status capture_tail() {
+        const long long n0 = nl_;
+        OTM_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
+        otm_status st = enqueue_tail();
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(stream, &g);
+        if (st != OTM_OK) {
+            if (g) cudaGraphDestroy(g);
+            nl_ = n0;
+            return st;
+        }
+        if (e != cudaSuccess) {
+            err = std::string("cudaStreamEndCapture (tail): ") + cudaGetErrorString(e);
+            nl_ = n0;
+            return OTM_ECUDA;
+        }
+        e = cudaGraphInstantiate(&gx_tail, g, 0);
+        cudaGraphDestroy(g);
+        nlg_tail = nl_ - n0;
+        nl_ = n0;
+        if (e != cudaSuccess) {
+            err = std::string("cudaGraphInstantiate (tail): ") + cudaGetErrorString(e);
+            return OTM_ECUDA;
+        }
+        return OTM_OK;
+    }
+
+    otm_status ensure_graphs() {
+        if (gx_first) return OTM_OK;
+        OTM_TRY(capture_pass(true, 0, &gx_first, &nlg_first));
+        OTM_TRY(capture_pass(false, 1, &gx_pass, &nlg_pass));
+        OTM_TRY(capture_tail());
+        return OTM_OK;
+    }
+
+    otm_status launch_pass(cudaGraphExec_t gx, long long fixed) {
+        const int before = ps_h->total;
+        OTM_CU(cudaGraphLaunch(gx, stream));
+        OTM_TRY(read_ps());
+        const int ran = ps_h->total - before;
+        nl_ += fixed + nlg_body * (ran > 0 ? ran : 0);
+        return OTM_OK;
+    }
+
+    // Setup + solve.  Returns OTM_OK / OTM_ENOCONV; fills iterations and the
+    // checked residuals.
+    otm_status setup_and_solve(bool warm, otm_step_info* info) {
+        if (!warm) {
+            OTM_CU(cudaMemsetAsync(x, 0, 3 * N * sizeof(R), stream));
+            if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));
+        }
         int iters[3] = {0, 0, 0};
+        ps_h->total = 0;
+        if (use_graphs) {
+            OTM_TRY(ensure_graphs());
+            OTM_TRY(launch_pass(gx_first, nlg_first));
+        } else {
+            OTM_TRY(enqueue_setup());
+            OTM_TRY(pass_direct(0));
+        }
         bool converged = false;
         double prev_worst = 1e300;
-        int use_true = 0;
         for (int restart = 0;; ++restart) {
-            ++nl_;
-            k_residual_x2<R, FinInit><<<grid(N), 256, 0, stream>>>(n, kf, x, xl, f, r, rb, FinInit{ps, use_true});
-            OTM_LAUNCH();
-            OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
-            OTM_CU(cudaStreamSynchronize(stream));
-            if (ps_h->nactive > 0 && total < prm.cg_maxit) {
-                OTM_TRY(vcycle());
-                ++nl_;
-                k_dot_rz<R, S><<<grid(N), 256, 0, stream>>>(N, r, z, rb, FinBeta{ps, 1});
-                ++nl_;
-                k_update_p<R, S><<<grid(N), 256, 0, stream>>>(N, p, z, ps, 1);
-                OTM_LAUNCH();
-                while (total < prm.cg_maxit) {
-                    ++nl_;
-                    k_stencil_apply<0, true, R, R, R, R, FinAlpha><<<grid(N), 256, 0, stream>>>(
-                        n, kf, p, (const R*)nullptr, q, rb, FinAlpha{ps});
-                    ++nl_;
-                    k_update_xr<R, S><<<grid(N), 256, 0, stream>>>(N, x, xl, r, p, q, z, ps, rb, FinResid{ps});
-                    OTM_LAUNCH();
-                    ++total;
-                    OTM_CU(cudaMemcpyAsync(&ps_h->nactive, &ps->nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-                    OTM_CU(cudaStreamSynchronize(stream));
-                    if (ps_h->nactive == 0) break;
-                    OTM_TRY(vcycle());
-                    ++nl_;
-                    k_dot_rz<R, S><<<grid(N), 256, 0, stream>>>(N, r, z, rb, FinBeta{ps, 0});
-                    ++nl_;
-                    k_update_p<R, S><<<grid(N), 256, 0, stream>>>(N, p, z, ps, 0);
-                    OTM_LAUNCH();
-                }
-                OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
-                OTM_CU(cudaStreamSynchronize(stream));
-                for (int i = 0; i < 3; ++i) iters[i] += ps_h->iters[i];
-            }
-            ++nl_;
-            k_true_residual<R><<<grid(N), 256, 0, stream>>>(n, kf, x, xl, f, rb, FinTrue{ps});
-            OTM_LAUNCH();
-            OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
-            OTM_CU(cudaStreamSynchronize(stream));
+            for (int i = 0; i < 3; ++i) iters[i] += ps_h->iters[i];
             double worst = 0.0;
             bool all_ok = true;
             for (int i = 0; i < 3; ++i) {
@@ -544,15 +802,19 @@ class Solver : public SolverBase {
                 converged = true;
                 break;
             }
-            if (restart >= kMaxRestarts || total >= prm.cg_maxit || !(worst < 0.5 * prev_worst)) break;
+            if (restart >= kMaxRestarts || ps_h->total >= prm.cg_maxit || !(worst < 0.5 * prev_worst)) break;
             prev_worst = worst;
-            use_true = 1;
+            if (use_graphs) OTM_TRY(launch_pass(gx_pass, nlg_pass));
+            else OTM_TRY(pass_direct(1));
         }
         for (int i = 0; i < 3; ++i) {
             const double ff = ps_h->true_ff[i];
-            resid_out[i] = ff > 0 ? std::sqrt(ps_h->true_rr[i] / ff) : 0.0;
-            iters_out[i] = iters[i];
+            const double rel = ff > 0 ? std::sqrt(ps_h->true_rr[i] / ff) : 0.0;
             last_iters[i] = iters[i];
+            if (info) {
+                info->cg_iters[i] = iters[i];
+                info->resid[i] = rel;
+            }
         }
         if (!converged) {
             err = "PCG did not reach cg_tol (cg_maxit reached or the residual stagnated)";
@@ -564,13 +826,13 @@ class Solver : public SolverBase {
     // kappa (and the objective) from x; optionally the sensitivity chain.
     otm_status tensor_and_sens(bool with_sens) {
         ++nl_;
-        k_kappa<R><<<grid(N), 256, 0, stream>>>(n, kf, x, rbuf(), FinKappa{ds, 1.0 / (double)N, 1});
+        launch_pdl(k_kappa<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, rbuf(), FinKappa{ds, 1.0 / (double)N, 1});
         OTM_LAUNCH();
         if (with_sens) {
             ++nl_;
-            k_sens<R><<<grid(N), 256, 0, stream>>>(n, rho_f, x, ds, sp, s_f);
+            launch_pdl(k_sens<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, rho_f, x, ds, sp, s_f);
             ++nl_;
-            k_filter<R, false><<<grid(N), 256, 0, stream>>>(n, fw, -1, s_f, s, nullptr, sp, rbuf(), FinFilter{ds});
+            launch_filter<R, false>(rl(n, n * n), stream, n, fw, -1, (const R*)s_f, s, (R*)nullptr, sp, rbuf(), FinFilter{ds});
             OTM_LAUNCH();
         }
         return OTM_OK;
@@ -579,71 +841,52 @@ class Solver : public SolverBase {
     otm_status oc_update() {
         const double dN = (double)N;
         ++nl_;
-        k_oc_prep<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, rbuf(), FinOcPrep{ds, dN});
+        launch_pdl(k_oc_prep<R>, grid(N), 256, stream, N, rho, s, op, ds, rbuf(), FinOcPrep{ds, dN});
         OTM_LAUNCH();
         const int passes = std::is_same<C, double>::value ? 7 : 4;
         for (int pidx = 0; pidx < passes; ++pidx) {
             const int linear = pidx == passes - 1;
             ++nl_;
-            k_oc_search<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, linear, rbuf(),
+            launch_pdl(k_oc_search<R>, grid(N), 256, stream, N, rho, s, op, ds, linear, rbuf(),
                                                         FinOcSearch{ds, dN, linear, linear, 1.0 / prm.damp});
             OTM_LAUNCH();
         }
         ++nl_;
-        k_oc_apply<R><<<grid(N), 256, 0, stream>>>(N, rho, s, op, ds, rho_tmp);
+        launch_pdl(k_oc_apply<R>, grid(N), 256, stream, N, rho, s, op, ds, rho_tmp);
+        ++nl_;
+        launch_pdl(k_convert<R, R>, grid(N), 256, stream, N, rho_tmp, rho, 0);
         OTM_LAUNCH();
-        std::swap(rho, rho_tmp);
         return OTM_OK;
     }
 
-    otm_status run_solve(bool warm, otm_step_info* info) {
-        if (!warm) {
-            OTM_CU(cudaMemsetAsync(x, 0, 3 * N * sizeof(R), stream));
-            if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));
-        }
-        int iters[3];
-        double resid[3];
-        otm_status st = solve(iters, resid);
-        if (info) {
-            for (int i = 0; i < 3; ++i) {
-                info->cg_iters[i] = iters[i];
-                info->resid[i] = resid[i];
-            }
-        }
-        return st;
+    void fill_info(otm_step_info& loc) {
+        loc.g = ds_h->g;
+        for (int c = 0; c < 6; ++c) loc.kappa[c] = ds_h->kappa[c];
+        loc.mean_rho = ds_h->sum_rho / (double)N;
+        loc.mean_rhop = ds_h->sum_rhop / (double)N;
+        loc.vstar = ds_h->vstar;
+        loc.iteration = iteration;
     }
 
     otm_status homogenize(const float* rho_in, bool on_device, double kappa[6], otm_step_info* info) override {
-        R* saved = nullptr;
         if (rho_in) {
-            saved = rho;
-            rho = rho_tmp;
+            OTM_CU(cudaMemcpyAsync(rho_save, rho, N * sizeof(R), cudaMemcpyDeviceToDevice, stream));
             OTM_TRY(to_R(rho_in, on_device, rho, N, true));
         }
-        otm_status st = OTM_OK;
-        st = filter_simp();
-        if (st == OTM_OK) st = build_hierarchy();
-        otm_status sst = OTM_OK;
-        if (st == OTM_OK) sst = run_solve(false, info);
-        if (sst != OTM_OK && sst != OTM_ENOCONV) st = sst;
-        if (st == OTM_OK) st = tensor_and_sens(false);
-        if (saved) {
-            rho_tmp = rho;
-            rho = saved;
-        }
+        otm_step_info loc;
+        memset(&loc, 0, sizeof(loc));
+        const long long nl0 = nl_;
+        otm_status sst = setup_and_solve(false, &loc);
+        otm_status st = (sst == OTM_OK || sst == OTM_ENOCONV) ? tensor_and_sens(false) : sst;
+        if (rho_in) OTM_CU(cudaMemcpyAsync(rho, rho_save, N * sizeof(R), cudaMemcpyDeviceToDevice, stream));
         if (st != OTM_OK) return st;
         OTM_CU(cudaMemcpyAsync(ds_h, ds, sizeof(DesignScalars), cudaMemcpyDeviceToHost, stream));
         OTM_CU(cudaStreamSynchronize(stream));
         for (int c = 0; c < 6; ++c) kappa[c] = ds_h->kappa[c];
-        if (info) {
-            info->g = ds_h->g;
-            for (int c = 0; c < 6; ++c) info->kappa[c] = ds_h->kappa[c];
-            info->mean_rho = ds_h->sum_rho / (double)N;
-            info->mean_rhop = ds_h->sum_rhop / (double)N;
-            info->vstar = ds_h->vstar;
-            info->lambda = 0.0;
-            info->iteration = iteration;
-        }
+        fill_info(loc);
+        loc.lambda = 0.0;
+        loc.kernel_launches = (int)(nl_ - nl0);
+        if (info) *info = loc;
         have_prev = false;
         return sst;
     }
@@ -653,42 +896,25 @@ class Solver : public SolverBase {
         memset(&loc, 0, sizeof(loc));
         const long long nl0 = nl_;
         OTM_CU(cudaEventRecord(ev[0], stream));
-        OTM_TRY(filter_simp());
-        OTM_CU(cudaEventRecord(ev[1], stream));
-        OTM_TRY(build_hierarchy());
-        OTM_CU(cudaEventRecord(ev[2], stream));
         const bool warm = have_prev && prm.warm_start != OTM_WS_NONE;
-        otm_status sst = run_solve(warm, &loc);
+        otm_status sst = setup_and_solve(warm, &loc);
         if (sst != OTM_OK && sst != OTM_ENOCONV) return sst;
         have_prev = true;
-        OTM_CU(cudaEventRecord(ev[3], stream));
-        OTM_TRY(tensor_and_sens(true));
-        OTM_CU(cudaEventRecord(ev[4], stream));
-        ++nl_;
-        k_governor<<<1, 1, 0, stream>>>(ds, 1.0 / (double)N, 0, 0.0);
-        OTM_LAUNCH();
-        if (prm.symmetry) {
-            ++nl_;
-            k_symmetrize<R><<<grid(N / 2 + 1), 256, 0, stream>>>(N, rho, s);
-            OTM_LAUNCH();
+        OTM_CU(cudaEventRecord(ev[2], stream));
+        if (use_graphs) {
+            OTM_CU(cudaGraphLaunch(gx_tail, stream));
+            nl_ += nlg_tail;
+        } else {
+            OTM_TRY(enqueue_tail());
         }
-        OTM_TRY(oc_update());
         OTM_CU(cudaEventRecord(ev[5], stream));
         OTM_CU(cudaMemcpyAsync(ds_h, ds, sizeof(DesignScalars), cudaMemcpyDeviceToHost, stream));
         OTM_CU(cudaStreamSynchronize(stream));
-        loc.g = ds_h->g;
-        for (int c = 0; c < 6; ++c) loc.kappa[c] = ds_h->kappa[c];
-        loc.mean_rho = ds_h->sum_rho / (double)N;
-        loc.mean_rhop = ds_h->sum_rhop / (double)N;
-        loc.vstar = ds_h->vstar;
+        fill_info(loc);
         loc.lambda = ds_h->lambda;
-        loc.iteration = iteration;
         float ms;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]); loc.stage_ms[0] = ms;
-        cudaEventElapsedTime(&ms, ev[1], ev[2]); loc.stage_ms[1] = ms;
-        cudaEventElapsedTime(&ms, ev[2], ev[3]); loc.stage_ms[2] = ms;
-        cudaEventElapsedTime(&ms, ev[3], ev[4]); loc.stage_ms[3] = ms;
-        cudaEventElapsedTime(&ms, ev[4], ev[5]); loc.stage_ms[4] = ms;
+        cudaEventElapsedTime(&ms, ev[0], ev[2]); loc.stage_ms[2] = ms;
+        cudaEventElapsedTime(&ms, ev[2], ev[5]); loc.stage_ms[4] = ms;
         cudaEventElapsedTime(&ms, ev[0], ev[5]); loc.stage_ms[7] = ms;
         loc.kernel_launches = (int)(nl_ - nl0);
         iteration += 1;

@@ -1,0 +1,86 @@
+"""Run one libotm operator (or design steps) on seeded inputs, for timing and
+for profiling a single kernel under ncu.
+
+  python -m paper_2405_19991_gb300.opbench --op apply_K --n 128 --reps 3
+  python -m paper_2405_19991_gb300.opbench --op step --n 128 --reps 2 --warmup 3
+
+Ops: apply_K, gs (one fine colour pass), filter, kappa_sens, oc, step.
+Prints the mean CUDA-event time per repetition.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", default="apply_K")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--dtype", type=int, default=1, help="1 = FP32, 0 = FP64; precision for --op step (2 = mixed)")
+    args = ap.parse_args()
+
+    import torch
+    from paper_2405_19991_gb300 import otm
+    import workloads as W
+
+    n, N = args.n, args.n ** 3
+    dev = "cuda:0"
+    t = torch.float64 if args.dtype == 0 else torch.float32
+    st = torch.cuda.current_stream()
+    rng = np.random.default_rng(0)
+    rho = torch.as_tensor(W.initial_density(n, 0.3, 1), dtype=t, device=dev)
+    k = (1e-3 + rho ** 3 * (1 - 1e-3)).contiguous()
+    u = torch.as_tensor(rng.standard_normal(3 * N), dtype=t, device=dev)
+    out = torch.empty(3 * N, dtype=t, device=dev)
+    s = torch.as_tensor(-np.abs(rng.standard_normal(N)), dtype=t, device=dev)
+    ctx = None
+    if args.op == "step":
+        p = otm.otm_params_default(n=n, precision=args.dtype, kappa_target=W.TARGET_ORTHOTROPIC, rmin=2.0,
+                                   stream=st.cuda_stream)
+        ctx = otm.otm_create_ex(p)
+        r0 = W.initial_density(n, 0.3, 1).astype(np.float32)
+        otm.otm_set_density(ctx, r0.ctypes.data, 0)
+
+    def run():
+        if args.op == "apply_K":
+            otm.otm_op_apply_K(args.dtype, n, k, u, out, st.cuda_stream)
+        elif args.op == "gs":
+            otm.otm_op_gs_colour(args.dtype, n, k, u, out, 0, st.cuda_stream)
+        elif args.op == "filter":
+            otm.otm_op_filter_simp(args.dtype, n, 2.0, 3.0, 1.0, 1e-3, rho, out, out[N:], st.cuda_stream)
+        elif args.op == "kappa_sens":
+            otm.otm_op_kappa_sens(args.dtype, n, 3.0, 1.0, 1e-3, k, rho, u, [1, 1, 1, 0, 0, 0], out,
+                                  st.cuda_stream)
+        elif args.op == "oc":
+            otm.otm_op_oc_update(args.dtype, n, 0.29, 0.05, 0.5, 1e-3, rho, s, out, st.cuda_stream)
+        elif args.op == "step":
+            otm.otm_step(ctx)
+        else:
+            raise SystemExit(f"unknown op {args.op}")
+
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.reps):
+        run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    print(f"{args.op} n={n}: {e0.elapsed_time(e1) / args.reps * 1e3:.1f} us per repetition")
+    if ctx is not None:
+        otm.otm_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()

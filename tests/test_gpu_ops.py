@@ -70,7 +70,7 @@ def test_macro_load(dtype, n):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
-@pytest.mark.parametrize("n", [4, 5, 8, 13, 16])
+@pytest.mark.parametrize("n", [4, 5, 8, 13, 16, 32, 64, 96])
 def test_apply_K(dtype, n):
     otm = _otm()
     k = _k(n, 4)
