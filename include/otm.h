@@ -279,7 +279,9 @@ OTM_API otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u
 
 /* One colour pass of the Gauss-Seidel relaxation of Sec. 2.4,
  * S_v T_v = f_v - M_v, on the finest grid for the nodes of colour
- * c = (x%2) + 2(y%2) + 4(z%2) in [0, 8) (n even).  Updates T in place. */
+ * c = (x%2) + 2(y%2) + 4(z%2) in [0, 8) (n even); colour 8 + g, g in [0, 4),
+ * relaxes the two colours 2g and 2g + 1 together (they share no matrix
+ * entry), the pass the solver runs.  Updates T in place. */
 OTM_API otm_status otm_op_gs_colour(int dtype, int n, const void* k, const void* f,
                                     void* T, int colour, void* stream);
 

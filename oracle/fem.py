@@ -146,6 +146,28 @@ def apply_operator_at(n: int, k: np.ndarray, u: np.ndarray, nodes, K0: np.ndarra
     return out
 
 
+def gauss_seidel_at(n: int, k: np.ndarray, f: np.ndarray, T: np.ndarray, nodes,
+                    K0: np.ndarray | None = None) -> np.ndarray:
+    """New values at `nodes` of one Gauss-Seidel relaxation of those nodes
+    (Sec. 2.4): T_v = (f_v - M_v) / S_v with S_v = sum over incident
+    elements of k_e K^0_{ll} and M_v = [K T]_v - S_v T_v.  Exact for a set of
+    mutually uncoupled nodes (one colour); f, T of shape (m, n^3)."""
+    if K0 is None:
+        K0 = k0_matrix()
+    KT = apply_operator_at(n, k, T, nodes, K0)
+    out = np.zeros((np.atleast_2d(T).shape[0], len(nodes)))
+    for j, v in enumerate(nodes):
+        x, y, z = v % n, (v // n) % n, v // (n * n)
+        S = 0.0
+        for l in range(8):
+            a, b, c = corner_offset(l)
+            e = ((x - a) % n) + n * (((y - b) % n) + n * ((z - c) % n))
+            S += k[e] * K0[l, l]
+        M = KT[:, j] - S * np.atleast_2d(T)[:, v]
+        out[:, j] = (np.atleast_2d(f)[:, v] - M) / S
+    return out
+
+
 def gauss_seidel_pass(K: sp.csr_matrix, f: np.ndarray, T: np.ndarray, nodes) -> np.ndarray:
     """One Gauss-Seidel relaxation over `nodes` in the given order
     (Sec. 2.4): S_v T_v = f_v - M_v with S_v = K_vv and M_v the row of K

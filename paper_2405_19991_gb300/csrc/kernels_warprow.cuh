@@ -1,0 +1,316 @@
+// Warp-row forms of finest-grid kernels (n a multiple of 128): the fine
+// prolongation, the residual of the FP32-pair iterate and its error-free
+// check.
+//
+// A warp covers 128 consecutive x of one (y, z) row; lane l owns the four
+// nodes x = x0 + 4l .. x0 + 4l + 3.  For every neighbouring row the lane
+// loads its four values with one vector access, and the values at x - 1 and
+// x + 4 come from the neighbouring lanes by shuffle (lane 0 / lane 31 wrap
+// periodically when one warp spans the whole row, and load the value
+// otherwise).  Rows are folded into the four node sums as they arrive, so
+// one row is live at a time.  (Measured at 128^3, this layout is faster than
+// the row-mapped kernels for these three, and slower than the tiled stencil
+// and the row-mapped Gauss-Seidel pass, which the solver uses instead.)
+#pragma once
+#include "kernels_fine.cuh"
+
+namespace otm {
+
+inline bool warprow_ok(int n) { return n >= 128 && n % 128 == 0; }
+
+// Values of one row at x0+4l-1 .. x0+4l+4 (six floats).
+template <class T>
+__device__ __forceinline__ void row6(const T* __restrict__ F, size_t ro, int xb, int n, int lane, bool whole,
+                                     float (&v)[6]) {
+    const Q4<float> q = ld4f(F, ro + (size_t)xb);
+    v[1] = q.v[0];
+    v[2] = q.v[1];
+    v[3] = q.v[2];
+    v[4] = q.v[3];
+    v[0] = __shfl_sync(0xffffffffu, v[4], (lane + 31) & 31);
+    v[5] = __shfl_sync(0xffffffffu, v[1], (lane + 1) & 31);
+    if (!whole) {
+        if (lane == 0) v[0] = (float)St<T>::ld(F, ro + (size_t)(xb == 0 ? n - 1 : xb - 1));
+        if (lane == 31) v[5] = (float)St<T>::ld(F, ro + (size_t)(xb + 4 == n ? 0 : xb + 4));
+    }
+}
+
+// Row offsets of the 3 x 3 (y, z) neighbourhood: ro[dz+1][dy+1].
+__device__ __forceinline__ void row_offsets(int n, int y, int z, size_t (&ro)[3][3]) {
+    const size_t nn = (size_t)n * n;
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+            ro[dz + 1][dy + 1] = (size_t)wrapd(y, dy, n) * n + (size_t)wrapd(z, dz, n) * nn;
+}
+
+template <class KT>
+__device__ __forceinline__ void load_k_rows(const KT* __restrict__ k, int n, int y, int z, int xb, int lane,
+                                            bool whole, float (&kr)[2][2][6]) {
+    const size_t nn = (size_t)n * n;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            row6<KT>(k, (size_t)wrapd(y, -b, n) * n + (size_t)wrapd(z, -c, n) * nn, xb, n, lane, whole, kr[c][b]);
+}
+
+// Contribution of the neighbouring row (dy, dz) (six values v at x-1..x+4)
+// to the neighbour sums of the lane's four nodes.  Coefficients as in
+// kernels_fine.cuh: corners carry k_abc, edges the sum of the two elements
+// sharing them; face neighbours and the centre carry nothing.  DIFF
+// subtracts the centre value uc[j] (difference form).
+template <bool DIFF>
+__device__ __forceinline__ void add_row(int dy, int dz, const float (&v)[6], const float (&kr)[2][2][6],
+                                        const float (&uc)[4], float (&acc)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float c0 = DIFF ? uc[j] : 0.f;
+        const float vm = v[j] - c0, v0 = v[1 + j] - c0, vp = v[2 + j] - c0;   // x-1, x, x+1
+        auto K = [&](int c, int b, int a) -> float { return kr[c][b][1 + j - a]; };
+        if (dy != 0 && dz != 0) {
+            const int b = (1 - dy) / 2, c = (1 - dz) / 2;
+            acc[j] += K(c, b, 0) * vp + K(c, b, 1) * vm + (K(c, b, 0) + K(c, b, 1)) * v0;
+        } else if (dy != 0) {
+            const int b = (1 - dy) / 2;
+            acc[j] += (K(0, b, 0) + K(1, b, 0)) * vp + (K(0, b, 1) + K(1, b, 1)) * vm;
+        } else if (dz != 0) {
+            const int c = (1 - dz) / 2;
+            acc[j] += (K(c, 0, 0) + K(c, 1, 0)) * vp + (K(c, 0, 1) + K(c, 1, 1)) * vm;
+        }
+    }
+}
+
+// Prolongation + correction on the finest grid, T += P Tc (trilinear).  Lane
+// l's four fine nodes x = 4l..4l+3 (within the warp's 128) use the coarse
+// values at 2l, 2l+1, 2l+2.
+template <class CT, class TT>
+__global__ void __launch_bounds__(256)
+k_prolong_wr(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
+    pdl_enter();
+    const int nc = nf / 2;
+    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    const int lane = threadIdx.x & 31;
+    const int wpr = nf / 128;
+    const long long nwarps = (long long)nf * nf * wpr;
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwarps;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int seg = (int)(w % wpr);
+        const int row = (int)(w / wpr);
+        const int y = row % nf, z = row / nf;
+        const int xb = seg * 128 + 4 * lane;
+        const int cxb = xb / 2;                      // even
+        int yi[2], zi[2];
+        float wy[2], wz[2];
+        int cy = 1, cz = 1;
+        if (y & 1) { yi[0] = y >> 1; yi[1] = wrapp(y >> 1, nc); wy[0] = wy[1] = 0.5f; cy = 2; }
+        else { yi[0] = yi[1] = y >> 1; wy[0] = 1.f; wy[1] = 0.f; }
+        if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = 0.5f; cz = 2; }
+        else { zi[0] = zi[1] = z >> 1; wz[0] = 1.f; wz[1] = 0.f; }
+        const size_t vb = (size_t)row * nf + (size_t)xb;
+#pragma unroll 1
+        for (int i = 0; i < 3; ++i) {
+            const CT* tc = Tc + (size_t)i * Nc;
+            float s[3] = {0.f, 0.f, 0.f};
+            for (int c = 0; c < cz; ++c)
+                for (int b = 0; b < cy; ++b) {
+                    const size_t ro = (size_t)yi[b] * nc + (size_t)zi[c] * nc * nc;
+                    const float a0 = (float)St<CT>::ld(tc, ro + cxb);
+                    const float a1 = (float)St<CT>::ld(tc, ro + cxb + 1);
+                    float a2 = __shfl_sync(0xffffffffu, a0, (lane + 1) & 31);
+                    if (lane == 31 && wpr > 1) a2 = (float)St<CT>::ld(tc, ro + (size_t)(cxb + 2 == nc ? 0 : cxb + 2));
+                    const float wgt = wz[c] * wy[b];
+                    s[0] += wgt * a0;
+                    s[1] += wgt * a1;
+                    s[2] += wgt * a2;
+                }
+            Q4<float> t = ld4f(T + (size_t)i * Nf, vb);
+            t.v[0] += s[0];
+            t.v[1] += 0.5f * (s[0] + s[1]);
+            t.v[2] += s[1];
+            t.v[3] += 0.5f * (s[1] + s[2]);
+            st4f(T + (size_t)i * Nf, vb, t);
+        }
+    }
+}
+
+// Values of row (dy, dz) of the pair field hi + lo minus the centre pair, each
+// difference rounded once: d[t] for x-1..x+4 relative to node t-1 ... (the
+// centre of node j is (hv[j], lv[j])).
+__device__ __forceinline__ void pair_row(const float* __restrict__ xh, const float* __restrict__ xl, size_t ro, int xb,
+                                         int n, int lane, bool whole, float (&vh)[6], float (&vl)[6]) {
+    row6<float>(xh, ro, xb, n, lane, whole, vh);
+    if (xl) row6<float>(xl, ro, xb, n, lane, whole, vl);
+    else
+#pragma unroll
+        for (int t = 0; t < 6; ++t) vl[t] = 0.f;
+}
+
+// r = f - K (hi + lo) (residual of the FP32-pair iterate; lo may be null),
+// reducing ||r||^2 and ||f||^2 into FinInit.
+template <class Fin>
+__global__ void __launch_bounds__(256, 3)
+k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
+                 const float* __restrict__ f, float* __restrict__ r, RedBuf rb, Fin fin) {
+    pdl_enter();
+    const size_t N = (size_t)n * n * n;
+    const int lane = threadIdx.x & 31;
+    const int wpr = n / 128;
+    const bool whole = wpr == 1;
+    const long long nwarps = (long long)n * n * wpr;
+    Acc<float> acc[6];
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwarps;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int seg = (int)(w % wpr);
+        const int row = (int)(w / wpr);
+        const int y = row % n, z = row / n;
+        const int xb = seg * 128 + 4 * lane;
+        size_t ro[3][3];
+        row_offsets(n, y, z, ro);
+        float kr[2][2][6];
+        load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
+        const size_t vb = ro[1][1] + (size_t)xb;
+#pragma unroll 1
+        for (int i = 0; i < 3; ++i) {
+            const size_t fo = (size_t)i * N;
+            const Q4<float> ch = ld4f(xh + fo, vb);
+            Q4<float> cl{{0.f, 0.f, 0.f, 0.f}};
+            if (xl) cl = ld4f(xl + fo, vb);
+            const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+            float nd[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    if (dy == 0 && dz == 0) continue;
+                    float vh[6], vl[6];
+                    pair_row(xh + fo, xl ? xl + fo : nullptr, ro[dz + 1][dy + 1], xb, n, lane, whole, vh, vl);
+                    // the three x-neighbours of node j as pair differences,
+                    // placed where add_row reads them for node j
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int t = 0; t < 3; ++t) d[j + t] = df_diff(vh[j + t], vl[j + t], ch.v[j], cl.v[j]);
+                        float a[4] = {0.f, 0.f, 0.f, 0.f};
+                        add_row<false>(dy, dz, d, kr, zero4, a);
+                        nd[j] += a[j];
+                    }
+                }
+            const Q4<float> fv = ld4f(f + fo, vb);
+            Q4<float> o;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                o.v[j] = fv.v[j] + nd[j] * (1.0f / 12.0f);
+                acc[i].add_prod(o.v[j], o.v[j]);
+                acc[3 + i].add_prod(fv.v[j], fv.v[j]);
+            }
+            st4f(r + fo, vb, o);
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (is_thread0()) fin(res);
+    }
+}
+
+// ||f - K (hi + lo)||^2 with error-free element terms (see k_true_residual):
+// each of the 32 terms k_e (u_w - u_v) of a node is formed with TwoProduct
+// and summed with TwoSum.
+static __global__ void __launch_bounds__(256, 3)
+k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
+                   const float* __restrict__ f, RedBuf rb, FinTrue fin) {
+    pdl_enter();
+    const size_t N = (size_t)n * n * n;
+    const int lane = threadIdx.x & 31;
+    const int wpr = n / 128;
+    const bool whole = wpr == 1;
+    const long long nwarps = (long long)n * n * wpr;
+    Acc<float> acc[6];
+    for (long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwarps;
+         w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int seg = (int)(w % wpr);
+        const int row = (int)(w / wpr);
+        const int y = row % n, z = row / n;
+        const int xb = seg * 128 + 4 * lane;
+        size_t ro[3][3];
+        row_offsets(n, y, z, ro);
+        float kr[2][2][6];
+        load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
+        const size_t vb = ro[1][1] + (size_t)xb;
+#pragma unroll 1
+        for (int i = 0; i < 3; ++i) {
+            const size_t fo = (size_t)i * N;
+            const Q4<float> ch = ld4f(xh + fo, vb);
+            Q4<float> cl{{0.f, 0.f, 0.f, 0.f}};
+            if (xl) cl = ld4f(xl + fo, vb);
+            float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+                for (int dy = -1; dy <= 1; ++dy) {
+                    if (dy == 0 && dz == 0) continue;
+                    float vh[6], vl[6];
+                    pair_row(xh + fo, xl ? xl + fo : nullptr, ro[dz + 1][dy + 1], xb, n, lane, whole, vh, vl);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        auto term = [&](float kv, float dv) {
+                            const float p = kv * dv;
+                            const float pe = fmaf(kv, dv, -p);
+                            float t, e;
+                            two_sum(s[j], p, t, e);
+                            s[j] = t;
+                            c[j] += e + pe;
+                        };
+                        auto D = [&](int dx) -> float { return df_diff(vh[1 + j + dx], vl[1 + j + dx], ch.v[j], cl.v[j]); };
+                        auto K = [&](int cc, int b, int a) -> float { return kr[cc][b][1 + j - a]; };
+                        if (dy != 0 && dz != 0) {
+                            const int b = (1 - dy) / 2, cc = (1 - dz) / 2;
+                            const float d0 = D(0);
+                            term(K(cc, b, 0), D(1));
+                            term(K(cc, b, 1), D(-1));
+                            term(K(cc, b, 0), d0);
+                            term(K(cc, b, 1), d0);
+                        } else if (dy != 0) {
+                            const int b = (1 - dy) / 2;
+                            const float dp = D(1), dm = D(-1);
+                            term(K(0, b, 0), dp);
+                            term(K(1, b, 0), dp);
+                            term(K(0, b, 1), dm);
+                            term(K(1, b, 1), dm);
+                        } else {
+                            const int cc = (1 - dz) / 2;
+                            const float dp = D(1), dm = D(-1);
+                            term(K(cc, 0, 0), dp);
+                            term(K(cc, 1, 0), dp);
+                            term(K(cc, 0, 1), dm);
+                            term(K(cc, 1, 1), dm);
+                        }
+                    }
+                }
+            const Q4<float> fv = ld4f(f + fo, vb);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float fvj = fv.v[j];
+                float t, e;
+                two_sum(fvj, s[j] * (1.0f / 12.0f), t, e);
+                const float rv = t + (e + c[j] * (1.0f / 12.0f) + fmaf(s[j], 1.0f / 12.0f, -(s[j] * (1.0f / 12.0f))));
+                acc[i].add_prod(rv, rv);
+                acc[3 + i].add_prod(fvj, fvj);
+            }
+        }
+    }
+    __shared__ double res[6];
+    double vals[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
+    if (grid_reduce<6>(vals, rb, res)) {
+        if (is_thread0()) fin(res);
+    }
+}
+
+}  // namespace otm

@@ -118,6 +118,19 @@ __device__ __forceinline__ void st4(__nv_bfloat16* p, size_t i, const Q4<float>&
     *reinterpret_cast<uint2*>(p + i) = raw;
 }
 
+// Four consecutive values as floats, whatever the storage type.
+__device__ __forceinline__ Q4<float> ld4f(const float* p, size_t i) { return ld4(p, i); }
+__device__ __forceinline__ Q4<float> ld4f(const __nv_bfloat16* p, size_t i) { return ld4(p, i); }
+__device__ __forceinline__ Q4<float> ld4f(const double* p, size_t i) {
+    const Q4<double> d = ld4(p, i);
+    return Q4<float>{{(float)d.v[0], (float)d.v[1], (float)d.v[2], (float)d.v[3]}};
+}
+__device__ __forceinline__ void st4f(float* p, size_t i, const Q4<float>& q) { st4(p, i, q); }
+__device__ __forceinline__ void st4f(__nv_bfloat16* p, size_t i, const Q4<float>& q) { st4(p, i, q); }
+__device__ __forceinline__ void st4f(double* p, size_t i, const Q4<float>& q) {
+    st4(p, i, Q4<double>{{(double)q.v[0], (double)q.v[1], (double)q.v[2], (double)q.v[3]}});
+}
+
 // ---------------------------------------------------------------------------
 // Accumulators for inner products and volume/tensor sums.  FP32 products are
 // summed with an error-free transformation (TwoSum of the running sum and

@@ -9,6 +9,7 @@
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
 #include "kernels_tiled.cuh"
+#include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -158,8 +159,14 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
 template <class R>
 otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* stream) {
     OpCtx oc(stream);
-    otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n / 2, (n / 2) * (n / 2))), 0, oc.st>>>(n, colour >> 1, colour & 1, (const R*)k,
-                                                                      (const R*)f, (R*)T);
+    if (colour >= 8) {   // a group pass (both x parities), as the solver runs it
+        const int group = colour - 8;
+        otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n, (n / 2) * (n / 2))), 0, oc.st>>>(
+            n, group, -1, (const R*)k, (const R*)f, (R*)T);
+    } else {
+        otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n / 2, (n / 2) * (n / 2))), 0, oc.st>>>(
+            n, colour >> 1, colour & 1, (const R*)k, (const R*)f, (R*)T);
+    }
     return finish(oc.st, "otm_op_gs_colour");
 }
 
@@ -257,8 +264,8 @@ otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u, void* 
 }
 
 otm_status otm_op_gs_colour(int dtype, int n, const void* k, const void* f, void* T, int colour, void* stream) {
-    OP_CHECK(bad_dtype(dtype) || bad_n(n) || (n & 1) || !k || !f || !T || colour < 0 || colour > 7,
-             "otm_op_gs_colour: bad argument (n must be even, colour in [0, 8))");
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || (n & 1) || !k || !f || !T || colour < 0 || colour > 11,
+             "otm_op_gs_colour: bad argument (n must be even, colour in [0, 12))");
     if (dtype == OTM_FP64) return gs_t<double>(n, k, f, T, colour, stream);
     return gs_t<float>(n, k, f, T, colour, stream);
 }

@@ -14,6 +14,7 @@
 #include "kernels_mg.cuh"
 #include "kernels_tiled.cuh"
 #include "kernels_cluster.cuh"
+#include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
 
 namespace otm {
@@ -210,6 +211,13 @@ class Solver : public SolverBase {
         return q * q * sizeof(C) <= 24 * 1024 ? q * q * sizeof(C) : 0;
     }
     int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
+    // warp-row kernels on the finest grid (FP32 / mixed paths, 128 | n)
+    bool wr_ = false;
+    int wr_grid(long long warps) const {
+        long long b = (warps + 7) / 8;
+        if (b > max_blocks) b = max_blocks;
+        return (int)(b < 1 ? 1 : b);
+    }
     int grid(size_t work, int threads = 256) const {
         size_t b = (work + threads - 1) / threads;
         if (b < 1) b = 1;
@@ -240,6 +248,7 @@ class Solver : public SolverBase {
         OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
         max_blocks = sm_count * 8;
         tz_ = tiled_tz(pin.n, sm_count, max_blocks);
+        wr_ = warprow_ok(pin.n) && std::is_same<R, float>::value;
         if (pin.stream) {
             stream = (cudaStream_t)pin.stream;
         } else {
@@ -474,7 +483,8 @@ class Solver : public SolverBase {
         launch_pdl(k_gs_fine<true, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, 0, -1, k_vc, r, z);
         for (int gidx = 1; gidx < 4; ++gidx) {
             ++nl_;
-            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc, r, z);
+            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
+                           r, z);
         }
         ++nl_;
         if (tz_ > 0 && !std::is_same<S, double>::value)
@@ -533,10 +543,14 @@ class Solver : public SolverBase {
             OTM_LAUNCH();
         }
         ++nl_;
-        launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
+        if (wr_)
+            launch_pdl(k_prolong_wr<S, S>, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const S*)Tl[1], z);
+        else
+            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
         for (int gidx = 3; gidx >= 0; --gidx) {
             ++nl_;
-            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc, r, z);
+            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
+                           r, z);
         }
         OTM_LAUNCH();
         return OTM_OK;
@@ -591,13 +605,23 @@ if (tz_ > 0 && std::is_same<R, float>::value)
     }
     otm_status enqueue_pass_head(int use_true) {
         ++nl_;
-        launch_pdl(k_residual_x2<R, FinInit>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, r, rbuf(), FinInit{ps, use_true});
+        if (wr_)
+            launch_pdl(k_residual_x2_wr<FinInit>, wr_grid((long long)n * n * (n / 128)), 256, stream, n,
+                       (const float*)kf, (const float*)x, (const float*)xl, (const float*)f, (float*)r, rbuf(),
+                       FinInit{ps, use_true});
+        else
+            launch_pdl(k_residual_x2<R, FinInit>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, r, rbuf(),
+                       FinInit{ps, use_true});
         OTM_LAUNCH();
         return OTM_OK;
     }
     otm_status enqueue_check() {
         ++nl_;
-        launch_pdl(k_true_residual<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, rbuf(), FinTrue{ps});
+        if (wr_)
+            launch_pdl(k_true_residual_wr, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const float*)kf,
+                       (const float*)x, (const float*)xl, (const float*)f, rbuf(), FinTrue{ps});
+        else
+            launch_pdl(k_true_residual<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, rbuf(), FinTrue{ps});
         OTM_LAUNCH();
         return OTM_OK;
     }

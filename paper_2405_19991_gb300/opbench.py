@@ -27,6 +27,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--dtype", type=int, default=1, help="1 = FP32, 0 = FP64; precision for --op step (2 = mixed)")
+    ap.add_argument("--colour", type=int, default=8, help="--op gs: colour (0-7) or group pass 8 + g")
     args = ap.parse_args()
 
     import torch
@@ -55,7 +56,7 @@ def main():
         if args.op == "apply_K":
             otm.otm_op_apply_K(args.dtype, n, k, u, out, st.cuda_stream)
         elif args.op == "gs":
-            otm.otm_op_gs_colour(args.dtype, n, k, u, out, 0, st.cuda_stream)
+            otm.otm_op_gs_colour(args.dtype, n, k, u, out, args.colour, st.cuda_stream)
         elif args.op == "filter":
             otm.otm_op_filter_simp(args.dtype, n, 2.0, 3.0, 1.0, 1e-3, rho, out, out[N:], st.cuda_stream)
         elif args.op == "kappa_sens":

@@ -70,7 +70,7 @@ def test_macro_load(dtype, n):
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
-@pytest.mark.parametrize("n", [4, 5, 8, 13, 16, 32, 64, 96])
+@pytest.mark.parametrize("n", [4, 5, 8, 13, 16, 32, 64, 96, 128, 256])
 def test_apply_K(dtype, n):
     otm = _otm()
     k = _k(n, 4)
@@ -78,11 +78,19 @@ def test_apply_K(dtype, n):
     t = _tdt(dtype)
     k_d, u_d, o_d = dev(k, t), dev(u.ravel(), t), empty(3 * n ** 3, t)
     otm.otm_op_apply_K(dtype, n, k_d, u_d, o_d)
-    ref = fem.apply_operator(n, host(k_d), host(u_d).reshape(3, -1)).ravel()
+    if n <= 128:
+        ref = fem.apply_operator(n, host(k_d), host(u_d).reshape(3, -1)).ravel()
+        got = host(o_d)
+    else:   # sampled nodes, computed one by one
+        nodes = np.random.default_rng(n).choice(n ** 3, 400, replace=False)
+        ref = fem.apply_operator_at(n, host(k_d), host(u_d).reshape(3, -1), nodes).ravel()
+        got = host(o_d).reshape(3, -1)[:, nodes].ravel()
     # FP32: about 40 rounded operations on terms bounded by 16/3 kmax umax
     scale = np.max(k) * np.max(np.abs(u)) * 16.0 / 3.0
     tol = 1e-13 * scale if dtype == 0 else 40 * 6e-8 * scale
-    assert np.max(np.abs(host(o_d) - ref)) <= tol
+    if n <= 128:
+        got = host(o_d)
+    assert np.max(np.abs(got - ref)) <= tol
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
@@ -162,3 +170,49 @@ def test_oc_update(dtype, case, n):
         assert got.mean() <= vstar + 1e-6
         if np.isfinite(lam_ref) and lam_ref > 0:
             assert abs(lam - lam_ref) <= 1e-4 * lam_ref
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [8, 16, 32])
+def test_gs_group_pass(dtype, n):
+    """Colour 8 + g relaxes colours 2g and 2g+1 together, as the solver does."""
+    otm = _otm()
+    k = _k(n, 19)
+    rng = np.random.default_rng(20)
+    f = rng.standard_normal((3, n ** 3))
+    T = rng.standard_normal((3, n ** 3))
+    t = _tdt(dtype)
+    k_d, f_d, T_d = dev(k, t), dev(f.ravel(), t), dev(T.ravel(), t)
+    K = fem.assemble(n, host(k_d))
+    Tref = host(T_d).reshape(3, -1)
+    fh = host(f_d).reshape(3, -1)
+    for g in (0, 3, 1, 2):
+        otm.otm_op_gs_colour(dtype, n, k_d, f_d, T_d, 8 + g)
+        nodes = np.concatenate([fem.colour_nodes(n, 2 * g), fem.colour_nodes(n, 2 * g + 1)])
+        for i in range(3):
+            Tref[i] = fem.gauss_seidel_pass(K, fh[i], Tref[i], nodes)
+        tol = 1e-11 if dtype == 0 else 2e-4 * max(1.0, np.max(np.abs(Tref)))
+        assert np.max(np.abs(host(T_d).reshape(3, -1) - Tref)) <= tol, g
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_gs_group_pass_full_size_sampled(n):
+    """The group pass the solver runs, at the benchmark sizes, checked node by node."""
+    otm = _otm()
+    import torch
+    k = _k(n, 21)
+    rng = np.random.default_rng(22)
+    f = rng.standard_normal((3, n ** 3)).astype(np.float32)
+    T = rng.standard_normal((3, n ** 3)).astype(np.float32)
+    k_d, f_d, T_d = dev(k, torch.float32), dev(f.ravel(), torch.float32), dev(T.ravel(), torch.float32)
+    kh, fh, Th = host(k_d), host(f_d).reshape(3, -1), host(T_d).reshape(3, -1)
+    g = 2
+    otm.otm_op_gs_colour(1, n, k_d, f_d, T_d, 8 + g)
+    got = host(T_d).reshape(3, -1)
+    nodes = np.concatenate([fem.colour_nodes(n, 2 * g), fem.colour_nodes(n, 2 * g + 1)])
+    sample = rng.choice(nodes, 300, replace=False)
+    ref = fem.gauss_seidel_at(n, kh, fh, Th, sample)
+    assert np.max(np.abs(got[:, sample] - ref)) <= 2e-4 * max(1.0, np.max(np.abs(ref)))
+    # nodes of the other groups are untouched
+    other = np.setdiff1d(rng.choice(n ** 3, 2000, replace=False), nodes)
+    assert np.array_equal(got[:, other], Th[:, other])

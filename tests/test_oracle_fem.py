@@ -326,3 +326,15 @@ def test_x_parity_pairs_are_uncoupled():
     for c in range(0, 8, 2):
         a, b = fem.colour_nodes(n, c), fem.colour_nodes(n, c + 1)
         assert np.max(np.abs(K[np.ix_(a, b)])) < 1e-15
+
+
+def test_gauss_seidel_at_matches_pass():
+    n = 6
+    k = _random_k(n, 18)
+    K = fem.assemble(n, k)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((1, n ** 3))
+    T = rng.standard_normal((1, n ** 3))
+    nodes = fem.colour_nodes(n, 5)
+    full = fem.gauss_seidel_pass(K, f[0], T[0], nodes)
+    assert np.allclose(fem.gauss_seidel_at(n, k, f, T, nodes)[0], full[nodes], atol=1e-12)
