@@ -65,7 +65,8 @@ enum {
 enum {
     OTM_WS_NONE = 0,    /* start from zero */
     OTM_WS_PREV = 1,    /* start from the previous design iteration's solution */
-    OTM_WS_LEARNED = 2  /* start from the learned predictor, falling back to the better of zero/previous */
+    OTM_WS_LEARNED = 2  /* candidates from the attached U-Net predictor (otm_set_predictor) and the
+                           previous solution; per load case the one with the smallest true residual */
 };
 
 /* Objective g(kappa^H, kappa*) (params.objective). */
@@ -133,9 +134,11 @@ typedef struct otm_step_info {
     int cg_iters[3];      /* PCG iterations per load case */
     int iteration;        /* design iteration index (0-based) of this report */
     double resid[3];      /* true relative residual per load case at exit */
-    float stage_ms[8];    /* filter+SIMP, load+coarse operators, solve, tensor+sensitivity, OC, -, -, total */
+    float stage_ms[8];    /* [1] warm-start prediction and choice (OTM_WS_LEARNED), [2] setup and solve,
+                             [4] tensor, sensitivity and OC update, [7] total; others 0 */
     int kernel_launches;  /* CUDA kernels this call launched (graph kernel nodes counted per execution) */
-    int reserved;
+    int ws_choice;        /* start chosen per load case i, 2 bits at 2i: 0 zero, 1 previous solution,
+                             2 predictor, 3 previous + predictor change (OTM_WS_LEARNED only) */
 } otm_step_info;
 
 /* State of Alg. 1's adaptive volume bound. */
@@ -319,6 +322,82 @@ OTM_API otm_status otm_op_oc_update(int dtype, int n, double vstar, double move,
                                     double damp, double rho_min, const void* rho,
                                     const void* s, void* rho_new, double* lambda_out,
                                     void* stream);
+
+
+/* ------------------------------------------------- learned warm start (U-Net)
+ *
+ * A periodic 3-D convolutional U-Net maps the filtered density rho_f (n^3) to
+ * three fields y (3 n^3, load case major) that, times a scale, predict the
+ * solutions chi of the three load cases (Sec. 2.4).  The paper has no such
+ * network; it is the learned initial guess of the homogenization solve.
+ *
+ * Architecture (widths c0..c3, grid n, n % 8 == 0):
+ *   E0 = B(1 -> c0)(x) at n,  E1 = B(c0 -> c1)(pool E0) at n/2,
+ *   E2 = B(c1 -> c2)(pool E1) at n/4,  E3 = B(c2 -> c3)(pool E2) at n/8,
+ *   D2 = B(c3 + c2 -> c2)(cat(up E3, E2)),  D1 = B(c2 + c1 -> c1)(cat(up D2, E1)),
+ *   D0 = B(c1 + c0 -> c0)(cat(up D1, E0)),  y = H D0 + h (1x1 convolution c0 -> 3),
+ * B(a -> b) = relu(conv(relu(conv(., a -> b)), b -> b)) with 3x3x3 circular
+ * convolutions with bias, pool the 2x2x2 average, up the nearest x2 copy.
+ *
+ * Parameters are one FP32 vector, per block in the order E0 E1 E2 E3 D2 D1 D0:
+ * W1 [27][a][b], b1 [b], W2 [27][b][b], b2 [b]; then H [c0][3], h [3].  A
+ * convolution weight W[t][ci][co] multiplies input channel ci at offset
+ * (dx, dy, dz) = (t % 3 - 1, (t / 3) % 3 - 1, t / 9 - 1) for output channel co.
+ * Computation: BF16 activations and weights, FP32 accumulation (tensor cores),
+ * FP32 master parameters, Adam with beta = (0.9, 0.999), eps = 1e-8.
+ *
+ * Calls taking a stream order their work on it (NULL = the stream given at
+ * creation) and return after it completes.  x, y, target and grads are device
+ * pointers on the network's device.  One network serves one caller at a time:
+ * its activations are held inside it. */
+typedef struct otm_unet otm_unet;
+
+/* Create a network for grid n (8 <= n <= 512, n % 8 == 0) with widths
+ * c0..c3 (each a multiple of 16 in [16, 256]) and He-normal initial weights
+ * drawn from a counter-based generator seeded by `seed`.  Allocates its
+ * parameters, Adam moments and activation buffers on the current device.
+ * OTM_EINVAL on bad sizes, OTM_ENOMEM when the buffers do not fit. */
+OTM_API otm_status otm_unet_create(int n, const int widths[4], uint64_t seed, void* stream,
+                                   otm_unet** out);
+OTM_API otm_status otm_unet_destroy(otm_unet* u);
+/* Number of FP32 parameters. */
+OTM_API otm_status otm_unet_param_count(const otm_unet* u, size_t* count);
+/* Copy the parameter vector out of / into the network (count = param_count;
+ * host or device memory per on_device).  set resets the Adam moments. */
+OTM_API otm_status otm_unet_get_params(otm_unet* u, float* p, int on_device);
+OTM_API otm_status otm_unet_set_params(otm_unet* u, const float* p, int on_device);
+/* y = net(x): x n^3 FP32, y 3 n^3 FP32 (device). */
+OTM_API otm_status otm_unet_forward(otm_unet* u, const float* x, float* y, void* stream);
+/* Gradient of sum(dy * y) with respect to every parameter, for the x of the
+ * last otm_unet_forward: dy 3 n^3 (device), grads param_count FP32 (device,
+ * may be NULL: the gradient then stays inside the network). */
+OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads, void* stream);
+/* One Adam step on L = mean((net(x) - target)^2) over the 3 n^3 entries:
+ * forward, loss, backward, update.  *loss (host, may be NULL) = L before
+ * the update. */
+OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target, double lr,
+                                       double* loss, void* stream);
+/* L = mean((net(x) - target)^2) without an update. */
+OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target, double* loss,
+                                 void* stream);
+/* Attach a network (grid n equal to the context's) as the predictor used by
+ * OTM_WS_LEARNED, with chi_i ~ scale * y_i; NULL detaches.  The context
+ * borrows the network: keep it alive while attached, and do not run other
+ * calls on it concurrently with the context's steps. */
+OTM_API otm_status otm_set_predictor(otm_ctx* ctx, otm_unet* u, double scale);
+
+/* One 3x3x3 circular convolution of the network (operator-level test entry):
+ * out[v][co] = act(bias[co] + sum_t sum_ci w[t][ci][co] in[v + d_t][ci]) on an
+ * n^3 grid, BF16 in [n^3][cin], w [27][cin][cout], out [n^3][cout] (channels
+ * innermost), bias FP32 (may be NULL), act = relu when relu != 0.  cin and
+ * cout multiples of 16, <= 512.  Device pointers. */
+OTM_API otm_status otm_op_conv3(int n, int cin, int cout, const void* in, const void* w,
+                                const float* bias, int relu, void* out, void* stream);
+/* Its weight and bias gradients for output gradient g [n^3][cout] (BF16):
+ * dw [27][cin][cout] += sum_v in[v + d_t][ci] g[v][co], db[co] += sum_v g[v][co]
+ * (FP32, accumulated into; db may be NULL). */
+OTM_API otm_status otm_op_conv3_wgrad(int n, int cin, int cout, const void* in, const void* g,
+                                      float* dw, float* db, void* stream);
 
 #ifdef __cplusplus
 }

@@ -410,10 +410,10 @@ struct FinTrue {
     }
 };
 
-template <class R>
+template <class R, class Fin = FinTrue>
 __global__ void __launch_bounds__(256)
 k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const R* __restrict__ xl,
-                const R* __restrict__ f, RedBuf rb, FinTrue fin) {
+                const R* __restrict__ f, RedBuf rb, Fin fin) {
     pdl_enter();
     using C = typename St<R>::C;
     const size_t N = (size_t)n * n * n;

@@ -275,6 +275,11 @@ otm_status otm_set_state(otm_ctx* ctx, const void* buf, size_t len) {
     return ctx->s->set_state(buf, len);
 }
 
+otm_status otm_set_predictor(otm_ctx* ctx, otm_unet* u, double scale) {
+    CTX_CHECK(ctx);
+    return ctx->s->set_predictor(u, scale);
+}
+
 const char* otm_last_error(const otm_ctx* ctx) {
     if (ctx && ctx->s) return ctx->s->err.c_str();
     return g_err.c_str();

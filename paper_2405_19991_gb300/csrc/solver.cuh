@@ -15,7 +15,9 @@
 #include "kernels_tiled.cuh"
 #include "kernels_cluster.cuh"
 #include "kernels_warprow.cuh"
+#include "kernels_ws.cuh"
 #include "otm_internal.cuh"
+#include "unet_api.cuh"
 
 namespace otm {
 
@@ -33,6 +35,7 @@ struct SolverBase {
     virtual size_t state_size() const = 0;
     virtual otm_status get_state(void* buf) = 0;
     virtual otm_status set_state(const void* buf, size_t len) = 0;
+    virtual otm_status set_predictor(otm_unet* u, double scale) = 0;
     std::string err;
     otm_params prm;
     cudaStream_t stream = nullptr;
@@ -160,6 +163,16 @@ class Solver : public SolverBase {
     OcP op;
     bool have_prev = false;
     int iteration = 0;
+    // learned warm start (OTM_WS_LEARNED with an attached network)
+    otm_unet* predictor = nullptr;
+    double pred_scale = 1.0;
+    float* ynet[2] = {};
+    int ycur = 0;
+    bool have_y = false;
+    R *xc_net = nullptr, *xc_delta = nullptr;
+    PcgScalars* ps_c = nullptr;
+    WsState* ws = nullptr;
+    WsState* ws_h = nullptr;
     GovState gov_init;
     cudaEvent_t ev[8] = {};
 
@@ -170,8 +183,10 @@ class Solver : public SolverBase {
         if (gx_pass) cudaGraphExecDestroy(gx_pass);
         if (gx_tail) cudaGraphExecDestroy(gx_tail);
         if (cap2) cudaStreamDestroy(cap2);
+        if (gx_setup) cudaGraphExecDestroy(gx_setup);
+        if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
         void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
-                        partials, counter, ps, ds, stage_f};
+                        partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
         if (k_vc && (void*)k_vc != (void*)kf) cudaFree(k_vc);
@@ -183,6 +198,7 @@ class Solver : public SolverBase {
             if (Kel[l]) cudaFree(Kel[l]);
         }
         if (ps_h) cudaFreeHost(ps_h);
+        if (ws_h) cudaFreeHost(ws_h);
         if (ds_h) cudaFreeHost(ds_h);
         for (auto& e : ev)
             if (e) cudaEventDestroy(e);
@@ -575,7 +591,8 @@ class Solver : public SolverBase {
     bool use_graphs = true;
     cudaStream_t cap2 = nullptr;
     cudaGraphExec_t gx_first = nullptr, gx_pass = nullptr, gx_tail = nullptr;
-    long long nlg_first = 0, nlg_pass = 0, nlg_body = 0, nlg_tail = 0;
+    cudaGraphExec_t gx_setup = nullptr, gx_solve0 = nullptr;   // learned warm start: setup, then solve
+    long long nlg_first = 0, nlg_pass = 0, nlg_body = 0, nlg_tail = 0, nlg_setup = 0, nlg_solve0 = 0;
     R* rho_save = nullptr;
 
     // one PCG iteration: z = V(r), beta, p, q = K p, alpha, x and r updates
@@ -750,10 +767,13 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         return st;
     }
 
-    otm_status capture_tail() {
+    otm_status capture_tail() { return capture_seq(false, &gx_tail, &nlg_tail); }
+
+    // Capture the design tail (setup = false) or the solve setup (true).
+    otm_status capture_seq(bool setup, cudaGraphExec_t* out, long long* count) {
         const long long n0 = nl_;
         OTM_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
-        otm_status st = enqueue_tail();
+        otm_status st = setup ? enqueue_setup() : enqueue_tail();
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(stream, &g);
         if (st != OTM_OK) {
@@ -766,9 +786,9 @@ if (tz_ > 0 && std::is_same<R, float>::value)
             nl_ = n0;
             return OTM_ECUDA;
         }
-        e = cudaGraphInstantiate(&gx_tail, g, 0);
+        e = cudaGraphInstantiate(out, g, 0);
         cudaGraphDestroy(g);
-        nlg_tail = nl_ - n0;
+        *count = nl_ - n0;
         nl_ = n0;
         if (e != cudaSuccess) {
             err = std::string("cudaGraphInstantiate (tail): ") + cudaGetErrorString(e);
@@ -796,14 +816,43 @@ if (tz_ > 0 && std::is_same<R, float>::value)
 
     // Setup + solve.  Returns OTM_OK / OTM_ENOCONV; fills iterations and the
     // checked residuals.
-    otm_status setup_and_solve(bool warm, otm_step_info* info) {
+    otm_status setup_and_solve(bool warm, otm_step_info* info, bool learned = false) {
         if (!warm) {
             OTM_CU(cudaMemsetAsync(x, 0, 3 * N * sizeof(R), stream));
             if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));
         }
         int iters[3] = {0, 0, 0};
         ps_h->total = 0;
-        if (use_graphs) {
+        if (learned) {
+            if (use_graphs) {
+                OTM_TRY(ensure_graphs());
+                if (!gx_setup) OTM_TRY(capture_seq(true, &gx_setup, &nlg_setup));
+                if (!gx_solve0) {
+                    long long fixed = 0;
+                    const long long body = nlg_body;
+                    OTM_TRY(capture_pass(false, 0, &gx_solve0, &fixed));
+                    nlg_solve0 = fixed;
+                    nlg_body = body;
+                }
+                OTM_CU(cudaGraphLaunch(gx_setup, stream));
+                nl_ += nlg_setup;
+            } else {
+                OTM_TRY(enqueue_setup());
+            }
+            OTM_CU(cudaEventRecord(ev[1], stream));
+            OTM_TRY(predict_start(warm));
+            OTM_CU(cudaEventRecord(ev[3], stream));
+            if (use_graphs) OTM_TRY(launch_pass(gx_solve0, nlg_solve0));
+            else OTM_TRY(pass_direct(0));
+            if (info) {
+                int code = 0;
+                for (int i = 0; i < 3; ++i) code |= (ws_h->choice[i] & 3) << (2 * i);
+                info->ws_choice = code;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[1], ev[3]);
+                info->stage_ms[1] = ms;
+            }
+        } else if (use_graphs) {
             OTM_TRY(ensure_graphs());
             OTM_TRY(launch_pass(gx_first, nlg_first));
         } else {
@@ -844,6 +893,70 @@ if (tz_ > 0 && std::is_same<R, float>::value)
             err = "PCG did not reach cg_tol (cg_maxit reached or the residual stagnated)";
             return OTM_ENOCONV;
         }
+        return OTM_OK;
+    }
+
+    // Learned warm start: predict from rho_f, score the candidates by their
+    // true residuals and install the best per load case into (x, xl).
+    otm_status predict_start(bool have_prev_x) {
+        float* y = ynet[ycur];
+        const float* yp = ynet[ycur ^ 1];
+        const long long u0 = unet_launches();
+        OTM_TRY(unet_predict(predictor, rho_f, std::is_same<R, double>::value, y, stream));
+        nl_ += unet_launches() - u0;
+        const bool delta = have_prev_x && have_y;
+        RedBuf rb = rbuf();
+        auto score = [&](const R* xh, const R* xlo, int slot) -> otm_status {
+            ++nl_;
+            launch_pdl(k_true_residual<R, FinStore>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, xh, xlo, f, rb,
+                       FinStore{&ws->cand[slot][0]});
+            OTM_LAUNCH();
+            return OTM_OK;
+        };
+        auto cand = [&](int mode, R* xc) -> otm_status {
+            nl_ += 3;
+            k_ws_cand<R><<<grid(3 * N), 256, 0, stream>>>(N, mode, x, xl, y, yp, pred_scale, xc);
+            launch_pdl(k_sum3<R>, grid(N), 256, stream, N, (const R*)xc, rb, FinMean{ps_c, 1.0 / (double)N});
+            launch_pdl(k_sub_mean<R>, grid(N), 256, stream, N, xc, (const PcgScalars*)ps_c);
+            OTM_LAUNCH();
+            return score(xc, nullptr, mode);
+        };
+        OTM_TRY(cand(kWsNet, xc_net));
+        if (have_prev_x) OTM_TRY(score(x, xl, kWsPrev));
+        if (delta) OTM_TRY(cand(kWsDelta, xc_delta));
+        nl_ += 2;
+        k_ws_decide<<<1, 32, 0, stream>>>(ws, have_prev_x ? 1 : 0, delta ? 1 : 0);
+        k_ws_take<R><<<grid(3 * N), 256, 0, stream>>>(N, ws, xc_net, xc_delta, x, xl);
+        OTM_LAUNCH();
+        OTM_CU(cudaMemcpyAsync(ws_h, ws, sizeof(WsState), cudaMemcpyDeviceToHost, stream));
+        ycur ^= 1;
+        have_y = true;
+        return OTM_OK;
+    }
+
+    otm_status set_predictor(otm_unet* u, double scale) override {
+        if (u && unet_grid(u) != n) {
+            err = "otm_set_predictor: the network's grid differs from the context's n";
+            return OTM_EINVAL;
+        }
+        if (u && !(std::isfinite(scale) && scale != 0.0)) {
+            err = "otm_set_predictor: scale must be finite and nonzero";
+            return OTM_EINVAL;
+        }
+        if (u && !ws) {
+            OTM_TRY(alloc(ynet[0], 3 * N));
+            OTM_TRY(alloc(ynet[1], 3 * N));
+            OTM_TRY(alloc(xc_net, 3 * N));
+            OTM_TRY(alloc(xc_delta, 3 * N));
+            OTM_TRY(alloc(ps_c, 1));
+            OTM_TRY(alloc(ws, 1));
+            OTM_CU(cudaMallocHost((void**)&ws_h, sizeof(WsState)));
+            memset(ws_h, 0, sizeof(WsState));
+        }
+        OTM_CU(cudaStreamSynchronize(stream));
+        predictor = u;
+        pred_scale = scale;
+        have_y = false;
         return OTM_OK;
     }
 
@@ -921,7 +1034,8 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         const long long nl0 = nl_;
         OTM_CU(cudaEventRecord(ev[0], stream));
         const bool warm = have_prev && prm.warm_start != OTM_WS_NONE;
-        otm_status sst = setup_and_solve(warm, &loc);
+        const bool learned = prm.warm_start == OTM_WS_LEARNED && predictor != nullptr;
+        otm_status sst = setup_and_solve(warm, &loc, learned);
         if (sst != OTM_OK && sst != OTM_ENOCONV) return sst;
         have_prev = true;
         OTM_CU(cudaEventRecord(ev[2], stream));
@@ -1003,6 +1117,7 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         OTM_CU(cudaStreamSynchronize(stream));
         iteration = h.iteration;
         have_prev = h.have_prev != 0;
+        have_y = false;
         return OTM_OK;
     }
 

@@ -1,0 +1,403 @@
+// Kernels of the periodic 3-D convolutional U-Net used as the learned warm
+// start of the homogenization solve (a predictor of the three corrector
+// fields from the filtered density).  Activations are BF16, stored voxel-major
+// with channels innermost ([voxel][C], C a multiple of 16); weights of a
+// 3x3x3 convolution are [27][Cin][Cout] (tap t = (dz+1)*9 + (dy+1)*3 + dx+1,
+// Cout innermost); accumulation is FP32.
+//
+// The 3x3x3 circular convolution is an implicit GEMM (M = voxels,
+// N = output channels, K = 27 taps x input channels) on the BF16 tensor
+// cores with mma.sync m16n8k16 and ldmatrix fragment loads.  Its gradient
+// with respect to the input is the same convolution with flipped taps and
+// transposed weights; the weight gradient is a GEMM that reduces over voxels.
+#pragma once
+#include "otm_internal.cuh"
+
+namespace otm {
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ void ldsm_x4(unsigned (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned (&r)[4], const void* p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+// c += a (16x16, row) * b (16x8, col), BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int tap_dz(int t) { return t / 9 - 1; }
+__device__ __forceinline__ int tap_dy(int t) { return (t / 3) % 3 - 1; }
+__device__ __forceinline__ int tap_dx(int t) { return t % 3 - 1; }
+
+constexpr int kCM = 64;   // voxels per CTA of the convolution
+
+// out[v][co] = act(b[co] + sum_t sum_ci W[t][ci][co] in[v + d_t][ci]).
+// Grid (N / 64, Cout / BN), 128 threads; warp w computes voxels 16w..16w+15.
+// bias may be null; RELU applies max(0, .).  Rows past the last voxel (the
+// ragged last tile) load voxel N-1 and are not stored.
+template <int BN, bool RELU>
+__global__ void __launch_bounds__(128)
+k_conv3(int n, int Cin, int Cout, const bf16* __restrict__ in, const bf16* __restrict__ W,
+        const float* __restrict__ bias, bf16* __restrict__ out) {
+    pdl_enter();
+    const size_t N = (size_t)n * n * n;
+    __shared__ __align__(16) bf16 As[kCM][24];
+    __shared__ __align__(16) bf16 Bs[16][BN + 8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t m0 = (size_t)blockIdx.x * kCM;
+    const int n0 = blockIdx.y * BN;
+    const int am = tid >> 1, ah = tid & 1;                 // A: voxel am, channels ah*8..ah*8+7
+    const size_t v = m0 + am < N ? m0 + am : N - 1;
+    const int vx = (int)(v % n), vy = (int)((v / n) % n), vz = (int)(v / ((size_t)n * n));
+    constexpr int BCH = BN / 8;                            // 16-byte chunks per B row
+    const bool bload = tid < 16 * BCH;
+    const int bk = tid / BCH, bc = (tid % BCH) * 8;
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    const int kch = Cin / 16;
+    for (int t = 0; t < 27; ++t) {
+        const size_t nb = (size_t)wrapd(vx, tap_dx(t), n) +
+                          (size_t)n * ((size_t)wrapd(vy, tap_dy(t), n) + (size_t)n * wrapd(vz, tap_dz(t), n));
+        for (int c = 0; c < kch; ++c) {
+            const uint4 a = *reinterpret_cast<const uint4*>(in + nb * Cin + c * 16 + ah * 8);
+            uint4 b = make_uint4(0, 0, 0, 0);
+            if (bload) b = *reinterpret_cast<const uint4*>(W + ((size_t)t * Cin + c * 16 + bk) * Cout + n0 + bc);
+            __syncthreads();
+            *reinterpret_cast<uint4*>(&As[am][ah * 8]) = a;
+            if (bload) *reinterpret_cast<uint4*>(&Bs[bk][bc]) = b;
+            __syncthreads();
+            unsigned af[4];
+            ldsm_x4(af, &As[warp * 16 + (lane & 15)][(lane >> 4) * 8]);
+#pragma unroll
+            for (int j = 0; j < BN / 8; j += 2) {
+                unsigned bf[4];
+                ldsm_x4_t(bf, &Bs[lane & 15][j * 8 + (lane >> 4) * 8]);
+                mma_bf16(acc[j], af, bf[0], bf[1]);
+                mma_bf16(acc[j + 1], af, bf[2], bf[3]);
+            }
+        }
+    }
+    const int row = warp * 16 + (lane >> 2);
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+        const int co = n0 + j * 8 + (lane & 3) * 2;
+        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float y0 = acc[j][2 * h] + b0, y1 = acc[j][2 * h + 1] + b1;
+            if (RELU) {
+                y0 = fmaxf(y0, 0.f);
+                y1 = fmaxf(y1, 0.f);
+            }
+            const size_t m = m0 + row + 8 * h;
+            if (m < N) *reinterpret_cast<__nv_bfloat162*>(out + m * Cout + co) = __floats2bfloat162_rn(y0, y1);
+        }
+    }
+}
+
+// dW[t][ci][co] += sum_v in[v + d_t][ci] * g[v][co] over a chunk of voxels
+// (input stored with Cin channels, of which the first Ca are real: dW is
+// [27][Ca][Cout]),
+// and (blockIdx.z == 0 only) db[co] += sum_v g[v][co].  Grid
+// (chunks, Cin / 16, 27 * (Cout / BN)), 128 threads; each warp reduces 16
+// voxels per step, warps are combined in shared memory, and the CTA adds its
+// partial to dW with FP32 atomics.
+template <int BN>
+__global__ void __launch_bounds__(128)
+k_conv3_dw(int n, int Cin, int Ca, int Cout, int chunk, const bf16* __restrict__ in, const bf16* __restrict__ g,
+           float* __restrict__ dW, float* __restrict__ db) {
+    pdl_enter();
+    __shared__ __align__(16) bf16 As[64][24];       // [voxel][ci]
+    __shared__ __align__(16) bf16 Bs[64][BN + 8];   // [voxel][co]
+    __shared__ float red[4][16][BN];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t N = (size_t)n * n * n;
+    const int ci0 = blockIdx.y * 16;
+    const int nbt = Cout / BN;
+    const int t = blockIdx.z / nbt, n0 = (blockIdx.z % nbt) * BN;
+    const size_t v0 = (size_t)blockIdx.x * chunk;
+    size_t v1 = v0 + chunk;
+    if (v1 > N) v1 = N;
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    float bsum = 0.f;
+    constexpr int BCH = BN / 8;
+    for (size_t vb = v0; vb < v1; vb += 64) {
+        // A: 64 voxels x 16 channels of the shifted input (2 chunks of 8 per voxel)
+        {
+            const int am = tid >> 1, ah = tid & 1;
+            const size_t v = vb + am;
+            uint4 a = make_uint4(0, 0, 0, 0);
+            if (v < v1) {
+                const int vx = (int)(v % n), vy = (int)((v / n) % n), vz = (int)(v / ((size_t)n * n));
+                const size_t nb = (size_t)wrapd(vx, tap_dx(t), n) +
+                                  (size_t)n * ((size_t)wrapd(vy, tap_dy(t), n) + (size_t)n * wrapd(vz, tap_dz(t), n));
+                a = *reinterpret_cast<const uint4*>(in + nb * Cin + ci0 + ah * 8);
+            }
+            *reinterpret_cast<uint4*>(&As[am][ah * 8]) = a;
+        }
+        // B: 64 voxels x BN channels of the output gradient
+        for (int e = tid; e < 64 * BCH; e += 128) {
+            const int bv = e / BCH, bc = (e % BCH) * 8;
+            const size_t v = vb + bv;
+            uint4 b = make_uint4(0, 0, 0, 0);
+            if (v < v1) b = *reinterpret_cast<const uint4*>(g + v * Cout + n0 + bc);
+            *reinterpret_cast<uint4*>(&Bs[bv][bc]) = b;
+        }
+        __syncthreads();
+        // warp w reduces voxels 16w..16w+15: A^T fragment via transposed loads
+        unsigned af[4];
+        ldsm_x4_t(af, &As[warp * 16 + (lane & 7) + ((lane >> 4) << 3)][((lane >> 3) & 1) * 8]);
+#pragma unroll
+        for (int j = 0; j < BN / 8; j += 2) {
+            unsigned bf[4];
+            ldsm_x4_t(bf, &Bs[warp * 16 + (lane & 15)][j * 8 + (lane >> 4) * 8]);
+            mma_bf16(acc[j], af, bf[0], bf[1]);
+            mma_bf16(acc[j + 1], af, bf[2], bf[3]);
+        }
+        if (db && blockIdx.y == 0 && t == 0 && tid < BN) {
+            for (int r = 0; r < 64 && vb + r < v1; ++r) bsum += __bfloat162float(Bs[r][tid]);
+        }
+        __syncthreads();
+    }
+    // combine the four warps
+#pragma unroll
+    for (int j = 0; j < BN / 8; ++j) {
+        const int r0 = lane >> 2, c0 = j * 8 + (lane & 3) * 2;
+        red[warp][r0][c0] = acc[j][0];
+        red[warp][r0][c0 + 1] = acc[j][1];
+        red[warp][r0 + 8][c0] = acc[j][2];
+        red[warp][r0 + 8][c0 + 1] = acc[j][3];
+    }
+    __syncthreads();
+    for (int e = tid; e < 16 * BN; e += 128) {
+        const int r = e / BN, c = e % BN;
+        const float s = red[0][r][c] + red[1][r][c] + red[2][r][c] + red[3][r][c];
+        if (ci0 + r < Ca) atomicAdd(dW + ((size_t)t * Ca + ci0 + r) * Cout + n0 + c, s);
+    }
+    if (db && blockIdx.y == 0 && t == 0 && tid < BN) atomicAdd(db + n0 + tid, bsum);
+}
+
+// g = g * (y > 0): ReLU backward, y the block output.
+static __global__ void k_relu_mask(size_t count, bf16* __restrict__ g, const bf16* __restrict__ y) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(y[i]) > 0.f)) g[i] = __float2bfloat16_rn(0.f);
+}
+
+// 2x2x2 average pooling, [8 Nc][C] -> [Nc][C] (coarse grid nc per side).
+static __global__ void k_pool(int nc, int C, const bf16* __restrict__ in, bf16* __restrict__ out) {
+    const size_t Nc = (size_t)nc * nc * nc;
+    const int nf = 2 * nc;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nc * C; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t V = e / C;
+        const int c = (int)(e % C);
+        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((size_t)nc * nc));
+        float s = 0.f;
+        for (int q = 0; q < 8; ++q) {
+            const size_t f = (size_t)(2 * X + (q & 1)) + (size_t)nf * ((2 * Y + ((q >> 1) & 1)) + (size_t)nf * (2 * Z + (q >> 2)));
+            s += __bfloat162float(in[f * C + c]);
+        }
+        out[e] = __float2bfloat16_rn(0.125f * s);
+    }
+}
+
+// din[v][c] += dout[v / 2][c] / 8 (adjoint of the pooling), fine grid nf.
+static __global__ void k_pool_back_add(int nf, int C, const bf16* __restrict__ dout, bf16* __restrict__ din) {
+    const size_t Nf = (size_t)nf * nf * nf;
+    const int nc = nf / 2;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * C; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = e / C;
+        const int c = (int)(e % C);
+        const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
+        const size_t V = (size_t)(x >> 1) + (size_t)nc * ((y >> 1) + (size_t)nc * (z >> 1));
+        din[e] = __float2bfloat16_rn(__bfloat162float(din[e]) + 0.125f * __bfloat162float(dout[V * C + c]));
+    }
+}
+
+// cat[v][0..Cu) = up(coarse)[v], cat[v][Cu..Cu+Cs) = skip[v]  (fine grid nf)
+static __global__ void k_up_cat(int nf, int Cu, int Cs, const bf16* __restrict__ coarse, const bf16* __restrict__ skip,
+                         bf16* __restrict__ cat) {
+    const size_t Nf = (size_t)nf * nf * nf;
+    const int nc = nf / 2;
+    const int Ct = Cu + Cs;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * Ct; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = e / Ct;
+        const int c = (int)(e % Ct);
+        if (c < Cu) {
+            const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
+            const size_t V = (size_t)(x >> 1) + (size_t)nc * ((y >> 1) + (size_t)nc * (z >> 1));
+            cat[e] = coarse[V * Cu + c];
+        } else {
+            cat[e] = skip[v * Cs + (c - Cu)];
+        }
+    }
+}
+
+// Split the gradient of a concatenation: dcoarse[V][c] = sum over the 8
+// children of dcat[v][c] (c < Cu) (the adjoint of the upsampling), and
+// dskip[v][c] = dcat[v][Cu + c].
+static __global__ void k_up_cat_back(int nf, int Cu, int Cs, const bf16* __restrict__ dcat, bf16* __restrict__ dcoarse,
+                              bf16* __restrict__ dskip) {
+    const int nc = nf / 2;
+    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    const int Ct = Cu + Cs;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nc * Cu; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t V = e / Cu;
+        const int c = (int)(e % Cu);
+        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((size_t)nc * nc));
+        float s = 0.f;
+        for (int q = 0; q < 8; ++q) {
+            const size_t f = (size_t)(2 * X + (q & 1)) + (size_t)nf * ((2 * Y + ((q >> 1) & 1)) + (size_t)nf * (2 * Z + (q >> 2)));
+            s += __bfloat162float(dcat[f * Ct + c]);
+        }
+        dcoarse[e] = __float2bfloat16_rn(s);
+    }
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * Cs; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = e / Cs;
+        const int c = (int)(e % Cs);
+        dskip[e] = dcat[v * Ct + Cu + c];
+    }
+}
+
+// Input layer: x[v][0] = rho[v], channels 1..15 zero (Cin padded to 16).
+template <class T>
+__global__ void k_input16(size_t N, const T* __restrict__ rho, bf16* __restrict__ x) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+        uint4 z = make_uint4(0, 0, 0, 0);
+        __nv_bfloat162 a = __floats2bfloat162_rn((float)rho[v], 0.f);
+        z.x = *reinterpret_cast<unsigned*>(&a);
+        reinterpret_cast<uint4*>(x + v * 16)[0] = z;
+        reinterpret_cast<uint4*>(x + v * 16)[1] = make_uint4(0, 0, 0, 0);
+    }
+}
+
+// Head: y[j][v] = b[j] + sum_c d[v][c] H[c][j], j < 3 (FP32 out, [3][N]).
+static __global__ void k_head(size_t N, int C, const bf16* __restrict__ d, const float* __restrict__ H,
+                       const float* __restrict__ b, float* __restrict__ y) {
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+        float a0 = b[0], a1 = b[1], a2 = b[2];
+        for (int c = 0; c < C; ++c) {
+            const float dv = __bfloat162float(d[v * C + c]);
+            a0 += dv * H[c * 3 + 0];
+            a1 += dv * H[c * 3 + 1];
+            a2 += dv * H[c * 3 + 2];
+        }
+        y[v] = a0;
+        y[N + v] = a1;
+        y[2 * N + v] = a2;
+    }
+}
+
+// Head backward: dd[v][c] = sum_j dy[j][v] H[c][j] (written), and the
+// sums dH[c][j] += sum_v d[v][c] dy[j][v], db[j] += sum_v dy[j][v]
+// (per-thread partials over 16-channel slices, warp and block sums in shared
+// memory, then FP32 atomics).  C <= 256, a multiple of 16.
+static __global__ void __launch_bounds__(256)
+k_head_back(size_t N, int C, const bf16* __restrict__ d, const float* __restrict__ H,
+            const float* __restrict__ dy, bf16* __restrict__ dd, float* __restrict__ dH,
+            float* __restrict__ db) {
+    __shared__ float sH[256 * 3 + 3];
+    for (int i = threadIdx.x; i < C * 3 + 3; i += blockDim.x) sH[i] = 0.f;
+    __syncthreads();
+    for (int cb = 0; cb < C; cb += 16) {
+        float lH[48];
+        float lb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 48; ++i) lH[i] = 0.f;
+        for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+            const float g0 = dy[v], g1 = dy[N + v], g2 = dy[2 * N + v];
+            lb[0] += g0;
+            lb[1] += g1;
+            lb[2] += g2;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float dv = __bfloat162float(d[v * C + cb + c]);
+                lH[c * 3 + 0] += dv * g0;
+                lH[c * 3 + 1] += dv * g1;
+                lH[c * 3 + 2] += dv * g2;
+                const float* h = H + (cb + c) * 3;
+                dd[v * C + cb + c] = __float2bfloat16_rn(g0 * h[0] + g1 * h[1] + g2 * h[2]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 48; ++i) {
+            float w = lH[i];
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&sH[cb * 3 + i], w);
+        }
+        if (cb == 0) {
+            for (int j = 0; j < 3; ++j) {
+                float w = lb[j];
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                if ((threadIdx.x & 31) == 0) atomicAdd(&sH[C * 3 + j], w);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < C * 3; i += blockDim.x) atomicAdd(dH + i, sH[i]);
+    if (threadIdx.x < 3) atomicAdd(db + threadIdx.x, sH[C * 3 + threadIdx.x]);
+}
+
+// MSE loss against target t ([3][N]): dy = 2 (y - t) / (3N); loss partials
+// summed into *loss (FP64 atomics).
+static __global__ void k_mse(size_t M, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dy,
+                      double* __restrict__ loss) {
+    double s = 0.0;
+    const float sc = 2.0f / (float)M;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        s += (double)d * d;
+        dy[i] = sc * d;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (double)M);
+}
+
+// Adam update of the FP32 master parameters.
+static __global__ void k_adam(size_t P, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// Copy a [27][a][b] FP32 weight block into the BF16 compute layout
+// [27][ap][b] (ap >= a, padded channels zero), optionally also the flipped,
+// transposed form [27][b][ap] used by the input-gradient convolution
+// (tap t -> 26 - t).
+static __global__ void k_pack_w(int a, int ap, int b, const float* __restrict__ w, bf16* __restrict__ wc,
+                         bf16* __restrict__ wt) {
+    const size_t M = (size_t)27 * ap * b;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < M; e += (size_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / ((size_t)ap * b));
+        const int ci = (int)((e / b) % ap), co = (int)(e % b);
+        const float val = ci < a ? w[((size_t)t * a + ci) * b + co] : 0.f;
+        const bf16 bv = __float2bfloat16_rn(val);
+        wc[e] = bv;
+        if (wt) wt[((size_t)(26 - t) * b + co) * ap + ci] = bv;
+    }
+}
+
+}  // namespace nn
+}  // namespace otm

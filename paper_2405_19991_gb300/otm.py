@@ -63,7 +63,7 @@ class otm_step_info(C.Structure):
         ("resid", C.c_double * 3),
         ("stage_ms", C.c_float * 8),
         ("kernel_launches", C.c_int),
-        ("reserved", C.c_int),
+        ("ws_choice", C.c_int),
     ]
 
     def as_dict(self):
@@ -71,7 +71,8 @@ class otm_step_info(C.Structure):
                     mean_rhop=self.mean_rhop, vstar=self.vstar, lam=self.lambda_,
                     cg_iters=list(self.cg_iters), iteration=self.iteration,
                     resid=list(self.resid), stage_ms=list(self.stage_ms),
-                    kernel_launches=self.kernel_launches)
+                    kernel_launches=self.kernel_launches,
+                    ws_choice=[(self.ws_choice >> (2 * i)) & 3 for i in range(3)])
 
 
 class otm_governor_state(C.Structure):
@@ -118,6 +119,18 @@ def _load():
         "otm_op_kappa_sens": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_op_oc_update": [i, i, d, d, d, d, vp, vp, vp, P(C.c_double), vp],
         "otm_op_kappa_sens_noalloc": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
+        "otm_unet_create": [i, P(C.c_int), C.c_uint64, vp, P(vp)],
+        "otm_unet_destroy": [vp],
+        "otm_unet_param_count": [vp, P(sz)],
+        "otm_unet_get_params": [vp, vp, i],
+        "otm_unet_set_params": [vp, vp, i],
+        "otm_unet_forward": [vp, vp, vp, vp],
+        "otm_unet_backward": [vp, vp, vp, vp],
+        "otm_unet_train_step": [vp, vp, vp, d, P(d), vp],
+        "otm_unet_eval": [vp, vp, vp, P(d), vp],
+        "otm_set_predictor": [vp, vp, d],
+        "otm_op_conv3": [i, i, i, vp, vp, vp, i, vp, vp],
+        "otm_op_conv3_wgrad": [i, i, i, vp, vp, vp, vp, vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -137,7 +150,10 @@ EXPORTED = [
     "otm_run", "otm_design_batch", "otm_get_state", "otm_set_state", "otm_last_error",
     "otm_governor_init", "otm_governor_update", "otm_op_filter_simp", "otm_op_filter_transpose",
     "otm_op_macro_load", "otm_op_apply_K", "otm_op_gs_colour", "otm_op_kappa_sens",
-    "otm_op_oc_update", "otm_op_kappa_sens_noalloc",
+    "otm_op_oc_update", "otm_op_kappa_sens_noalloc", "otm_unet_create", "otm_unet_destroy",
+    "otm_unet_param_count", "otm_unet_get_params", "otm_unet_set_params", "otm_unet_forward",
+    "otm_unet_backward", "otm_unet_train_step", "otm_unet_eval", "otm_set_predictor", "otm_op_conv3",
+    "otm_op_conv3_wgrad",
 ]
 
 
@@ -305,3 +321,62 @@ def otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, rho, s, rho_new, stre
     check(lib.otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, _p(rho), _p(s), _p(rho_new),
                                C.byref(lam), stream))
     return lam.value
+
+
+# ------------------------------------------------------------ learned warm start
+
+def otm_unet_create(n, widths, seed=0, stream=None):
+    u = C.c_void_p()
+    w = (C.c_int * 4)(*[int(v) for v in widths])
+    check(lib.otm_unet_create(n, w, seed, stream, C.byref(u)))
+    return u
+
+
+def otm_unet_destroy(u):
+    return lib.otm_unet_destroy(u)
+
+
+def otm_unet_param_count(u) -> int:
+    c = C.c_size_t(0)
+    check(lib.otm_unet_param_count(u, C.byref(c)))
+    return c.value
+
+
+def otm_unet_get_params(u, ptr, on_device):
+    return check(lib.otm_unet_get_params(u, _p(ptr), int(on_device)))
+
+
+def otm_unet_set_params(u, ptr, on_device):
+    return check(lib.otm_unet_set_params(u, _p(ptr), int(on_device)))
+
+
+def otm_unet_forward(u, x, y, stream=None):
+    return check(lib.otm_unet_forward(u, _p(x), _p(y), stream))
+
+
+def otm_unet_backward(u, dy, grads, stream=None):
+    return check(lib.otm_unet_backward(u, _p(dy), _p(grads), stream))
+
+
+def otm_unet_train_step(u, x, target, lr, stream=None) -> float:
+    loss = C.c_double(0.0)
+    check(lib.otm_unet_train_step(u, _p(x), _p(target), float(lr), C.byref(loss), stream))
+    return loss.value
+
+
+def otm_unet_eval(u, x, target, stream=None) -> float:
+    loss = C.c_double(0.0)
+    check(lib.otm_unet_eval(u, _p(x), _p(target), C.byref(loss), stream))
+    return loss.value
+
+
+def otm_set_predictor(ctx, u, scale):
+    return check(lib.otm_set_predictor(ctx, u, float(scale)), ctx)
+
+
+def otm_op_conv3(n, cin, cout, x, w, bias, relu, out, stream=None):
+    return check(lib.otm_op_conv3(n, cin, cout, _p(x), _p(w), _p(bias), int(relu), _p(out), stream))
+
+
+def otm_op_conv3_wgrad(n, cin, cout, x, g, dw, db, stream=None):
+    return check(lib.otm_op_conv3_wgrad(n, cin, cout, _p(x), _p(g), _p(dw), _p(db), stream))

@@ -151,3 +151,21 @@ def test_level_hierarchy_sizes_accepted():
             otm.lib.otm_destroy(ctx)
         else:
             assert st in (otm.OTM_ECUDA, otm.OTM_ENOMEM), (n, otm.otm_last_error())
+
+
+def test_unet_and_conv_entry_points_validate_sizes_before_touching_the_gpu():
+    otm = _lib()
+    bad_widths = [(16, 24, 32, 32), (8, 16, 16, 16), (16, 16, 16, 272)]
+    for w in bad_widths:
+        with pytest.raises(otm.OtmError) as e:
+            otm.otm_unet_create(16, w)
+        assert e.value.status == otm.OTM_EINVAL
+    for n in (4, 12, 520):
+        with pytest.raises(otm.OtmError) as e:
+            otm.otm_unet_create(n, (16, 16, 16, 16))
+        assert e.value.status == otm.OTM_EINVAL
+    with pytest.raises(otm.OtmError):
+        otm.otm_op_conv3(8, 24, 16, 1, 1, None, 0, 1)
+    with pytest.raises(otm.OtmError):
+        otm.otm_op_conv3_wgrad(0, 16, 16, 1, 1, 1, None)
+    assert otm.lib.otm_set_predictor(None, None, 1.0) == otm.OTM_EINVAL

@@ -1,0 +1,305 @@
+"""Parity of the learned warm start's network (BF16 tensor-core U-Net) with
+the FP64 oracle network, and of the warm-start choice inside the design step.
+
+Tolerances come from the arithmetic:
+* one convolution: inputs and weights are the same BF16 values on both sides;
+  the GPU accumulates K = 27 cin products in FP32 (tensor cores; bound each
+  addition by 2^-22 relative to allow non-nearest internal rounding) and
+  rounds the output to BF16 (2^-9 relative), so
+  |gpu - ref| <= 2^-9 |ref| + K 2^-22 S with S the same sum over |terms|;
+* the weight gradient sums N (voxels) products in FP32 per CTA chunk and
+  across chunks with FP32 atomics: |gpu - ref| <= N 2^-22 S;
+* the whole network rounds activations and weights to BF16 at every stage
+  (14 convolutions, 3 poolings, the input, the head's input: 19 stages, each
+  at most 2 x 2^-9 relative in norm when the layers' gains are near 1, as the
+  He initialisation makes them), so the norm-wise forward error is bounded by
+  19 x 2 x 2^-9 = 0.074; the backward pass adds one BF16 gradient rounding
+  per convolution, pooling and concatenation (about 3 x as many stages),
+  giving 0.2 for the gradients.  Structural mistakes (a wrong tap, a
+  transposed weight, a dropped skip connection) give O(1) errors.
+"""
+import numpy as np
+import pytest
+
+from oracle import unet as U
+import workloads as W
+from tests.gpu_util import dev, empty, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _otm():
+    from paper_2405_19991_gb300 import otm
+    return otm
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _bf16_dev(a):
+    """FP64 array -> BF16 device tensor, and the rounded values as FP64."""
+    torch = _torch()
+    t = torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32).to(torch.bfloat16).cuda()
+    return t, t.float().cpu().double().numpy()
+
+
+def _to_oracle(a, n, c):
+    """[voxel][C] (voxel = x + n (y + n z)) -> (C, z, y, x)."""
+    return np.moveaxis(a.reshape(n, n, n, c), -1, 0)
+
+
+def _from_oracle(a):
+    return np.ascontiguousarray(np.moveaxis(a, 0, -1)).reshape(-1)
+
+
+def _flat(params, widths):
+    parts = []
+    for name in U.BLOCKS:
+        for key in ("W1", "b1", "W2", "b2"):
+            parts.append(params[f"{name}.{key}"].reshape(-1))
+    parts += [params["H.W"].reshape(-1), params["H.b"].reshape(-1)]
+    return np.concatenate(parts)
+
+
+def _unflat(vec, widths):
+    out, o = {}, 0
+    for name, (a, b) in U.block_channels(widths).items():
+        for key, shape in (("W1", (27, a, b)), ("b1", (b,)), ("W2", (27, b, b)), ("b2", (b,))):
+            sz = int(np.prod(shape))
+            out[f"{name}.{key}"] = vec[o:o + sz].reshape(shape)
+            o += sz
+    out["H.W"] = vec[o:o + widths[0] * 3].reshape(widths[0], 3)
+    o += widths[0] * 3
+    out["H.b"] = vec[o:o + 3]
+    o += 3
+    assert o == vec.size
+    return out
+
+
+@pytest.mark.parametrize("n,cin,cout,relu", [(4, 16, 16, 1), (6, 16, 32, 0), (8, 48, 16, 1),
+                                             (5, 32, 64, 1), (8, 128, 64, 0), (3, 64, 128, 1)])
+def test_conv3_matches_definition(n, cin, cout, relu):
+    otm = _otm()
+    torch = _torch()
+    rng = np.random.default_rng(n * 1000 + cin + cout)
+    N = n ** 3
+    x_d, x = _bf16_dev(rng.standard_normal((N, cin)))
+    w_d, w = _bf16_dev(rng.standard_normal((27, cin, cout)) / np.sqrt(27 * cin))
+    b = rng.standard_normal(cout) * 0.1
+    b_d = dev(b, torch.float32)
+    out = torch.empty((N, cout), dtype=torch.bfloat16, device="cuda")
+    otm.otm_op_conv3(n, cin, cout, x_d, w_d, b_d, relu, out)
+    xo = _to_oracle(x, n, cin)
+    bref = host(b_d)
+    ref = U.conv3(xo, w, bref)
+    S = U.conv3(np.abs(xo), np.abs(w), np.abs(bref))
+    if relu:
+        ref = U.relu(ref)
+    got = _to_oracle(out.float().cpu().double().numpy(), n, cout)
+    K = 27 * cin
+    tol = 2.0 ** -9 * np.abs(ref) + K * 2.0 ** -22 * S + 1e-30
+    assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
+
+
+@pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32)])
+def test_conv3_weight_gradient_matches_definition(n, cin, cout):
+    otm = _otm()
+    torch = _torch()
+    rng = np.random.default_rng(7 * n + cin)
+    N = n ** 3
+    x_d, x = _bf16_dev(rng.standard_normal((N, cin)))
+    g_d, g = _bf16_dev(rng.standard_normal((N, cout)))
+    dw = torch.zeros((27, cin, cout), dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    otm.otm_op_conv3_wgrad(n, cin, cout, x_d, g_d, dw, db)
+    xo, go = _to_oracle(x, n, cin), _to_oracle(g, n, cout)
+    W0 = np.zeros((27, cin, cout))
+    _, dW_ref, db_ref = U.conv3_backward(xo, W0, go)
+    _, S_w, S_b = U.conv3_backward(np.abs(xo), W0, np.abs(go))
+    tol_w = N * 2.0 ** -22 * S_w + 1e-30
+    tol_b = N * 2.0 ** -22 * S_b + 1e-30
+    assert np.all(np.abs(host(dw) - dW_ref) <= tol_w)
+    assert np.all(np.abs(host(db) - db_ref) <= tol_b)
+
+
+def _net(n, widths, seed):
+    otm = _otm()
+    torch = _torch()
+    u = otm.otm_unet_create(n, widths, seed)
+    P = otm.otm_unet_param_count(u)
+    p = U.init_params(widths, seed)
+    flat = _flat(p, widths)
+    assert flat.size == P
+    otm.otm_unet_set_params(u, dev(flat, torch.float32), 1)
+    back = torch.empty(P, dtype=torch.float32, device="cuda")
+    otm.otm_unet_get_params(u, back, 1)
+    pf = host(back)
+    assert np.array_equal(pf, flat.astype(np.float32).astype(np.float64))
+    return u, _unflat(pf, widths)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("n,widths", [(8, (16, 16, 16, 16)), (16, (16, 32, 64, 128)), (24, (16, 32, 32, 48))])
+def test_unet_forward_and_backward_match_oracle(n, widths):
+    otm = _otm()
+    torch = _torch()
+    u, p = _net(n, widths, seed=3)
+    try:
+        x = W.random_density(n, 5).reshape(1, n, n, n)
+        x_d = dev(x.reshape(-1), torch.float32)
+        y_d = empty(3 * n ** 3, torch.float32)
+        otm.otm_unet_forward(u, x_d, y_d)
+        y_ref, cache = U.forward(p, host(x_d).reshape(1, n, n, n))
+        err_f = _rel(host(y_d).reshape(3, n, n, n), y_ref)
+        assert err_f <= 0.074, err_f
+        rng = np.random.default_rng(11)
+        dy = rng.standard_normal((3, n, n, n))
+        dy_d = dev(dy.reshape(-1), torch.float32)
+        P = otm.otm_unet_param_count(u)
+        g_d = empty(P, torch.float32)
+        otm.otm_unet_backward(u, dy_d, g_d)
+        g_ref, _ = U.backward(p, cache, host(dy_d).reshape(3, n, n, n), widths)
+        g = _unflat(host(g_d), widths)
+        worst = max(_rel(g[k], g_ref[k]) for k in g_ref)
+        assert worst <= 0.2, {k: _rel(g[k], g_ref[k]) for k in g_ref}
+    finally:
+        otm.otm_unet_destroy(u)
+
+
+def test_adam_step_and_loss():
+    """One Adam step from zero moments moves every parameter by lr * g / (|g| + eps)
+    (so by about lr against the sign of its gradient); the reported loss is the
+    mean squared error before the update."""
+    otm = _otm()
+    torch = _torch()
+    n, widths, lr = 8, (16, 16, 32, 32), 1e-3
+    u, p = _net(n, widths, seed=4)
+    try:
+        x = W.random_density(n, 6).reshape(1, n, n, n)
+        x_d = dev(x.reshape(-1), torch.float32)
+        rng = np.random.default_rng(12)
+        t = 0.1 * rng.standard_normal((3, n, n, n))
+        t_d = dev(t.reshape(-1), torch.float32)
+        ev = otm.otm_unet_eval(u, x_d, t_d)
+        y_ref, cache = U.forward(p, host(x_d).reshape(1, n, n, n))
+        L_ref, dy = U.mse_loss(y_ref, host(t_d).reshape(3, n, n, n))
+        assert abs(ev - L_ref) <= 0.074 * 2 * np.sqrt(L_ref * np.mean(y_ref ** 2)) + 1e-12
+        loss = otm.otm_unet_train_step(u, x_d, t_d, lr)
+        assert loss == pytest.approx(ev, rel=1e-6)
+        g_ref, _ = U.backward(p, cache, dy, widths)
+        P = otm.otm_unet_param_count(u)
+        after = empty(P, torch.float32)
+        otm.otm_unet_get_params(u, after, 1)
+        step = _unflat(host(after), widths)
+        agree = total = 0
+        for k, gk in g_ref.items():
+            d = step[k] - p[k]
+            assert np.max(np.abs(d)) <= lr * 1.001 + 1e-7, k
+            big = np.abs(gk) > 0.2 * np.max(np.abs(gk))
+            agree += int(np.sum(np.sign(d[big]) == -np.sign(gk[big])))
+            total += int(np.sum(big))
+        assert agree >= 0.97 * total, (agree, total)
+        # a few more steps lower the loss
+        for _ in range(20):
+            last = otm.otm_unet_train_step(u, x_d, t_d, lr)
+        assert last < loss
+    finally:
+        otm.otm_unet_destroy(u)
+
+
+def _ctx(n, ws, stream, prec=1):
+    otm = _otm()
+    p = otm.otm_params_default(n=n, precision=prec, kappa_target=W.TARGET_ORTHOTROPIC, rmin=2.0,
+                               warm_start=ws, cg_tol=1e-6, stream=stream)
+    ctx = otm.otm_create_ex(p)
+    r0 = W.initial_density(n, 0.3, 1).astype(np.float32)
+    otm.otm_set_density(ctx, r0.ctypes.data, 0)
+    return ctx
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_learned_start_picks_the_smallest_residual(prec):
+    """First design iteration with a predictor attached: per load case the
+    solve starts from zero or from the (zero-mean) prediction, whichever has
+    the smaller true residual; the design step then matches the one started
+    from zero."""
+    otm = _otm()
+    torch = _torch()
+    n, scale = 16, 3.0
+    st = torch.cuda.current_stream().cuda_stream
+    u = otm.otm_unet_create(n, (16, 16, 32, 32), 9, st)
+    ctx = _ctx(n, otm.OTM_WS_LEARNED, st, prec)
+    ref = _ctx(n, otm.OTM_WS_PREV, st, prec)
+    try:
+        otm.otm_set_predictor(ctx, u, scale)
+        info, _ = otm.otm_step(ctx)
+        info_r, _ = otm.otm_step(ref)
+        choice = info.as_dict()["ws_choice"]
+        assert all(c in (0, 2) for c in choice)
+        # recompute both candidates' residuals from the fields the step used
+        N = n ** 3
+        rf = empty(N, torch.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_RHO_FILT, rf.data_ptr(), N, 1)
+        f = empty(3 * N, torch.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_LOAD, f.data_ptr(), 3 * N, 1)
+        k = empty(N, torch.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_K, k.data_ptr(), N, 1)
+        y = empty(3 * N, torch.float32)
+        otm.otm_unet_forward(u, rf, y)
+        xc = scale * host(y).reshape(3, N)
+        xc -= xc.mean(axis=1, keepdims=True)
+        Kx = empty(3 * N, torch.float64)
+        otm.otm_op_apply_K(0, n, dev(host(k), torch.float64), dev(xc.reshape(-1), torch.float64), Kx)
+        fh = host(f).reshape(3, N)
+        r_net = np.linalg.norm(fh - host(Kx).reshape(3, N), axis=1)
+        r_zero = np.linalg.norm(fh, axis=1)
+        for i in range(3):
+            gap = abs(r_net[i] - r_zero[i]) / r_zero[i]
+            if gap > 1e-3:
+                assert choice[i] == (2 if r_net[i] < r_zero[i] else 0), (i, r_net, r_zero, choice)
+        assert max(info.resid) <= 1e-6
+        assert info.g == pytest.approx(info_r.g, rel=1e-4)
+        assert np.allclose(info.kappa, info_r.kappa, rtol=1e-4, atol=1e-9)
+    finally:
+        otm.otm_destroy(ctx)
+        otm.otm_destroy(ref)
+        otm.otm_unet_destroy(u)
+
+
+def test_learned_trajectory_matches_previous_start():
+    """Ten design iterations with the learned start (an untrained network)
+    follow the previous-solution trajectory: every solve reaches the
+    tolerance, so the designs agree to the solver's accuracy."""
+    otm = _otm()
+    torch = _torch()
+    n = 16
+    st = torch.cuda.current_stream().cuda_stream
+    u = otm.otm_unet_create(n, (16, 16, 32, 32), 10, st)
+    ctx = _ctx(n, otm.OTM_WS_LEARNED, st)
+    ref = _ctx(n, otm.OTM_WS_PREV, st)
+    try:
+        otm.otm_set_predictor(ctx, u, float(n))
+        for it in range(10):
+            a, _ = otm.otm_step(ctx)
+            b, _ = otm.otm_step(ref)
+            assert max(a.resid) <= 1e-6
+            assert a.g == pytest.approx(b.g, rel=1e-3), it
+            if it > 0:
+                assert all(c in (0, 1, 2, 3) for c in a.as_dict()["ws_choice"])
+        N = n ** 3
+        ra, rb = np.empty(N, np.float32), np.empty(N, np.float32)
+        otm.otm_get_density(ctx, ra.ctypes.data, 0)
+        otm.otm_get_density(ref, rb.ctypes.data, 0)
+        assert np.max(np.abs(ra - rb)) <= 1e-3
+        otm.otm_set_predictor(ctx, None, 1.0)
+        a, _ = otm.otm_step(ctx)
+        assert a.as_dict()["ws_choice"] == [0, 0, 0]
+    finally:
+        otm.otm_destroy(ctx)
+        otm.otm_destroy(ref)
+        otm.otm_unet_destroy(u)
