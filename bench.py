@@ -9,6 +9,13 @@ workload, rho0 = 0.3 + U(-0.05, 0.05), r = 2, p = 3, k = 1 / 1e-3.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload ortho128|aniso128mixed|aniso256mixed] [--no-cpu-baseline]
+                  [--no-forms]
+
+`value` is the plain FP32 form (previous-iterate start).  The same run also
+times, on the same workload and GPU, the other forms of the solve (cold
+start, BF16 V-cycle, and the learned warm start with the BF16 V-cycle, whose
+U-Net is first trained on design histories of other seeds) and reports them
+under "forms" with their ratio to the plain FP32 form.
 
 Multi-GPU: replicas only.  Each rank runs its own independent design (seed
 offset by rank); the only collectives are the barrier and the max-time
@@ -45,6 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ortho128", choices=["ortho128", "aniso128mixed", "aniso256mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the cold / mixed / learned+mixed forms")
+    ap.add_argument("--train-steps", type=int, default=240, help="Adam steps of the warm-start network")
     ap.add_argument("--cpu-budget", type=float, default=25.0, help="seconds of oracle CG in the CPU sample")
     return ap.parse_args()
 
@@ -175,6 +184,96 @@ def cpu_sample(wl, budget_s=25.0, chunk=10, steps=None, warmup=0, log=None):
     cores = (time.process_time() - cpu0) / max(time.perf_counter() - wall0, 1e-9)
     return dict(value=1.0 / t_oc, cores=max(1, int(math.ceil(cores - 0.05))), nproc=os.cpu_count(), t_setup=t_setup, t_tail=t_tail, t_iter=t_iter, cg_done=done,
                 cg_needed=n_needed, res_reached=hist[-1][1], per_step=per_step, t_oc=t_oc)
+
+
+# ------------------------------------------------------------------ forms
+def timed_steps(otm, ctx, stream, steps, warmup):
+    """Device time of `steps` OC iterations after `warmup` untimed ones."""
+    import torch
+    for _ in range(warmup):
+        otm.otm_step(ctx)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = []
+    for _ in range(steps):
+        info, _ = otm.otm_step(ctx)
+        infos.append(info.as_dict())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), infos
+
+
+def run_forms(args, wl, dev, stream, rank, plain_value):
+    """Cold start, BF16 V-cycle, and learned warm start + BF16 V-cycle on the
+    benchmark workload; the warm-start network (widths 16/32/64/128) is
+    trained on (filtered density, solution) pairs from the design histories
+    of three other seeds before its form is timed."""
+    import torch
+    from paper_2405_19991_gb300 import otm, warmstart
+
+    def params(prec, ws):
+        return otm.otm_params_default(n=wl.n, kappa_target=wl.kappa_target, volfrac=wl.volfrac, penal=wl.penal,
+                                      rmin=wl.rmin, k_solid=wl.k_solid, k_void=wl.k_void, cg_tol=wl.cg_tol,
+                                      cg_maxit=500, precision=prec, warm_start=ws, stream=stream.cuda_stream,
+                                      device=dev)
+
+    rho0 = W.initial_density(wl.n, wl.volfrac, wl.seed + rank).astype(np.float32)
+    out = {}
+
+    def form(name, prec, ws, unet=None, scale=1.0):
+        ctx = otm.otm_create_ex(params(prec, ws))
+        try:
+            otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+            if unet is not None:
+                otm.otm_set_predictor(ctx, unet, scale)
+            ms, infos = timed_steps(otm, ctx, stream, args.steps, args.warmup)
+        finally:
+            otm.otm_destroy(ctx)
+        v = args.steps / (ms * 1e-3)
+        cg = [i["cg_iters"] for i in infos]
+        rec = {"value": v, "unit": UNIT, "ms_per_step": ms / args.steps, "mean_cg_iters": float(np.mean(cg)),
+               "max_true_resid": float(max(max(i["resid"]) for i in infos)),
+               "vs_plain_fp32": v / plain_value,
+               "stage_ms_mean": [float(np.mean([i["stage_ms"][k] for i in infos])) for k in (1, 2, 4, 7)]}
+        if ws == otm.OTM_WS_LEARNED:
+            counts = {}
+            for i in infos:
+                for c in i["ws_choice"]:
+                    counts[c] = counts.get(c, 0) + 1
+            names = {0: "zero", 1: "previous", 2: "predictor", 3: "previous+change"}
+            rec["start_choices"] = {names[k]: v for k, v in sorted(counts.items())}
+        out[name] = rec
+
+    form("plain_fp32_cold_start", 1, otm.OTM_WS_NONE)
+    form("mixed_bf16_vcycle_previous_start", 2, otm.OTM_WS_PREV)
+    # train the warm-start network on other seeds' histories
+    t0 = time.perf_counter()
+    hist_iters, seeds = 20, (10, 11, 12)
+    buf = warmstart.PairBuffer(wl.n, hist_iters * len(seeds))
+    for sd in seeds:
+        warmstart.collect(params(1, otm.OTM_WS_PREV), W.initial_density(wl.n, wl.volfrac, sd), hist_iters, buf)
+    t_collect = time.perf_counter() - t0
+    scale = wl.n / 8.0
+    unet = otm.otm_unet_create(wl.n, (16, 32, 64, 128), 0, stream.cuda_stream)
+    try:
+        t0 = time.perf_counter()
+        losses = warmstart.train(unet, buf, args.train_steps, 1e-3, scale, seed=1, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        held = warmstart.PairBuffer(wl.n, 4)
+        warmstart.collect(params(1, otm.OTM_WS_PREV), rho0, 4, held)
+        held_loss = warmstart.evaluate(unet, held, scale, stream.cuda_stream)
+        form("learned_start_mixed_bf16_vcycle", 2, otm.OTM_WS_LEARNED, unet, scale)
+        out["learned_start_mixed_bf16_vcycle"]["training"] = {
+            "pairs": buf.count, "histories": list(seeds), "iters_per_history": hist_iters,
+            "collect_s": t_collect, "adam_steps": args.train_steps, "lr": 1e-3, "train_s": t_train,
+            "ms_per_adam_step": t_train / max(args.train_steps, 1) * 1e3,
+            "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+            "held_out_loss": held_loss, "params": otm.otm_unet_param_count(unet), "target": "chi / (n / 8)"}
+    finally:
+        otm.otm_unet_destroy(unet)
+    return out
 
 
 # ------------------------------------------------------------------- ours
@@ -310,7 +409,7 @@ def run_ours(args, rank, world):
                    "volfrac": wl.volfrac, "rmin": wl.rmin, "penal": wl.penal, "k_void": wl.k_void,
                    "cg_tol": wl.cg_tol, "precision": {1: "fp32", 2: "mixed-bf16"}[prec],
                    "warm_start": "previous iterate", "parallelism": f"replicas{world}",
-                   "l2": "per-step working set (~0.4 GB of fields, ~0.7 GB moved per PCG iteration) exceeds the 126 MB L2",
+                   "l2": "per-step working set (~0.4 GB of fields, ~0.7 GB moved per PCG iteration) exceeds the 129 MB L2",
                    "mean_cg_iters": float(np.mean(cg)), "max_true_resid": float(max(max(i.resid) for i in infos))},
         "e2e": {"value": e_steps * world / float(e2e_t.item()), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes,
@@ -324,6 +423,14 @@ def run_ours(args, rank, world):
         "wall_s_timed": t_wall,
     }
     otm.otm_destroy(ctx)
+    if not args.no_forms and wl.n % 8 == 0:
+        forms = run_forms(args, wl, dev, stream, rank, value)
+        forms = {"plain_fp32_previous_start": {"value": value, "unit": UNIT, "ms_per_step": ms_max / args.steps,
+                                               "mean_cg_iters": float(np.mean(cg)), "vs_plain_fp32": 1.0},
+                 **forms}
+        result["forms"] = forms
+        lm = forms["learned_start_mixed_bf16_vcycle"]["value"]
+        result["learned_mixed_vs_plain_fp32"] = lm / value
     return result
 
 

@@ -372,14 +372,15 @@ OTM_API otm_status otm_unet_forward(otm_unet* u, const float* x, float* y, void*
  * last otm_unet_forward: dy 3 n^3 (device), grads param_count FP32 (device,
  * may be NULL: the gradient then stays inside the network). */
 OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads, void* stream);
-/* One Adam step on L = mean((net(x) - target)^2) over the 3 n^3 entries:
- * forward, loss, backward, update.  *loss (host, may be NULL) = L before
- * the update. */
-OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target, double lr,
-                                       double* loss, void* stream);
-/* L = mean((net(x) - target)^2) without an update. */
-OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target, double* loss,
-                                 void* stream);
+/* One Adam step on L = mean((net(x) - target / target_scale)^2) over the
+ * 3 n^3 entries (target_scale > 0; the predictor's scale when the targets are
+ * solutions): forward, loss, backward, update.  *loss (host, may be NULL) =
+ * L before the update. */
+OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target,
+                                       double target_scale, double lr, double* loss, void* stream);
+/* L = mean((net(x) - target / target_scale)^2) without an update. */
+OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target,
+                                 double target_scale, double* loss, void* stream);
 /* Attach a network (grid n equal to the context's) as the predictor used by
  * OTM_WS_LEARNED, with chi_i ~ scale * y_i; NULL detaches.  The context
  * borrows the network: keep it alive while attached, and do not run other

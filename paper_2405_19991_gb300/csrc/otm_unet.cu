@@ -361,9 +361,9 @@ struct otm_unet {
         return OTM_OK;
     }
 
-    otm_status loss(const float* target, cudaStream_t st) {
+    otm_status loss(const float* target, double tscale, cudaStream_t st) {
         U_CU(cudaMemsetAsync(loss_d, 0, sizeof(double), st));
-        otm::nn::k_mse<<<elt_grid(3 * Nl[0]), 256, 0, st>>>(3 * Nl[0], y, target, dy, loss_d);
+        otm::nn::k_mse<<<elt_grid(3 * Nl[0]), 256, 0, st>>>(3 * Nl[0], y, target, (float)(1.0 / tscale), dy, loss_d);
         g_launches += 1;
         U_LAUNCH();
         return OTM_OK;
@@ -471,13 +471,15 @@ OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads,
     return OTM_OK;
 }
 
-OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target, double lr, double* loss,
-                                       void* stream) {
+OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target, double target_scale,
+                                       double lr, double* loss, void* stream) {
     if (!u || !x || !target) return ufail(OTM_EINVAL, "otm_unet_train_step: NULL argument");
+    if (!(target_scale > 0.0 && std::isfinite(target_scale)))
+        return ufail(OTM_EINVAL, "otm_unet_train_step: target_scale must be finite and > 0");
     if (!(lr >= 0.0 && std::isfinite(lr))) return ufail(OTM_EINVAL, "otm_unet_train_step: lr must be finite, >= 0");
     cudaStream_t st = pick(u, stream);
     U_TRY(u->forward(x, st));
-    U_TRY(u->loss(target, st));
+    U_TRY(u->loss(target, target_scale, st));
     U_TRY(u->backward(u->dy, st));
     U_TRY(u->adam(lr, st));
     U_CU(cudaMemcpyAsync(u->loss_h, u->loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -486,11 +488,14 @@ OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float*
     return OTM_OK;
 }
 
-OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target, double* loss, void* stream) {
+OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target, double target_scale, double* loss,
+                                 void* stream) {
     if (!u || !x || !target || !loss) return ufail(OTM_EINVAL, "otm_unet_eval: NULL argument");
+    if (!(target_scale > 0.0 && std::isfinite(target_scale)))
+        return ufail(OTM_EINVAL, "otm_unet_eval: target_scale must be finite and > 0");
     cudaStream_t st = pick(u, stream);
     U_TRY(u->forward(x, st));
-    U_TRY(u->loss(target, st));
+    U_TRY(u->loss(target, target_scale, st));
     U_CU(cudaMemcpyAsync(u->loss_h, u->loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
     U_CU(cudaStreamSynchronize(st));
     *loss = *u->loss_h;

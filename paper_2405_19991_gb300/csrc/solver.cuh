@@ -321,6 +321,7 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(partials, (size_t)max_blocks * kRedMaxVals));
         OTM_TRY(alloc(counter, 4));
         OTM_TRY(alloc(ps, 1));
+        OTM_TRY(alloc(ps_c, 1));
         OTM_TRY(alloc(ds, 1));
         OTM_CU(cudaMallocHost((void**)&ps_h, sizeof(PcgScalars)));
         OTM_CU(cudaMallocHost((void**)&ds_h, sizeof(DesignScalars)));
@@ -414,6 +415,11 @@ class Solver : public SolverBase {
                 }
                 ++nl_;
                 launch_pdl(k_join<R, float>, grid(3 * N), 256, stream, 3 * N, x, xl, stage_f);
+                // the solutions are defined up to a constant: report the zero-mean one
+                nl_ += 2;
+                launch_pdl(k_sum3<float>, grid(N), 256, stream, N, (const float*)stage_f, rbuf(),
+                           FinMean{ps_c, 1.0 / (double)N});
+                launch_pdl(k_sub_mean<float>, grid(N), 256, stream, N, stage_f, (const PcgScalars*)ps_c);
                 OTM_LAUNCH();
                 OTM_CU(cudaMemcpyAsync(out, stage_f, 3 * N * sizeof(float),
                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
@@ -948,7 +954,6 @@ if (tz_ > 0 && std::is_same<R, float>::value)
             OTM_TRY(alloc(ynet[1], 3 * N));
             OTM_TRY(alloc(xc_net, 3 * N));
             OTM_TRY(alloc(xc_delta, 3 * N));
-            OTM_TRY(alloc(ps_c, 1));
             OTM_TRY(alloc(ws, 1));
             OTM_CU(cudaMallocHost((void**)&ws_h, sizeof(WsState)));
             memset(ws_h, 0, sizeof(WsState));

@@ -354,14 +354,14 @@ k_head_back(size_t N, int C, const bf16* __restrict__ d, const float* __restrict
     if (threadIdx.x < 3) atomicAdd(db + threadIdx.x, sH[C * 3 + threadIdx.x]);
 }
 
-// MSE loss against target t ([3][N]): dy = 2 (y - t) / (3N); loss partials
-// summed into *loss (FP64 atomics).
-static __global__ void k_mse(size_t M, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ dy,
-                      double* __restrict__ loss) {
+// MSE loss against the target t * inv_scale (t [3][N]): dy = 2 (y - t') / M;
+// loss partials summed into *loss (FP64 atomics).
+static __global__ void k_mse(size_t M, const float* __restrict__ y, const float* __restrict__ t, float inv_scale,
+                             float* __restrict__ dy, double* __restrict__ loss) {
     double s = 0.0;
     const float sc = 2.0f / (float)M;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
-        const float d = y[i] - t[i];
+        const float d = y[i] - t[i] * inv_scale;
         s += (double)d * d;
         dy[i] = sc * d;
     }

@@ -4,7 +4,9 @@ for profiling a single kernel under ncu.
   python -m paper_2405_19991_gb300.opbench --op apply_K --n 128 --reps 3
   python -m paper_2405_19991_gb300.opbench --op step --n 128 --reps 2 --warmup 3
 
-Ops: apply_K, gs (one fine colour pass), filter, kappa_sens, oc, step.
+Ops: apply_K, gs (one fine colour pass), filter, kappa_sens, oc, step,
+unet (network forward), unet_train (one Adam step), conv3 (one convolution,
+--cin/--cout).
 Prints the mean CUDA-event time per repetition.
 """
 from __future__ import annotations
@@ -28,6 +30,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--dtype", type=int, default=1, help="1 = FP32, 0 = FP64; precision for --op step (2 = mixed)")
     ap.add_argument("--colour", type=int, default=8, help="--op gs: colour (0-7) or group pass 8 + g")
+    ap.add_argument("--widths", default="16,32,64,128", help="--op unet*: network widths")
+    ap.add_argument("--cin", type=int, default=16)
+    ap.add_argument("--cout", type=int, default=16)
     args = ap.parse_args()
 
     import torch
@@ -45,6 +50,18 @@ def main():
     out = torch.empty(3 * N, dtype=t, device=dev)
     s = torch.as_tensor(-np.abs(rng.standard_normal(N)), dtype=t, device=dev)
     ctx = None
+    unet = None
+    if args.op.startswith("unet"):
+        widths = [int(v) for v in args.widths.split(",")]
+        unet = otm.otm_unet_create(n, widths, 0, st.cuda_stream)
+        y = torch.empty(3 * N, dtype=torch.float32, device=dev)
+        tgt = torch.as_tensor(rng.standard_normal(3 * N), dtype=torch.float32, device=dev)
+        rho32 = rho.float().contiguous()
+    if args.op == "conv3":
+        xin = torch.randn((N, args.cin), device=dev).to(torch.bfloat16)
+        wc = (torch.randn((27, args.cin, args.cout), device=dev) / (27 * args.cin) ** 0.5).to(torch.bfloat16)
+        bc = torch.zeros(args.cout, device=dev)
+        yc = torch.empty((N, args.cout), dtype=torch.bfloat16, device=dev)
     if args.op == "step":
         p = otm.otm_params_default(n=n, precision=args.dtype, kappa_target=W.TARGET_ORTHOTROPIC, rmin=2.0,
                                    stream=st.cuda_stream)
@@ -66,6 +83,12 @@ def main():
             otm.otm_op_oc_update(args.dtype, n, 0.29, 0.05, 0.5, 1e-3, rho, s, out, st.cuda_stream)
         elif args.op == "step":
             otm.otm_step(ctx)
+        elif args.op == "unet":
+            otm.otm_unet_forward(unet, rho32, y, st.cuda_stream)
+        elif args.op == "unet_train":
+            otm.otm_unet_train_step(unet, rho32, tgt, 1e-4, 1.0, st.cuda_stream)
+        elif args.op == "conv3":
+            otm.otm_op_conv3(n, args.cin, args.cout, xin, wc, bc, 1, yc, st.cuda_stream)
         else:
             raise SystemExit(f"unknown op {args.op}")
 
@@ -79,8 +102,13 @@ def main():
     e1.record(st)
     torch.cuda.synchronize()
     print(f"{args.op} n={n}: {e0.elapsed_time(e1) / args.reps * 1e3:.1f} us per repetition")
+    if args.op == "conv3":
+        flops = 2.0 * N * 27 * args.cin * args.cout
+        print(f"conv3 {args.cin}->{args.cout}: {flops / (e0.elapsed_time(e1) / args.reps * 1e-3) / 1e12:.1f} TFLOP/s")
     if ctx is not None:
         otm.otm_destroy(ctx)
+    if unet is not None:
+        otm.otm_unet_destroy(unet)
 
 
 if __name__ == "__main__":

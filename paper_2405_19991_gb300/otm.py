@@ -126,8 +126,8 @@ def _load():
         "otm_unet_set_params": [vp, vp, i],
         "otm_unet_forward": [vp, vp, vp, vp],
         "otm_unet_backward": [vp, vp, vp, vp],
-        "otm_unet_train_step": [vp, vp, vp, d, P(d), vp],
-        "otm_unet_eval": [vp, vp, vp, P(d), vp],
+        "otm_unet_train_step": [vp, vp, vp, d, d, P(d), vp],
+        "otm_unet_eval": [vp, vp, vp, d, P(d), vp],
         "otm_set_predictor": [vp, vp, d],
         "otm_op_conv3": [i, i, i, vp, vp, vp, i, vp, vp],
         "otm_op_conv3_wgrad": [i, i, i, vp, vp, vp, vp, vp],
@@ -358,15 +358,15 @@ def otm_unet_backward(u, dy, grads, stream=None):
     return check(lib.otm_unet_backward(u, _p(dy), _p(grads), stream))
 
 
-def otm_unet_train_step(u, x, target, lr, stream=None) -> float:
+def otm_unet_train_step(u, x, target, lr, target_scale=1.0, stream=None) -> float:
     loss = C.c_double(0.0)
-    check(lib.otm_unet_train_step(u, _p(x), _p(target), float(lr), C.byref(loss), stream))
+    check(lib.otm_unet_train_step(u, _p(x), _p(target), float(target_scale), float(lr), C.byref(loss), stream))
     return loss.value
 
 
-def otm_unet_eval(u, x, target, stream=None) -> float:
+def otm_unet_eval(u, x, target, target_scale=1.0, stream=None) -> float:
     loss = C.c_double(0.0)
-    check(lib.otm_unet_eval(u, _p(x), _p(target), C.byref(loss), stream))
+    check(lib.otm_unet_eval(u, _p(x), _p(target), float(target_scale), C.byref(loss), stream))
     return loss.value
 
 

@@ -52,7 +52,8 @@ def test_homogenize_matches_oracle(precision, n, rmin):
         chi = np.empty(3 * N, dtype=np.float32)
         otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * N, 0)
         chi = chi.reshape(3, N).astype(np.float64)
-        chi -= chi.mean(axis=1, keepdims=True)
+        # reported with zero mean (to the FP32 rounding of the stored values)
+        assert np.all(np.abs(chi.mean(axis=1)) <= 1e-6 * (np.max(np.abs(chi)) + 1e-30))
         scale = np.max(np.abs(ref["chi"])) + 1e-30
         ctol = {0: 1e-6, 1: 2e-3, 2: 2e-2}[precision]
         assert np.max(np.abs(chi - ref["chi"])) <= ctol * max(scale, 1e-3)
