@@ -243,6 +243,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
                     counts[c] = counts.get(c, 0) + 1
             names = {0: "zero", 1: "previous", 2: "predictor", 3: "previous+change"}
             rec["start_choices"] = {names[k]: v for k, v in sorted(counts.items())}
+            rec["iterations_predictor_skipped"] = int(sum(1 for i in infos if i["ws_skipped"]))
         out[name] = rec
 
     form("plain_fp32_cold_start", 1, otm.OTM_WS_NONE)
@@ -254,7 +255,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
     for sd in seeds:
         warmstart.collect(params(1, otm.OTM_WS_PREV), W.initial_density(wl.n, wl.volfrac, sd), hist_iters, buf)
     t_collect = time.perf_counter() - t0
-    scale = wl.n / 8.0
+    scale = warmstart.target_scale(buf)
     unet = otm.otm_unet_create(wl.n, (16, 32, 64, 128), 0, stream.cuda_stream)
     try:
         t0 = time.perf_counter()
@@ -270,7 +271,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
             "collect_s": t_collect, "adam_steps": args.train_steps, "lr": 1e-3, "train_s": t_train,
             "ms_per_adam_step": t_train / max(args.train_steps, 1) * 1e3,
             "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
-            "held_out_loss": held_loss, "params": otm.otm_unet_param_count(unet), "target": "chi / (n / 8)"}
+            "held_out_loss": held_loss, "params": otm.otm_unet_param_count(unet), "target": "chi / rms(chi)", "scale": scale}
     finally:
         otm.otm_unet_destroy(unet)
     return out

@@ -137,8 +137,9 @@ typedef struct otm_step_info {
     float stage_ms[8];    /* [1] warm-start prediction and choice (OTM_WS_LEARNED), [2] setup and solve,
                              [4] tensor, sensitivity and OC update, [7] total; others 0 */
     int kernel_launches;  /* CUDA kernels this call launched (graph kernel nodes counted per execution) */
-    int ws_choice;        /* start chosen per load case i, 2 bits at 2i: 0 zero, 1 previous solution,
-                             2 predictor, 3 previous + predictor change (OTM_WS_LEARNED only) */
+    int ws_choice;        /* OTM_WS_LEARNED with a predictor: start chosen per load case i, 2 bits at
+                             2i: 0 zero, 1 previous solution, 2 predictor, 3 previous + predictor
+                             change; bit 6 set: the predictor was skipped this iteration (back-off) */
 } otm_step_info;
 
 /* State of Alg. 1's adaptive volume bound. */
@@ -382,9 +383,16 @@ OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float*
 OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* target,
                                  double target_scale, double* loss, void* stream);
 /* Attach a network (grid n equal to the context's) as the predictor used by
- * OTM_WS_LEARNED, with chi_i ~ scale * y_i; NULL detaches.  The context
- * borrows the network: keep it alive while attached, and do not run other
- * calls on it concurrently with the context's steps. */
+ * OTM_WS_LEARNED, with chi_i ~ scale * y_i; NULL detaches.  Each design
+ * iteration that runs the predictor scores four starts per load case by
+ * their true residual ||f_i - K x_i|| (zero, the previous solution, the
+ * zero-mean prediction, the previous solution plus the prediction's change
+ * since the previous iteration) and starts PCG from the best.  A prediction
+ * that no load case uses doubles the number of following iterations that
+ * skip the predictor and start from the previous solution (up to 63); one
+ * that is used resets it.  The context borrows the network: keep it alive
+ * while attached, and do not run other calls on it concurrently with the
+ * context's steps. */
 OTM_API otm_status otm_set_predictor(otm_ctx* ctx, otm_unet* u, double scale);
 
 /* One 3x3x3 circular convolution of the network (operator-level test entry):

@@ -316,7 +316,7 @@ struct PcgScalars {
     int total;           // PCG iterations of this solve (all passes)
     int breakdown;       // bit i set: load case i broke down (pq <= 0 or non-finite)
     int flexible;        // 1: Polak-Ribiere beta
-    int pad;
+    int dev_err;         // set by a kernel whose bounded wait ran out
 };
 
 struct GovState {

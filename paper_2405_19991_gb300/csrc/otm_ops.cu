@@ -8,6 +8,7 @@
 
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
+#include "kernels_x2.cuh"
 #include "kernels_tiled.cuh"
 #include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
@@ -145,8 +146,14 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int tz = sizeof(R) == 4 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
-    if (tz > 0)   // the same kernel and launch shape the solver uses at this size
+    const int x2tz = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::x2_tz(n, sms, oc.max_blocks) : 0;
+    if (x2tz > 0) {   // the kernel and launch shape the solver uses at this size
+        otm::k_stencil_x2<false, otm::FinNone><<<otm::x2_grid(n, x2tz), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
+            n, x2tz, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
+        return finish(oc.st, "otm_op_apply_K");
+    }
+    const int tz = sizeof(R) == 4 && otm::stencil_choice() <= 1 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
+    if (tz > 0)
         otm::k_stencil_tiled<0, false, R, R, R, R, otm::FinNone>
             <<<(n / otm::kTX) * (n / otm::kTY) * (n / tz), dim3(otm::kTX, otm::kTY), 0, oc.st>>>(
                 n, tz, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});

@@ -15,6 +15,7 @@
 #include "kernels_tiled.cuh"
 #include "kernels_cluster.cuh"
 #include "kernels_warprow.cuh"
+#include "kernels_x2.cuh"
 #include "kernels_ws.cuh"
 #include "otm_internal.cuh"
 #include "unet_api.cuh"
@@ -173,6 +174,12 @@ class Solver : public SolverBase {
     PcgScalars* ps_c = nullptr;
     WsState* ws = nullptr;
     WsState* ws_h = nullptr;
+    // back-off: after a prediction that no load case used, the next
+    // ws_period - 1 iterations skip the predictor (ws_period doubles up to
+    // kWsMaxPeriod); a prediction that is used resets it to 1
+    static constexpr int kWsMaxPeriod = 64;
+    int ws_period = 1, ws_wait = 0;
+    int y_iter = -2;   // design iteration of the prediction held in ynet[ycur ^ 1]
     GovState gov_init;
     cudaEvent_t ev[8] = {};
 
@@ -227,6 +234,7 @@ class Solver : public SolverBase {
         return q * q * sizeof(C) <= 24 * 1024 ? q * q * sizeof(C) : 0;
     }
     int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
+    int x2tz_ = 0;   // z-planes per CTA of the paired-node fine stencil (FP32 fields), 0: not used
     // warp-row kernels on the finest grid (FP32 / mixed paths, 128 | n)
     bool wr_ = false;
     int wr_grid(long long warps) const {
@@ -263,7 +271,8 @@ class Solver : public SolverBase {
         OTM_CU(cudaGetDevice(&device));
         OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
         max_blocks = sm_count * 8;
-        tz_ = tiled_tz(pin.n, sm_count, max_blocks);
+        tz_ = stencil_choice() <= 1 ? tiled_tz(pin.n, sm_count, max_blocks) : 0;
+        if (std::is_same<R, float>::value && stencil_choice() == 0) x2tz_ = x2_tz(pin.n, sm_count, max_blocks);
         wr_ = warprow_ok(pin.n) && std::is_same<R, float>::value;
         if (pin.stream) {
             stream = (cudaStream_t)pin.stream;
@@ -612,7 +621,10 @@ class Solver : public SolverBase {
         if (N % 4 == 0) launch_pdl(k_update_p4<R, S>, grid(N / 4), 256, stream, N, p, z, ps);
         else launch_pdl(k_update_p<R, S>, grid(N), 256, stream, N, p, z, ps);
         ++nl_;
-if (tz_ > 0 && std::is_same<R, float>::value)
+if (x2tz_ > 0)
+            launch_pdl(k_stencil_x2<true, FinAlpha>, x2_grid(n, x2tz_), dim3(kX2T, kX2Y), stream, n, x2tz_,
+                       (const float*)kf, (const float*)p, (float*)q, rb, FinAlpha{ps});
+        else if (tz_ > 0 && std::is_same<R, float>::value)
             launch_pdl(k_stencil_tiled<0, true, R, R, R, R, FinAlpha>, tiled_grid(), dim3(kTX, kTY), stream, n, tz_,
                        kf, p, (const R*)nullptr, q, rb, FinAlpha{ps});
         else
@@ -674,6 +686,10 @@ if (tz_ > 0 && std::is_same<R, float>::value)
     otm_status read_ps() {
         OTM_CU(cudaMemcpyAsync(ps_h, ps, sizeof(PcgScalars), cudaMemcpyDeviceToHost, stream));
         OTM_CU(cudaStreamSynchronize(stream));
+        if (ps_h->dev_err) {
+            err = "a bounded device wait ran out (asynchronous copy did not complete)";
+            return OTM_ETIMEOUT;
+        }
         return OTM_OK;
     }
 
@@ -910,7 +926,9 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         const long long u0 = unet_launches();
         OTM_TRY(unet_predict(predictor, rho_f, std::is_same<R, double>::value, y, stream));
         nl_ += unet_launches() - u0;
-        const bool delta = have_prev_x && have_y;
+        // the change of the prediction is only meaningful against the
+        // previous iteration's prediction
+        const bool delta = have_prev_x && have_y && y_iter == iteration - 1;
         RedBuf rb = rbuf();
         auto score = [&](const R* xh, const R* xlo, int slot) -> otm_status {
             ++nl_;
@@ -937,7 +955,20 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         OTM_CU(cudaMemcpyAsync(ws_h, ws, sizeof(WsState), cudaMemcpyDeviceToHost, stream));
         ycur ^= 1;
         have_y = true;
+        y_iter = iteration;
         return OTM_OK;
+    }
+
+    // after the solve (ws_h is current): update the back-off
+    void ws_after_prediction() {
+        bool used = false;
+        for (int i = 0; i < 3; ++i) used |= ws_h->choice[i] == kWsNet || ws_h->choice[i] == kWsDelta;
+        if (used) {
+            ws_period = 1;
+        } else {
+            ws_period = ws_period * 2 > kWsMaxPeriod ? kWsMaxPeriod : ws_period * 2;
+        }
+        ws_wait = ws_period - 1;
     }
 
     otm_status set_predictor(otm_unet* u, double scale) override {
@@ -962,6 +993,8 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         predictor = u;
         pred_scale = scale;
         have_y = false;
+        ws_period = 1;
+        ws_wait = 0;
         return OTM_OK;
     }
 
@@ -1039,8 +1072,14 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         const long long nl0 = nl_;
         OTM_CU(cudaEventRecord(ev[0], stream));
         const bool warm = have_prev && prm.warm_start != OTM_WS_NONE;
-        const bool learned = prm.warm_start == OTM_WS_LEARNED && predictor != nullptr;
+        const bool attached = prm.warm_start == OTM_WS_LEARNED && predictor != nullptr;
+        const bool learned = attached && (!warm || ws_wait == 0);
         otm_status sst = setup_and_solve(warm, &loc, learned);
+        if (learned && (sst == OTM_OK || sst == OTM_ENOCONV)) ws_after_prediction();
+        else if (attached) {
+            --ws_wait;
+            loc.ws_choice = 1 | (1 << 2) | (1 << 4) | (1 << 6);   // previous start, predictor skipped
+        }
         if (sst != OTM_OK && sst != OTM_ENOCONV) return sst;
         have_prev = true;
         OTM_CU(cudaEventRecord(ev[2], stream));
@@ -1123,6 +1162,8 @@ if (tz_ > 0 && std::is_same<R, float>::value)
         iteration = h.iteration;
         have_prev = h.have_prev != 0;
         have_y = false;
+        ws_period = 1;
+        ws_wait = 0;
         return OTM_OK;
     }
 

@@ -9,8 +9,9 @@ the buffers (torch device tensors).
   buf = PairBuffer(n=128, capacity=256)
   collect(params, rho0, iters=40, buf=buf)          # one design history
   u = otm.otm_unet_create(128, (16, 32, 64, 128), seed=0)
-  train(u, buf, steps=500, lr=1e-3, scale=128.0)
-  otm.otm_set_predictor(ctx, u, 128.0)
+  scale = target_scale(buf)
+  train(u, buf, steps=500, lr=1e-3, scale=scale)
+  otm.otm_set_predictor(ctx, u, scale)
 """
 from __future__ import annotations
 
@@ -56,6 +57,14 @@ def collect(params, rho0: np.ndarray, iters: int, buf: PairBuffer, every: int = 
     finally:
         otm.otm_destroy(ctx)
     return infos
+
+
+def target_scale(buf: PairBuffer, sample: int = 8) -> float:
+    """Root mean square of the stored solutions over up to `sample` pairs
+    (host copies): the scale that gives the network unit-variance targets."""
+    idx = np.linspace(0, buf.count - 1, min(sample, buf.count)).astype(int)
+    ms = [float(np.mean(buf.t[i].cpu().numpy().astype(np.float64) ** 2)) for i in idx]
+    return float(np.sqrt(np.mean(ms))) if ms and np.mean(ms) > 0 else 1.0
 
 
 def train(u, buf: PairBuffer, steps: int, lr: float, scale: float, seed: int = 0, stream=None):
