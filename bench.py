@@ -244,6 +244,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
             names = {0: "zero", 1: "previous", 2: "predictor", 3: "previous+change"}
             rec["start_choices"] = {names[k]: v for k, v in sorted(counts.items())}
             rec["iterations_predictor_skipped"] = int(sum(1 for i in infos if i["ws_skipped"]))
+            rec["predictions_that_paid"] = int(sum(1 for i in infos if i["ws_paid"]))
         out[name] = rec
 
     form("plain_fp32_cold_start", 1, otm.OTM_WS_NONE)

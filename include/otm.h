@@ -139,7 +139,8 @@ typedef struct otm_step_info {
     int kernel_launches;  /* CUDA kernels this call launched (graph kernel nodes counted per execution) */
     int ws_choice;        /* OTM_WS_LEARNED with a predictor: start chosen per load case i, 2 bits at
                              2i: 0 zero, 1 previous solution, 2 predictor, 3 previous + predictor
-                             change; bit 6 set: the predictor was skipped this iteration (back-off) */
+                             change; bit 6 set: the predictor was skipped this iteration (back-off);
+                             bit 7 set: the prediction paid (see otm_set_predictor) */
 } otm_step_info;
 
 /* State of Alg. 1's adaptive volume bound. */
@@ -388,9 +389,10 @@ OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* targe
  * their true residual ||f_i - K x_i|| (zero, the previous solution, the
  * zero-mean prediction, the previous solution plus the prediction's change
  * since the previous iteration) and starts PCG from the best.  A prediction
- * that no load case uses doubles the number of following iterations that
- * skip the predictor and start from the previous solution (up to 63); one
- * that is used resets it.  The context borrows the network: keep it alive
+ * that does not pay -- for no load case is its residual norm at most a
+ * quarter of the best start without it -- doubles the number of following
+ * iterations that skip the predictor and start from the previous solution
+ * (up to 63); one that pays resets it.  The context borrows the network: keep it alive
  * while attached, and do not run other calls on it concurrently with the
  * context's steps. */
 OTM_API otm_status otm_set_predictor(otm_ctx* ctx, otm_unet* u, double scale);

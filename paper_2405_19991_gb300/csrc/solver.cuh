@@ -180,6 +180,7 @@ class Solver : public SolverBase {
     static constexpr int kWsMaxPeriod = 64;
     int ws_period = 1, ws_wait = 0;
     int y_iter = -2;   // design iteration of the prediction held in ynet[ycur ^ 1]
+    bool ws_had_prev = false, ws_had_delta = false;   // candidates scored by the last prediction
     GovState gov_init;
     cudaEvent_t ev[8] = {};
 
@@ -945,6 +946,8 @@ if (x2tz_ > 0)
             OTM_LAUNCH();
             return score(xc, nullptr, mode);
         };
+        ws_had_prev = have_prev_x;
+        ws_had_delta = delta;
         OTM_TRY(cand(kWsNet, xc_net));
         if (have_prev_x) OTM_TRY(score(x, xl, kWsPrev));
         if (delta) OTM_TRY(cand(kWsDelta, xc_delta));
@@ -959,16 +962,27 @@ if (x2tz_ > 0)
         return OTM_OK;
     }
 
-    // after the solve (ws_h is current): update the back-off
-    void ws_after_prediction() {
+    // after the solve (ws_h is current): update the back-off.  A prediction
+    // pays when, for some load case, its residual norm is at most a quarter
+    // of the best start without it (about half a PCG iteration saved at the
+    // V-cycle's contraction); a smaller gain is still used for the start but
+    // does not reset the back-off.
+    bool ws_after_prediction() {
         bool used = false;
-        for (int i = 0; i < 3; ++i) used |= ws_h->choice[i] == kWsNet || ws_h->choice[i] == kWsDelta;
+        for (int i = 0; i < 3; ++i) {
+            double best_np = ws_h->cand[kWsNet][3 + i];   // zero start
+            if (ws_had_prev) best_np = std::min(best_np, ws_h->cand[kWsPrev][i]);
+            double best_p = ws_h->cand[kWsNet][i];
+            if (ws_had_delta) best_p = std::min(best_p, ws_h->cand[kWsDelta][i]);
+            used |= best_p <= best_np / 16.0;
+        }
         if (used) {
             ws_period = 1;
         } else {
             ws_period = ws_period * 2 > kWsMaxPeriod ? kWsMaxPeriod : ws_period * 2;
         }
         ws_wait = ws_period - 1;
+        return used;
     }
 
     otm_status set_predictor(otm_unet* u, double scale) override {
@@ -1075,7 +1089,9 @@ if (x2tz_ > 0)
         const bool attached = prm.warm_start == OTM_WS_LEARNED && predictor != nullptr;
         const bool learned = attached && (!warm || ws_wait == 0);
         otm_status sst = setup_and_solve(warm, &loc, learned);
-        if (learned && (sst == OTM_OK || sst == OTM_ENOCONV)) ws_after_prediction();
+        if (learned && (sst == OTM_OK || sst == OTM_ENOCONV)) {
+            if (ws_after_prediction()) loc.ws_choice |= 1 << 7;
+        }
         else if (attached) {
             --ws_wait;
             loc.ws_choice = 1 | (1 << 2) | (1 << 4) | (1 << 6);   // previous start, predictor skipped

@@ -73,7 +73,7 @@ class otm_step_info(C.Structure):
                     resid=list(self.resid), stage_ms=list(self.stage_ms),
                     kernel_launches=self.kernel_launches,
                     ws_choice=[(self.ws_choice >> (2 * i)) & 3 for i in range(3)],
-                    ws_skipped=bool(self.ws_choice & 64))
+                    ws_skipped=bool(self.ws_choice & 64), ws_paid=bool(self.ws_choice & 128))
 
 
 class otm_governor_state(C.Structure):

@@ -321,13 +321,12 @@ def test_learned_trajectory_matches_previous_start():
             assert a.g == pytest.approx(b.g, rel=1e-3), it
             d = a.as_dict()
             # the back-off rule: predict when there is no previous solution or
-            # the wait is over; a used prediction resets the period to 1, an
-            # unused one doubles it (at most 64)
+            # the wait is over; a prediction that pays resets the period to 1,
+            # one that does not doubles it (at most 64)
             predicted = it == 0 or wait == 0
             assert d["ws_skipped"] == (not predicted), it
             if predicted:
-                used = any(c in (2, 3) for c in d["ws_choice"])
-                period = 1 if used else min(2 * period, 64)
+                period = 1 if d["ws_paid"] else min(2 * period, 64)
                 wait = period - 1
             else:
                 wait -= 1
