@@ -23,13 +23,15 @@ template <class S, class C>
 struct ClusterArgs {
     int lc, L;                 // first level run here, coarsest level
     int minv_smem;             // 1: stage the coarsest inverse in shared memory
-    int pad;
+    int lb;                    // levels lb..L run in CTA 0 with shared-memory fields (lb > L: none)
     int n[kMaxLevelsDev];
     S* T[kMaxLevelsDev];
     S* F[kMaxLevelsDev];
     S* Rr[kMaxLevelsDev];
     const S* A[kMaxLevelsDev];
     const C* Minv;
+    // shared-memory tail layout (byte offsets, from tail_layout on the host)
+    unsigned tT[kMaxLevelsDev], tF[kMaxLevelsDev], tA[kMaxLevelsDev], tR, tMinv;
 };
 
 // Cluster-wide barrier.  The arrive has release and the wait acquire
@@ -52,6 +54,98 @@ __device__ __forceinline__ void cl_gs_pass(int n, int colour, const S* A, const 
     }
 }
 
+// Byte offsets of the shared-memory tail's arrays: per level l in lb..L the
+// fields T_l and F_l (3 N_l values each) and the stencil A_l (27 N_l), one
+// residual buffer of 3 N_lb values reused by every level, then the staged
+// coarsest inverse.  Each array starts on a 16-byte boundary.
+struct TailLayout {
+    size_t T[kMaxLevelsDev], F[kMaxLevelsDev], A[kMaxLevelsDev], R, minv, total;
+};
+template <class S, class C>
+inline TailLayout tail_layout(int lb, int L, const int* n, int minv_smem) {
+    TailLayout t = {};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 15) / 16 * 16;
+        return o;
+    };
+    for (int l = lb; l <= L; ++l) {
+        const size_t m = 3 * (size_t)n[l] * n[l] * n[l] * sizeof(S);
+        t.T[l] = take(m);
+        t.F[l] = take(m);
+        t.A[l] = take(9 * m);
+    }
+    t.R = take(3 * (size_t)n[lb] * n[lb] * n[lb] * sizeof(S));
+    const size_t q = (size_t)n[L] * n[L] * n[L] - 1;
+    t.minv = off;
+    if (minv_smem) take(q * q * sizeof(C));
+    t.total = off;
+    return t;
+}
+
+// Levels lb..L (including the coarsest solve) in one CTA: the fields and the
+// stencils live in shared memory (copied in once per V-cycle), and phases are
+// separated by __syncthreads instead of cluster barriers or kernel
+// boundaries.  Reads F_lb and A_lb..A_L from, and writes T_lb to, global
+// memory.
+template <class S, class C>
+__device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm) {
+    const int t0 = threadIdx.x, ts = blockDim.x;
+    auto Ts = [&](int l) { return reinterpret_cast<S*>(sm + a.tT[l]); };
+    auto Fs = [&](int l) { return reinterpret_cast<S*>(sm + a.tF[l]); };
+    auto As = [&](int l) { return reinterpret_cast<const S*>(sm + a.tA[l]); };
+    S* Rs = reinterpret_cast<S*>(sm + a.tR);
+    {
+        const int nb = a.n[a.lb];
+        const int m = 3 * nb * nb * nb;
+        for (int i = t0; i < m; i += ts) Fs(a.lb)[i] = a.F[a.lb][i];
+        for (int l = a.lb; l <= a.L; ++l) {
+            const int ma = 27 * a.n[l] * a.n[l] * a.n[l];
+            S* dst = reinterpret_cast<S*>(sm + a.tA[l]);
+            for (int i = t0; i < ma; i += ts) dst[i] = a.A[l][i];
+        }
+    }
+    __syncthreads();
+    for (int l = a.lb; l < a.L; ++l) {
+        const int n = a.n[l];
+        const size_t N = (size_t)n * n * n;
+        cl_gs_pass<true, S>(n, 0, As(l), Fs(l), Ts(l), t0, ts);
+        __syncthreads();
+        for (int c = 1; c < 8; ++c) {
+            cl_gs_pass<false, S>(n, c, As(l), Fs(l), Ts(l), t0, ts);
+            __syncthreads();
+        }
+        for (int t = t0; t < (int)N; t += ts)
+            residual_stencil_node<S, S, S, S>(n, N, t % n, (t / n) % n, t / (n * n), As(l), Fs(l), Ts(l), Rs);
+        __syncthreads();
+        const int nc = n / 2;
+        for (int t = t0; t < nc * nc * nc; t += ts)
+            restrict_node<S, S>(nc, t % nc, (t / nc) % nc, t / (nc * nc), Rs, Fs(l + 1));
+        __syncthreads();
+    }
+    {
+        const int nL = a.n[a.L];
+        const C* Minv = stage_minv<C>(a.Minv, nL * nL * nL - 1, a.minv_smem, sm + a.tMinv);
+        coarse_solve_block<C, S, S>(nL, Minv, Fs(a.L), Ts(a.L));
+    }
+    __syncthreads();
+    for (int l = a.L - 1; l >= a.lb; --l) {
+        const int n = a.n[l];
+        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), Ts(l + 1), Ts(l));
+        __syncthreads();
+        for (int c = 7; c >= 0; --c) {
+            cl_gs_pass<false, S>(n, c, As(l), Fs(l), Ts(l), t0, ts);
+            __syncthreads();
+        }
+    }
+    {
+        const int nb = a.n[a.lb];
+        const int m = 3 * nb * nb * nb;
+        for (int i = t0; i < m; i += ts) a.T[a.lb][i] = Ts(a.lb)[i];
+    }
+}
+
 template <class S, class C>
 __global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kClusterThreads)
 k_coarse_cluster(ClusterArgs<S, C> a) {
@@ -59,8 +153,9 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
     extern __shared__ __align__(16) unsigned char cl_sm[];
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int ts = gridDim.x * blockDim.x;
+    const int lend = a.lb <= a.L ? a.lb : a.L;   // first level not swept by the whole cluster
     // down: forward sweep, residual, restriction
-    for (int l = a.lc; l < a.L; ++l) {
+    for (int l = a.lc; l < lend; ++l) {
         const int n = a.n[l];
         const size_t N = (size_t)n * n * n;
         cl_gs_pass<true, S>(n, 0, a.A[l], a.F[l], a.T[l], t0, ts);
@@ -77,15 +172,19 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
             restrict_node<S, S>(nc, t % nc, (t / nc) % nc, t / (nc * nc), a.Rr[l], a.F[l + 1]);
         cluster_barrier();
     }
-    // coarsest: dense solve in CTA 0
+    // coarsest: dense solve in CTA 0, or the shared-memory tail lb..L
     if (blockIdx.x == 0) {
-        const int nL = a.n[a.L];
-        const C* Minv = stage_minv<C>(a.Minv, nL * nL * nL - 1, a.minv_smem, cl_sm);
-        coarse_solve_block<C, S, S>(nL, Minv, a.F[a.L], a.T[a.L]);
+        if (a.lb <= a.L) {
+            coarse_tail_block<S, C>(a, cl_sm);
+        } else {
+            const int nL = a.n[a.L];
+            const C* Minv = stage_minv<C>(a.Minv, nL * nL * nL - 1, a.minv_smem, cl_sm);
+            coarse_solve_block<C, S, S>(nL, Minv, a.F[a.L], a.T[a.L]);
+        }
     }
     cluster_barrier();
     // up: prolongation + correction, reverse sweep
-    for (int l = a.L - 1; l >= a.lc; --l) {
+    for (int l = lend - 1; l >= a.lc; --l) {
         const int n = a.n[l];
         for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), a.T[l + 1], a.T[l]);
         cluster_barrier();

@@ -229,6 +229,32 @@ class Solver : public SolverBase {
             if (sz[l] <= cluster_maxn) return l;
         return L;
     }
+    // First level of the cluster kernel's shared-memory tail (CTA 0 runs
+    // levels lb..L with shared-memory fields): the first cluster level with
+    // at most tail_maxn nodes per side whose tail fits the shared-memory
+    // budget; L + 1 when none (or no cluster).  OTM_TAIL_MAXN overrides
+    // tail_maxn (0 disables the tail).
+    int tail_maxn = 8;
+    static constexpr size_t kTailSmemBudget = 200 * 1024;
+    int tail_lb() const {
+        const int L = nlev - 1;
+        const int lc = cluster_lc();
+        if (lc > L || tail_maxn <= 0) return L + 1;
+        int szs[kMaxLevelsDev] = {};
+        for (int l = 0; l <= L; ++l) szs[l] = sz[l];
+        const int mv = minv_smem_bytes(L) > 0 ? 1 : 0;
+        for (int l = lc; l <= L; ++l)
+            if (sz[l] <= tail_maxn && tail_layout<S, C>(l, L, szs, mv).total <= kTailSmemBudget) return l;
+        return L + 1;
+    }
+    size_t cluster_smem_bytes() const {
+        const int L = nlev - 1;
+        const int lb = tail_lb();
+        if (lb > L) return minv_smem_bytes(L);
+        int szs[kMaxLevelsDev] = {};
+        for (int l = 0; l <= L; ++l) szs[l] = sz[l];
+        return tail_layout<S, C>(lb, L, szs, minv_smem_bytes(L) > 0 ? 1 : 0).total;
+    }
     size_t minv_smem_bytes(int l) const {
         const size_t q = Nl[l] - 1;
         // staged inverse; with the kernel's static arrays this stays within 48 KB
@@ -290,6 +316,8 @@ class Solver : public SolverBase {
             use_cluster = !(nc && nc[0] == '1');
             const char* cm = getenv("OTM_CLUSTER_MAXN");
             if (cm) cluster_maxn = atoi(cm);
+            const char* tm = getenv("OTM_TAIL_MAXN");
+            if (tm) tail_maxn = atoi(tm);
         }
 
         OTM_TRY(alloc(rho, N));
@@ -328,6 +356,22 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(Bs_d, 8 * 64));
         OTM_CU(cudaMemcpyAsync(Ps_d, Psc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
         OTM_CU(cudaMemcpyAsync(Bs_d, Bsc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
+        {
+            // Opt in to exactly the dynamic shared memory the cluster kernel
+            // will be launched with (static + dynamic may exceed the default
+            // 48 KB); drop the shared-memory tail if the device cannot hold it.
+            cudaFuncAttributes fa;
+            OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_cluster<S, C>));
+            int optin = 0;
+            OTM_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+            if (fa.sharedSizeBytes + cluster_smem_bytes() > (size_t)optin) tail_maxn = 0;
+            const size_t cs = cluster_smem_bytes();
+            if (fa.sharedSizeBytes + cs > (size_t)optin) {
+                err = "the coarse-level kernel does not fit the device's shared memory";
+                return OTM_ECUDA;
+            }
+            OTM_CU(cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+        }
         OTM_TRY(alloc(partials, (size_t)max_blocks * kRedMaxVals));
         OTM_TRY(alloc(counter, 4));
         OTM_TRY(alloc(ps, 1));
@@ -549,6 +593,19 @@ class Solver : public SolverBase {
             ca.lc = lc;
             ca.L = L;
             ca.minv_smem = minv_smem_bytes(L) > 0 ? 1 : 0;
+            ca.lb = tail_lb();
+            if (ca.lb <= L) {
+                int szs[kMaxLevelsDev] = {};
+                for (int l = 0; l <= L; ++l) szs[l] = sz[l];
+                const TailLayout tl = tail_layout<S, C>(ca.lb, L, szs, ca.minv_smem);
+                for (int l = ca.lb; l <= L; ++l) {
+                    ca.tT[l] = (unsigned)tl.T[l];
+                    ca.tF[l] = (unsigned)tl.F[l];
+                    ca.tA[l] = (unsigned)tl.A[l];
+                }
+                ca.tR = (unsigned)tl.R;
+                ca.tMinv = (unsigned)tl.minv;
+            }
             for (int l = 0; l <= L; ++l) {
                 ca.n[l] = sz[l];
                 ca.T[l] = Tl[l];
@@ -558,7 +615,12 @@ class Solver : public SolverBase {
             }
             ca.Minv = Minv;
             ++nl_;
-            launch_pdl_smem(k_coarse_cluster<S, C>, kClusterCTAs, kClusterThreads, minv_smem_bytes(L), stream, ca);
+            const cudaError_t le =
+                launch_pdl_smem(k_coarse_cluster<S, C>, kClusterCTAs, kClusterThreads, cluster_smem_bytes(), stream, ca);
+            if (le != cudaSuccess) {
+                err = std::string("coarse-level cluster launch: ") + cudaGetErrorString(le);
+                return OTM_ECUDA;
+            }
         } else {
             ++nl_;
             launch_pdl_smem(k_coarse_solve<C, S, S>, 1, 1024, minv_smem_bytes(L), stream, sz[L], Minv, Fl[L], Tl[L],
