@@ -204,6 +204,48 @@ def timed_steps(otm, ctx, stream, steps, warmup):
     return e0.elapsed_time(e1), infos
 
 
+def run_batch(otm, args, count=64, iters=10):
+    """The batched workload: 64 designs with n drawn from {32, 48, 64, 96},
+    seeded SPD targets and volume fractions, FP32, `iters` OC iterations each,
+    through otm_design_batch with 1 (one design after another), 16, 32 and 64
+    host workers driving the designs' streams concurrently.  Aggregate OC
+    iterations per second over the host wall clock of the call, which
+    includes creating the 64 contexts and capturing their graphs (timed
+    alone as create_and_capture_s; steps_only subtracts it)."""
+    designs = W.batch_designs(count=count)
+    params, r0, keep = [], [], []
+    for d in designs:
+        params.append(otm.otm_params_default(n=d.n, precision=1, kappa_target=d.kappa_target, volfrac=d.volfrac,
+                                             rmin=2.0, cg_tol=1e-6, cg_maxit=500))
+        a = d.rho0(np.float32)
+        keep.append(a)
+        r0.append(a.ctypes.data)
+    rec = {"designs": count, "iters_each": iters, "sizes": sorted({d.n for d in designs}),
+           "unit": "OC iterations/s (all designs)"}
+    prev = os.environ.get("OTM_BATCH_WORKERS")
+    t0 = time.perf_counter()
+    otm.otm_design_batch(params, r0, 0, [None] * count, allow=(0, 4))   # contexts and graphs only
+    t_setup = time.perf_counter() - t0
+    rec["create_and_capture_s"] = t_setup
+    for workers in (1, 16, 32, 64):
+        os.environ["OTM_BATCH_WORKERS"] = str(workers)
+        t0 = time.perf_counter()
+        kaps, infos, st = otm.otm_design_batch(params, r0, iters, [None] * count, allow=(0, 4))
+        dt = time.perf_counter() - t0
+        rec[f"workers_{workers}"] = {
+            "value": count * iters / dt, "wall_s": dt,
+            "steps_only": count * iters / max(dt - t_setup, 1e-9),
+            "mean_cg_iters": float(np.mean([list(infos[i].cg_iters) for i in range(count * iters)]))}
+    if prev is None:
+        os.environ.pop("OTM_BATCH_WORKERS", None)
+    else:
+        os.environ["OTM_BATCH_WORKERS"] = prev
+    best = max((v["value"], k) for k, v in rec.items() if k.startswith("workers_"))
+    rec["best"] = best[1]
+    rec["speedup_vs_sequential"] = best[0] / rec["workers_1"]["value"]
+    return rec
+
+
 def run_forms(args, wl, dev, stream, rank, plain_value):
     """Cold start, BF16 V-cycle, and learned warm start + BF16 V-cycle on the
     benchmark workload; the warm-start network (widths 16/32/64/128) is
@@ -248,6 +290,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
         out[name] = rec
 
     form("plain_fp32_cold_start", 1, otm.OTM_WS_NONE)
+    out["batch_64_designs"] = run_batch(otm, args)
     form("mixed_bf16_vcycle_previous_start", 2, otm.OTM_WS_PREV)
     # train the warm-start network on other seeds' histories
     t0 = time.perf_counter()

@@ -116,7 +116,9 @@ typedef struct otm_params {
     double gov_small_rel;    /* Alg. 1 is_small(g^[I-1] - g^[I]): |dg| < gov_small_rel * g (default 1e-3) */
     double gov_vol_tol;      /* Alg. 1 is_small(V - V*): |V - V*| < gov_vol_tol (default 1e-2) */
     int symmetry;            /* 1: central symmetry (Sec. 4.1), average rho and dg/drho over point-symmetric pairs */
-    int reserved0;
+    int coarse_smoother;     /* smoother of the coarse V-cycle levels (the finest level always runs the
+                                8-colour Gauss-Seidel of Sec. 2.4): 0 = 8-colour symmetric Gauss-Seidel,
+                                1 = degree-3 Chebyshev on D^-1 A with a Gershgorin bound (symmetric) */
     uint64_t seed;           /* seed of the learned predictor's initial weights */
     void* stream;            /* cudaStream_t to order work on; NULL = context-owned stream */
     int device;              /* CUDA device ordinal; -1 = current device */
@@ -224,7 +226,15 @@ OTM_API otm_status otm_run(otm_ctx* ctx, int iters, otm_step_info* infos);
  * rho0[d] (host, n_d^3 floats; NULL = uniform volfrac) describe design d;
  * rho_out[d] (host, may be NULL), kappa_out[d] (may be NULL: the tensor of
  * the last iteration) and infos[d*iters + i] (may be NULL) receive results.
- * Returns the first non-OK status (designs after it are still attempted).
+ * All contexts are created first (device allocation synchronises the
+ * device); then up to `workers` host threads (the environment variable
+ * OTM_BATCH_WORKERS, default min(count, 16); 1 = one design after another)
+ * each take the next design and step it on that design's own stream, so the
+ * designs' kernels run concurrently on the GPU.  Each design's results are
+ * bitwise those of running it alone (params[d].stream is ignored: every
+ * design gets a stream of its own).
+ * Returns the first non-OK status in design order (every design is still
+ * attempted).
  */
 OTM_API otm_status otm_design_batch(int count, const otm_params* params,
                                     const float* const* rho0, int iters,

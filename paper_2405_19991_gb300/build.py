@@ -72,7 +72,7 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
     if relink:
         tmp = LIB + ".tmp"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ["-gencode", "arch=compute_103a,code=sm_103a",
-                                                    "-Xcompiler", "-fPIC", "-lcudart"]
+                                                    "-Xcompiler", "-fPIC", "-lcudart", "-lpthread"]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)

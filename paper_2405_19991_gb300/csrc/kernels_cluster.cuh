@@ -24,11 +24,15 @@ struct ClusterArgs {
     int lc, L;                 // first level run here, coarsest level
     int minv_smem;             // 1: stage the coarsest inverse in shared memory
     int lb;                    // levels lb..L run in CTA 0 with shared-memory fields (lb > L: none)
+    int cheb;                  // 1: Chebyshev smoother on the cluster levels (else 8-colour GS)
     int n[kMaxLevelsDev];
     S* T[kMaxLevelsDev];
     S* F[kMaxLevelsDev];
     S* Rr[kMaxLevelsDev];
     const S* A[kMaxLevelsDev];
+    S* T2[kMaxLevelsDev];      // second field buffer and direction of the Chebyshev smoother
+    S* D[kMaxLevelsDev];
+    const float* lam;          // per-level Gershgorin bounds
     const C* Minv;
     // shared-memory tail layout (byte offsets, from tail_layout on the host)
     unsigned tT[kMaxLevelsDev], tF[kMaxLevelsDev], tA[kMaxLevelsDev], tR, tMinv;
@@ -154,18 +158,48 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     const int ts = gridDim.x * blockDim.x;
     const int lend = a.lb <= a.L ? a.lb : a.L;   // first level not swept by the whole cluster
+    static_assert(kChebDeg % 2 == 1, "the Chebyshev buffers alternate: an odd degree ends in T2");
+    // one Chebyshev smoothing of level l: steps alternate T -> T2 -> T ...;
+    // from_zero: the field starts at zero (pre-smoothing, ends in T2), else
+    // it starts in T2 (post-smoothing, ends in T)
+    auto cheb_smooth = [&](int l, bool from_zero) {
+        const int n = a.n[l];
+        const size_t N = (size_t)n * n * n;
+        for (int k = 0; k < kChebDeg; ++k) {
+            float c_d, c_r;
+            cheb_coef(a.lam[l], k, c_d, c_r);
+            const bool to_t2 = from_zero ? (k % 2 == 0) : (k % 2 == 1);
+            const S* Tin = to_t2 ? a.T[l] : a.T2[l];
+            S* Tout = to_t2 ? a.T2[l] : a.T[l];
+            for (int t = t0; t < (int)N; t += ts) {
+                if (from_zero && k == 0)
+                    cheb_node<true, S, S, S>(n, N, t % n, (t / n) % n, t / (n * n), a.A[l], a.F[l], Tin, Tout, a.D[l],
+                                             c_d, c_r);
+                else
+                    cheb_node<false, S, S, S>(n, N, t % n, (t / n) % n, t / (n * n), a.A[l], a.F[l], Tin, Tout,
+                                              a.D[l], c_d, c_r);
+            }
+            cluster_barrier();
+        }
+    };
     // down: forward sweep, residual, restriction
     for (int l = a.lc; l < lend; ++l) {
         const int n = a.n[l];
         const size_t N = (size_t)n * n * n;
-        cl_gs_pass<true, S>(n, 0, a.A[l], a.F[l], a.T[l], t0, ts);
-        cluster_barrier();
-        for (int c = 1; c < 8; ++c) {
-            cl_gs_pass<false, S>(n, c, a.A[l], a.F[l], a.T[l], t0, ts);
+        S* Tcur = a.T[l];
+        if (a.cheb) {
+            cheb_smooth(l, true);
+            Tcur = a.T2[l];
+        } else {
+            cl_gs_pass<true, S>(n, 0, a.A[l], a.F[l], a.T[l], t0, ts);
             cluster_barrier();
+            for (int c = 1; c < 8; ++c) {
+                cl_gs_pass<false, S>(n, c, a.A[l], a.F[l], a.T[l], t0, ts);
+                cluster_barrier();
+            }
         }
         for (int t = t0; t < (int)N; t += ts)
-            residual_stencil_node<S, S, S, S>(n, N, t % n, (t / n) % n, t / (n * n), a.A[l], a.F[l], a.T[l], a.Rr[l]);
+            residual_stencil_node<S, S, S, S>(n, N, t % n, (t / n) % n, t / (n * n), a.A[l], a.F[l], Tcur, a.Rr[l]);
         cluster_barrier();
         const int nc = n / 2;
         for (int t = t0; t < nc * nc * nc; t += ts)
@@ -186,11 +220,16 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
     // up: prolongation + correction, reverse sweep
     for (int l = lend - 1; l >= a.lc; --l) {
         const int n = a.n[l];
-        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), a.T[l + 1], a.T[l]);
+        S* Tcur = a.cheb ? a.T2[l] : a.T[l];
+        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), a.T[l + 1], Tcur);
         cluster_barrier();
-        for (int c = 7; c >= 0; --c) {
-            cl_gs_pass<false, S>(n, c, a.A[l], a.F[l], a.T[l], t0, ts);
-            cluster_barrier();
+        if (a.cheb) {
+            cheb_smooth(l, false);
+        } else {
+            for (int c = 7; c >= 0; --c) {
+                cl_gs_pass<false, S>(n, c, a.A[l], a.F[l], a.T[l], t0, ts);
+                cluster_barrier();
+            }
         }
     }
 }

@@ -152,6 +152,110 @@ k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
     }
 }
 
+// ---- Chebyshev polynomial smoother on a 27-point stencil level ----
+// A degree-kChebDeg Chebyshev iteration for D^-1 A on [lmax / kChebRatio,
+// lmax], with lmax the level's Gershgorin bound max_v sum_o |A_o(v)| / A_0(v)
+// (an upper bound of the spectrum of D^-1 A, so the polynomial never
+// amplifies).  Step k: r = f - A T; d = c_d d + c_r D^-1 r; T += d, with
+// theta = (lmax + lmin) / 2, delta = (lmax - lmin) / 2, sigma = theta / delta,
+// rho_0 = 1 / sigma, rho_k = 1 / (2 sigma - rho_{k-1}); c_d = rho_k rho_{k-1}
+// and c_r = 2 rho_k / delta for k > 0, c_d = 0 and c_r = 1 / theta for k = 0.
+// The same polynomial before and after the coarse correction keeps the
+// V-cycle symmetric, as plain PCG needs.  Each step reads T from one buffer
+// and writes the other (Jacobi-type), so a step is one pass over all nodes.
+constexpr int kChebDeg = 3;
+constexpr float kChebRatio = 30.0f;
+
+__host__ __device__ inline void cheb_coef(float lmax, int k, float& c_d, float& c_r) {
+    const float lmin = lmax / kChebRatio;
+    const float theta = 0.5f * (lmax + lmin), delta = 0.5f * (lmax - lmin);
+    const float sigma = theta / delta;
+    if (k == 0) {
+        c_d = 0.0f;
+        c_r = 1.0f / theta;
+        return;
+    }
+    float rho = 1.0f / sigma, rho_new = rho;
+    for (int i = 1; i <= k; ++i) {
+        rho_new = 1.0f / (2.0f * sigma - rho);
+        if (i < k) rho = rho_new;
+    }
+    c_d = rho_new * rho;
+    c_r = 2.0f * rho_new / delta;
+}
+
+// One Chebyshev step at node (x, y, z).  ZERO: T starts at zero (not read).
+template <bool ZERO, class AT, class FT, class TT>
+__device__ __forceinline__ void cheb_node(int n, size_t N, int x, int y, int z, const AT* __restrict__ A,
+                                          const FT* __restrict__ f, const TT* __restrict__ Tin,
+                                          TT* __restrict__ Tout, TT* __restrict__ D, float c_d, float c_r) {
+    using C = typename St<TT>::C;
+    const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    int xs[3], ys[3], zs[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d] = wrapd(x, d - 1, n);
+        ys[d] = wrapd(y, d - 1, n) * n;
+        zs[d] = wrapd(z, d - 1, n) * n * n;
+    }
+    C a[27];
+#pragma unroll
+    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+    const C inv = C(1) / a[13];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        C r = St<FT>::ld(f + (size_t)i * N, v);
+        C t0 = C(0), dv;
+        if (!ZERO) {
+            const TT* Ti = Tin + (size_t)i * N;
+#pragma unroll
+            for (int o = 0; o < 27; ++o) r -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
+            t0 = St<TT>::ld(Ti, v);
+            dv = C(c_d) * St<TT>::ld(D + (size_t)i * N, v) + C(c_r) * r * inv;
+        } else {
+            dv = C(c_r) * r * inv;
+        }
+        St<TT>::st(D + (size_t)i * N, v, dv);
+        St<TT>::st(Tout + (size_t)i * N, v, t0 + dv);
+    }
+}
+
+template <bool ZERO, class AT, class FT, class TT>
+__global__ void __launch_bounds__(256)
+k_cheb_stencil(int n, int k, const float* __restrict__ lam, const AT* __restrict__ A, const FT* __restrict__ f,
+               const TT* __restrict__ Tin, TT* __restrict__ Tout, TT* __restrict__ D) {
+    pdl_enter();
+    const size_t N = (size_t)n * n * n;
+    float c_d, c_r;
+    cheb_coef(*lam, k, c_d, c_r);
+    OTM_FOR_ROWS(row_, n * n) {
+        const int y = row_ % n, z = row_ / n;
+        OTM_FOR_X(x, n) cheb_node<ZERO, AT, FT, TT>(n, N, x, y, z, A, f, Tin, Tout, D, c_d, c_r);
+    }
+}
+
+// Gershgorin bound of D^-1 A: *lam = max(*lam, max_v sum_o |A_o(v)| / A_0(v))
+// (*lam starts at zero; positive floats order like their bit patterns).
+template <class AT>
+__global__ void __launch_bounds__(256)
+k_gershgorin(int n, const AT* __restrict__ A, float* __restrict__ lam) {
+    pdl_enter();
+    using C = typename St<AT>::C;
+    const size_t N = (size_t)n * n * n;
+    float g = 0.0f;
+    for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
+        C s = 0;
+#pragma unroll
+        for (int o = 0; o < 27; ++o) {
+            const C a = St<AT>::ld(A, (size_t)o * N + v);
+            s += a < C(0) ? -a : a;
+        }
+        g = fmaxf(g, (float)(s / St<AT>::ld(A, (size_t)13 * N + v)));
+    }
+    for (int o = 16; o > 0; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(lam), __float_as_int(g));
+}
+
 // ---- Gauss-Seidel colour pass on a 27-point stencil level ----
 // colour = (x%2) + 2(y%2) + 4(z%2); n even.  ZERO (colour 0 only): the field
 // starts at zero and the pass zeroes the other seven nodes of each 2x2x2 cell.

@@ -1,6 +1,9 @@
 // C ABI of libotm.so (declared in include/otm.h): argument checking,
 // context lifecycle and dispatch to the per-precision solvers.
+#include <atomic>
 #include <cmath>
+#include <cstdlib>
+#include <thread>
 #include <cstring>
 #include <new>
 #include <string>
@@ -67,6 +70,7 @@ std::string check_params(const otm_params* p) {
     if (!(p->gov_bound > 0.0 && p->gov_small_rel > 0.0 && p->gov_vol_tol > 0.0))
         return "governor thresholds must be positive";
     if (p->symmetry != 0 && p->symmetry != 1) return "symmetry must be 0 or 1";
+    if (p->coarse_smoother != 0 && p->coarse_smoother != 1) return "coarse_smoother must be 0 or 1";
     return "";
 }
 
@@ -109,6 +113,7 @@ otm_status otm_params_default(otm_params* p) {
     p->gov_small_rel = 1e-3;
     p->gov_vol_tol = 1e-2;
     p->symmetry = 0;
+    p->coarse_smoother = 0;
     p->seed = 0;
     p->stream = nullptr;
     p->device = -1;
@@ -225,32 +230,70 @@ otm_status otm_design_batch(int count, const otm_params* params, const float* co
         const std::string msg = check_params(&params[d]);
         if (!msg.empty()) return fail(OTM_EINVAL, "otm_design_batch: design " + std::to_string(d) + ": " + msg);
     }
+    std::vector<otm_ctx*> ctxs(count, nullptr);
+    std::vector<otm_status> stat(count, OTM_OK);
+    std::vector<std::string> msgs(count);
+    // contexts first: their allocations synchronise the device
+    for (int d = 0; d < count; ++d) {
+        otm_params p = params[d];
+        p.stream = nullptr;   // a stream of its own
+        stat[d] = otm_create_ex(&p, &ctxs[d]);
+        if (stat[d] != OTM_OK) msgs[d] = g_err;
+        if (stat[d] == OTM_OK && rho0 && rho0[d]) {
+            stat[d] = otm_set_density(ctxs[d], rho0[d], 0);
+            if (stat[d] != OTM_OK) msgs[d] = otm_last_error(ctxs[d]);
+        }
+        // graphs are built here, on the calling thread, before any worker starts
+        if (stat[d] == OTM_OK) {
+            stat[d] = ctxs[d]->s->prepare();
+            if (stat[d] != OTM_OK) msgs[d] = otm_last_error(ctxs[d]);
+        }
+    }
+    int workers = count < 16 ? count : 16;
+    if (const char* e = getenv("OTM_BATCH_WORKERS")) {
+        const int w = atoi(e);
+        if (w >= 1) workers = w < count ? w : count;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int d = next.fetch_add(1);
+            if (d >= count) break;
+            if (stat[d] != OTM_OK) continue;
+            otm_ctx* ctx = ctxs[d];
+            otm_status st = OTM_OK;
+            bool noconv = false;
+            otm_step_info last;
+            memset(&last, 0, sizeof(last));
+            for (int i = 0; st == OTM_OK && i < iters; ++i) {
+                const otm_status s2 = otm_step(ctx, &last);
+                if (infos) infos[(size_t)d * iters + i] = last;
+                if (s2 == OTM_ENOCONV) noconv = true;
+                else if (s2 != OTM_OK) st = s2;
+            }
+            if (st == OTM_OK && kappa_out)
+                for (int c = 0; c < 6; ++c) kappa_out[d][c] = last.kappa[c];
+            if (st == OTM_OK && rho_out && rho_out[d]) st = otm_get_density(ctx, rho_out[d], 0);
+            if (st != OTM_OK) msgs[d] = otm_last_error(ctx);
+            stat[d] = st != OTM_OK ? st : (noconv ? OTM_ENOCONV : OTM_OK);
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
     otm_status first = OTM_OK;
     std::string first_msg;
     for (int d = 0; d < count; ++d) {
-        otm_ctx* ctx = nullptr;
-        otm_status st = otm_create_ex(&params[d], &ctx);
-        if (st == OTM_OK && rho0 && rho0[d]) st = otm_set_density(ctx, rho0[d], 0);
-        otm_step_info last;
-        memset(&last, 0, sizeof(last));
-        for (int i = 0; st == OTM_OK && i < iters; ++i) {
-            otm_status s2 = otm_step(ctx, &last);
-            if (infos) infos[(size_t)d * iters + i] = last;
-            if (s2 == OTM_ENOCONV) {
-                if (first == OTM_OK) first = OTM_ENOCONV;
-            } else if (s2 != OTM_OK) {
-                st = s2;
-            }
+        if (stat[d] == OTM_ENOCONV && first == OTM_OK) first = OTM_ENOCONV;
+        if (stat[d] != OTM_OK && stat[d] != OTM_ENOCONV && (first == OTM_OK || first == OTM_ENOCONV)) {
+            first = stat[d];
+            first_msg = "design " + std::to_string(d) + ": " + msgs[d];
         }
-        if (st == OTM_OK && kappa_out) {
-            for (int c = 0; c < 6; ++c) kappa_out[d][c] = last.kappa[c];
-        }
-        if (st == OTM_OK && rho_out && rho_out[d]) st = otm_get_density(ctx, rho_out[d], 0);
-        if (st != OTM_OK && (first == OTM_OK || first == OTM_ENOCONV)) {
-            first = st;
-            first_msg = ctx ? std::string(otm_last_error(ctx)) : g_err;
-        }
-        otm_destroy(ctx);
+        otm_destroy(ctxs[d]);
     }
     if (first != OTM_OK && first != OTM_ENOCONV) g_err = "otm_design_batch: " + first_msg;
     return first;

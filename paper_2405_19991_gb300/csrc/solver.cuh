@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -24,6 +25,14 @@ namespace otm {
 
 constexpr int kMaxLevels = 12;
 
+// Graph capture and instantiation are done under one process-wide lock:
+// contexts stepped from several host threads (otm_design_batch) build their
+// graphs one at a time and only launch them concurrently.
+inline std::mutex& graph_build_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 // Abstract interface used by the C ABI.
 struct SolverBase {
     virtual ~SolverBase() {}
@@ -37,6 +46,9 @@ struct SolverBase {
     virtual otm_status get_state(void* buf) = 0;
     virtual otm_status set_state(const void* buf, size_t len) = 0;
     virtual otm_status set_predictor(otm_unet* u, double scale) = 0;
+    // Build the step's CUDA graphs now (they are otherwise built by the first
+    // step); graph construction is serialised process-wide.
+    virtual otm_status prepare() = 0;
     std::string err;
     otm_params prm;
     cudaStream_t stream = nullptr;
@@ -147,6 +159,9 @@ class Solver : public SolverBase {
     S *z = nullptr, *res0 = nullptr, *k_vc = nullptr;
     // coarse levels 1..nlev-1 (level 0 uses z / r / res0 / k_vc)
     S *Tl[kMaxLevels] = {}, *Fl[kMaxLevels] = {}, *Rl[kMaxLevels] = {}, *Al[kMaxLevels] = {};
+    S *T2l[kMaxLevels] = {}, *Dl[kMaxLevels] = {};   // Chebyshev smoother: second field buffer, direction
+    float* lam_d = nullptr;                          // per-level Gershgorin bounds of D^-1 A
+    bool cheb_ = false;                              // coarse levels smoothed by Chebyshev (coarse_smoother = 1)
     C *Kel[kMaxLevels] = {};
     C *Bs_d = nullptr, *Ps_d = nullptr, *Minv = nullptr;
     double* Wd = nullptr;
@@ -194,7 +209,7 @@ class Solver : public SolverBase {
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
         void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
-                        partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws};
+                        partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
         if (k_vc && (void*)k_vc != (void*)kf) cudaFree(k_vc);
@@ -202,6 +217,8 @@ class Solver : public SolverBase {
             if (Tl[l]) cudaFree(Tl[l]);
             if (Fl[l]) cudaFree(Fl[l]);
             if (Rl[l]) cudaFree(Rl[l]);
+            if (T2l[l]) cudaFree(T2l[l]);
+            if (Dl[l]) cudaFree(Dl[l]);
             if (Al[l]) cudaFree(Al[l]);
             if (Kel[l]) cudaFree(Kel[l]);
         }
@@ -283,6 +300,22 @@ class Solver : public SolverBase {
         return OTM_OK;
     }
 
+    // The shared-memory opt-in is one attribute of the kernel per device and
+    // process, shared by every context of this precision: only ever raise it
+    // (a smaller context created later must not lower it under a larger
+    // one).  This Solver instantiation lives in one translation unit, so the
+    // static below belongs to the kernel stub its launches go through.
+    otm_status raise_cluster_smem(size_t bytes) {
+        static std::mutex m;
+        static size_t granted[64] = {};
+        std::lock_guard<std::mutex> lock(m);
+        const int d = device >= 0 && device < 64 ? device : 0;
+        if (bytes <= granted[d]) return OTM_OK;
+        OTM_CU(cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        granted[d] = bytes;
+        return OTM_OK;
+    }
+
     otm_status init(const otm_params& pin) override {
         prm = pin;
         n = pin.n;
@@ -342,6 +375,10 @@ class Solver : public SolverBase {
             OTM_TRY(alloc(Tl[l], 3 * Nl[l]));
             OTM_TRY(alloc(Fl[l], 3 * Nl[l]));
             OTM_TRY(alloc(Rl[l], 3 * Nl[l]));
+            if (pin.coarse_smoother == 1) {
+                OTM_TRY(alloc(T2l[l], 3 * Nl[l]));
+                OTM_TRY(alloc(Dl[l], 3 * Nl[l]));
+            }
             OTM_TRY(alloc(Al[l], 27 * Nl[l]));
             OTM_TRY(alloc(Kel[l], 64 * Nl[l]));
         }
@@ -370,8 +407,10 @@ class Solver : public SolverBase {
                 err = "the coarse-level kernel does not fit the device's shared memory";
                 return OTM_ECUDA;
             }
-            OTM_CU(cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cs));
+            OTM_TRY(raise_cluster_smem(cs));
         }
+        cheb_ = pin.coarse_smoother == 1 && nlev > 1;
+        OTM_TRY(alloc(lam_d, kMaxLevels));
         OTM_TRY(alloc(partials, (size_t)max_blocks * kRedMaxVals));
         OTM_TRY(alloc(counter, 4));
         OTM_TRY(alloc(ps, 1));
@@ -532,6 +571,14 @@ class Solver : public SolverBase {
             }
         }
         const int L = nlev - 1;
+        if (cheb_) {
+            OTM_CU(cudaMemsetAsync(lam_d, 0, kMaxLevels * sizeof(float), stream));
+            for (int l = 1; l < L; ++l) {
+                ++nl_;
+                launch_pdl(k_gershgorin<S>, grid(Nl[l]), 256, stream, sz[l], (const S*)Al[l], lam_d + l);
+            }
+            OTM_LAUNCH();
+        }
         ++nl_;
         {
             const size_t q = Nl[L] - 1;
@@ -546,6 +593,23 @@ class Solver : public SolverBase {
 
     // z = V(r): one V-cycle of Alg. 3 with a forward 8-colour Gauss-Seidel
     // sweep before and the reverse sweep after the coarse correction.
+    // One Chebyshev smoothing of stencil level l (kChebDeg launches): from
+    // zero into T2 (pre-smoothing), or from T2 back into T (post-smoothing).
+    void cheb_smooth(int l, bool from_zero) {
+        for (int k = 0; k < kChebDeg; ++k) {
+            const bool to_t2 = from_zero ? (k % 2 == 0) : (k % 2 == 1);
+            const S* Tin = to_t2 ? Tl[l] : T2l[l];
+            S* Tout = to_t2 ? T2l[l] : Tl[l];
+            ++nl_;
+            if (from_zero && k == 0)
+                launch_pdl(k_cheb_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], k,
+                           (const float*)(lam_d + l), (const S*)Al[l], (const S*)Fl[l], Tin, Tout, Dl[l]);
+            else
+                launch_pdl(k_cheb_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], k,
+                           (const float*)(lam_d + l), (const S*)Al[l], (const S*)Fl[l], Tin, Tout, Dl[l]);
+        }
+    }
+
     otm_status vcycle() {
         const int L = nlev - 1;
         if (nlev == 1) {
@@ -575,14 +639,20 @@ class Solver : public SolverBase {
         const int lc = cluster_lc();   // levels lc..L run in one cluster launch (lc > L: none)
         const int Lsep = lc <= L ? lc : L;
         for (int l = 1; l < Lsep; ++l) {
-            ++nl_;
-            launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
-            for (int c = 1; c < 8; ++c) {
+            S* Tcur = Tl[l];
+            if (cheb_) {
+                cheb_smooth(l, true);
+                Tcur = T2l[l];
+            } else {
                 ++nl_;
-                launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
+                for (int c = 1; c < 8; ++c) {
+                    ++nl_;
+                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                }
             }
             ++nl_;
-            launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Al[l], Fl[l], Tl[l], Rl[l]);
+            launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Al[l], Fl[l], (const S*)Tcur, Rl[l]);
             ++nl_;
             launch_pdl(k_restrict<S, S>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1])), stream, sz[l + 1], Rl[l], Fl[l + 1]);
             OTM_LAUNCH();
@@ -594,6 +664,8 @@ class Solver : public SolverBase {
             ca.L = L;
             ca.minv_smem = minv_smem_bytes(L) > 0 ? 1 : 0;
             ca.lb = tail_lb();
+            ca.cheb = cheb_ ? 1 : 0;
+            ca.lam = lam_d;
             if (ca.lb <= L) {
                 int szs[kMaxLevelsDev] = {};
                 for (int l = 0; l <= L; ++l) szs[l] = sz[l];
@@ -611,6 +683,8 @@ class Solver : public SolverBase {
                 ca.T[l] = Tl[l];
                 ca.F[l] = Fl[l];
                 ca.Rr[l] = Rl[l];
+                ca.T2[l] = T2l[l];
+                ca.D[l] = Dl[l];
                 ca.A[l] = Al[l];
             }
             ca.Minv = Minv;
@@ -629,10 +703,15 @@ class Solver : public SolverBase {
         OTM_LAUNCH();
         for (int l = Lsep - 1; l >= 1; --l) {
             ++nl_;
-            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1], Tl[l]);
-            for (int c = 7; c >= 0; --c) {
-                ++nl_;
-                launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
+                       cheb_ ? T2l[l] : Tl[l]);
+            if (cheb_) {
+                cheb_smooth(l, false);
+            } else {
+                for (int c = 7; c >= 0; --c) {
+                    ++nl_;
+                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                }
             }
             OTM_LAUNCH();
         }
@@ -882,8 +961,11 @@ if (x2tz_ > 0)
         return OTM_OK;
     }
 
+    otm_status prepare() override { return use_graphs ? ensure_graphs() : OTM_OK; }
+
     otm_status ensure_graphs() {
         if (gx_first) return OTM_OK;
+        std::lock_guard<std::mutex> lock(graph_build_mutex());
         OTM_TRY(capture_pass(true, 0, &gx_first, &nlg_first));
         OTM_TRY(capture_pass(false, 1, &gx_pass, &nlg_pass));
         OTM_TRY(capture_tail());
@@ -911,6 +993,7 @@ if (x2tz_ > 0)
         if (learned) {
             if (use_graphs) {
                 OTM_TRY(ensure_graphs());
+                std::unique_lock<std::mutex> lock(graph_build_mutex());
                 if (!gx_setup) OTM_TRY(capture_seq(true, &gx_setup, &nlg_setup));
                 if (!gx_solve0) {
                     long long fixed = 0;
@@ -919,6 +1002,7 @@ if (x2tz_ > 0)
                     nlg_solve0 = fixed;
                     nlg_body = body;
                 }
+                lock.unlock();
                 OTM_CU(cudaGraphLaunch(gx_setup, stream));
                 nl_ += nlg_setup;
             } else {

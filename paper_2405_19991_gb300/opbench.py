@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--dtype", type=int, default=1, help="1 = FP32, 0 = FP64; precision for --op step (2 = mixed)")
     ap.add_argument("--colour", type=int, default=8, help="--op gs: colour (0-7) or group pass 8 + g")
     ap.add_argument("--widths", default="16,32,64,128", help="--op unet*: network widths")
+    ap.add_argument("--smoother", type=int, default=0, help="--op step: coarse_smoother (0 GS, 1 Chebyshev)")
     ap.add_argument("--cin", type=int, default=16)
     ap.add_argument("--cout", type=int, default=16)
     args = ap.parse_args()
@@ -64,7 +65,7 @@ def main():
         yc = torch.empty((N, args.cout), dtype=torch.bfloat16, device=dev)
     if args.op == "step":
         p = otm.otm_params_default(n=n, precision=args.dtype, kappa_target=W.TARGET_ORTHOTROPIC, rmin=2.0,
-                                   stream=st.cuda_stream)
+                                   stream=st.cuda_stream, coarse_smoother=args.smoother)
         ctx = otm.otm_create_ex(p)
         r0 = W.initial_density(n, 0.3, 1).astype(np.float32)
         otm.otm_set_density(ctx, r0.ctypes.data, 0)
@@ -102,6 +103,9 @@ def main():
     e1.record(st)
     torch.cuda.synchronize()
     print(f"{args.op} n={n}: {e0.elapsed_time(e1) / args.reps * 1e3:.1f} us per repetition")
+    if args.op == "step":
+        info, _ = otm.otm_step(ctx)
+        print(f"  PCG iterations per load case {list(info.cg_iters)}, resid {max(info.resid):.2e}")
     if args.op == "conv3":
         flops = 2.0 * N * 27 * args.cin * args.cout
         print(f"conv3 {args.cin}->{args.cout}: {flops / (e0.elapsed_time(e1) / args.reps * 1e-3) / 1e12:.1f} TFLOP/s")

@@ -42,7 +42,7 @@ class otm_params(C.Structure):
         ("gov_small_rel", C.c_double),
         ("gov_vol_tol", C.c_double),
         ("symmetry", C.c_int),
-        ("reserved0", C.c_int),
+        ("coarse_smoother", C.c_int),
         ("seed", C.c_uint64),
         ("stream", C.c_void_p),
         ("device", C.c_int),

@@ -206,3 +206,49 @@ def test_homogenize_leaves_design_state_alone():
         assert kap_cur[0] < kap_other[0]
     finally:
         otm.otm_destroy(ctx)
+
+
+def test_concurrent_batch_is_bitwise_the_sequential_one(monkeypatch):
+    """The batch's designs run on their own streams from several host
+    threads; results must not depend on the interleaving."""
+    otm = _otm()
+    designs = W.batch_designs(count=10, sizes=(16, 24, 32, 48))
+    params, r0 = [], []
+    keep = []
+    for d in designs:
+        params.append(otm.otm_params_default(n=d.n, precision=1, kappa_target=d.kappa_target, volfrac=d.volfrac,
+                                             cg_tol=1e-6, cg_maxit=2000))
+        a = d.rho0(np.float32)
+        keep.append(a)
+        r0.append(a.ctypes.data)
+    results = {}
+    for workers in ("1", "6"):
+        monkeypatch.setenv("OTM_BATCH_WORKERS", workers)
+        outs = [np.empty(d.n ** 3, np.float32) for d in designs]
+        kaps, infos, st = otm.otm_design_batch(params, r0, 4, [o.ctypes.data for o in outs])
+        assert st == otm.OTM_OK
+        results[workers] = (outs, kaps, [list(infos[i].cg_iters) for i in range(len(designs) * 4)])
+    for a, b in zip(results["1"][0], results["6"][0]):
+        assert np.array_equal(a, b)
+    assert results["1"][1] == results["6"][1]
+    assert results["1"][2] == results["6"][2]
+
+
+def test_contexts_of_different_sizes_coexist(monkeypatch):
+    """A context created after a larger one must not lower a kernel setting
+    the larger one relies on (the coarse-level kernel's shared memory): step
+    the larger context after the smaller one was created.  Host-driven loop,
+    so a bad launch surfaces as a status instead of inside a graph."""
+    monkeypatch.setenv("OTM_NO_GRAPH", "1")
+    otm = _otm()
+    made = []
+    try:
+        for n in (16, 12, 8):
+            p = otm.otm_params_default(n=n, precision=1, kappa_target=W.TARGET_ORTHOTROPIC, cg_tol=1e-6)
+            made.append(otm.otm_create_ex(p))
+        for ctx in made + made[::-1]:
+            info, st = otm.otm_step(ctx)
+            assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+    finally:
+        for ctx in made:
+            otm.otm_destroy(ctx)
