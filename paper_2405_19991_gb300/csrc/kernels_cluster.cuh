@@ -15,7 +15,7 @@
 
 namespace otm {
 
-constexpr int kClusterCTAs = 8;
+constexpr int kClusterCTAs = 8;        // portable cluster size; 16 (non-portable) where the device allows
 constexpr int kClusterThreads = 512;
 constexpr int kClusterMaxN = 32;
 
@@ -150,8 +150,9 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
     }
 }
 
+// Launched as one cluster (the cluster size is the grid size, set at launch).
 template <class S, class C>
-__global__ void __cluster_dims__(kClusterCTAs, 1, 1) __launch_bounds__(kClusterThreads)
+__global__ void __launch_bounds__(kClusterThreads)
 k_coarse_cluster(ClusterArgs<S, C> a) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char cl_sm[];

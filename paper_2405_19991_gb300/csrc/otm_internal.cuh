@@ -25,6 +25,28 @@ __device__ __forceinline__ void pdl_enter() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// One thread-block cluster of `ctas` CTAs (grid = cluster), with dynamic
+// shared memory and programmatic dependent launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cluster_pdl(void (*kern)(KArgs...), int ctas, dim3 block, size_t smem, cudaStream_t st,
+                                      Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas, 1, 1);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = ctas;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // Launch with the programmatic-stream-serialisation attribute.
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
@@ -65,11 +87,13 @@ template <> struct St<double> {
     using C = double;
     static __device__ __forceinline__ double ld(const double* p, size_t i) { return p[i]; }
     static __device__ __forceinline__ void st(double* p, size_t i, double v) { p[i] = v; }
+    static __device__ __forceinline__ double round(double v) { return v; }   // the value st stores
 };
 template <> struct St<float> {
     using C = float;
     static __device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
     static __device__ __forceinline__ void st(float* p, size_t i, float v) { p[i] = v; }
+    static __device__ __forceinline__ float round(float v) { return v; }
 };
 template <> struct St<__nv_bfloat16> {
     using C = float;
@@ -79,6 +103,7 @@ template <> struct St<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16* p, size_t i, float v) {
         p[i] = __float2bfloat16_rn(v);
     }
+    static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 // Four consecutive values, loaded and stored with one vector access where

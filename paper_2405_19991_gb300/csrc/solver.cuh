@@ -239,6 +239,7 @@ class Solver : public SolverBase {
     // a single level).  OTM_NO_CLUSTER=1 disables it.
     bool use_cluster = true;
     int cluster_maxn = kClusterMaxN;   // OTM_CLUSTER_MAXN overrides
+    int cl_ctas_ = kClusterCTAs;       // CTAs of the coarse-level cluster
     int cluster_lc() const {
         const int L = nlev - 1;
         if (!use_cluster || nlev < 2) return L + 1;
@@ -408,6 +409,32 @@ class Solver : public SolverBase {
                 return OTM_ECUDA;
             }
             OTM_TRY(raise_cluster_smem(cs));
+            // cluster size: 16 CTAs (non-portable) when the device can co-schedule
+            // them with this shared memory, else the portable 8; OTM_CLUSTER_CTAS
+            // (8 or 16) overrides
+            int want = 16;
+            if (const char* e = getenv("OTM_CLUSTER_CTAS")) want = atoi(e) == 8 ? 8 : 16;
+            cl_ctas_ = kClusterCTAs;
+            if (want == 16 &&
+                cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                    cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(16, 1, 1);
+                cfg.blockDim = dim3(kClusterThreads, 1, 1);
+                cfg.dynamicSmemBytes = cs;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = 16;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                int clusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&clusters, k_coarse_cluster<S, C>, &cfg) == cudaSuccess &&
+                    clusters >= 1)
+                    cl_ctas_ = 16;
+            }
+            cudaGetLastError();
         }
         cheb_ = pin.coarse_smoother == 1 && nlev > 1;
         OTM_TRY(alloc(lam_d, kMaxLevels));
@@ -689,8 +716,8 @@ class Solver : public SolverBase {
             }
             ca.Minv = Minv;
             ++nl_;
-            const cudaError_t le =
-                launch_pdl_smem(k_coarse_cluster<S, C>, kClusterCTAs, kClusterThreads, cluster_smem_bytes(), stream, ca);
+            const cudaError_t le = launch_cluster_pdl(k_coarse_cluster<S, C>, cl_ctas_, kClusterThreads,
+                                                      cluster_smem_bytes(), stream, ca);
             if (le != cudaSuccess) {
                 err = std::string("coarse-level cluster launch: ") + cudaGetErrorString(le);
                 return OTM_ECUDA;
@@ -723,7 +750,7 @@ class Solver : public SolverBase {
         for (int gidx = 3; gidx >= 0; --gidx) {
             ++nl_;
             launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
-                           r, z);
+                       r, z);
         }
         OTM_LAUNCH();
         return OTM_OK;
