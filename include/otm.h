@@ -292,6 +292,14 @@ OTM_API otm_status otm_op_macro_load(int dtype, int n, const void* k, void* f, v
 OTM_API otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u,
                                   void* Ku, void* stream);
 
+/* Same as otm_op_apply_K, but only enqueues the work on `stream` and returns
+ * without waiting for it (the stream-ordered form, for timing a kernel with
+ * events and for use inside a caller's pipeline).  Argument errors and launch
+ * errors are reported; errors during execution surface at the caller's next
+ * synchronisation of the stream. */
+OTM_API otm_status otm_op_apply_K_async(int dtype, int n, const void* k, const void* u,
+                                        void* Ku, void* stream);
+
 /* One colour pass of the Gauss-Seidel relaxation of Sec. 2.4,
  * S_v T_v = f_v - M_v, on the finest grid for the nodes of colour
  * c = (x%2) + 2(y%2) + 4(z%2) in [0, 8) (n even); colour 8 + g, g in [0, 4),

@@ -76,6 +76,12 @@ otm_status finish(cudaStream_t st, const char* what) {
     return OTM_OK;
 }
 
+otm_status launched(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return op_fail(OTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return OTM_OK;
+}
+
 bool bad_dtype(int dtype) { return dtype != OTM_FP32 && dtype != OTM_FP64; }
 
 otm::FilterW filter_w(double rmin) {
@@ -139,20 +145,26 @@ otm_status macro_load_t(int n, const void* k, void* f, void* stream) {
 }
 
 template <class R>
-otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream) {
+otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream, bool sync = true) {
     OpCtx oc(stream);
     const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{nullptr, nullptr, 0};
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int x2tz = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::x2_tz(n, sms, oc.max_blocks) : 0;
-    if (x2tz > 0) {   // the kernel and launch shape the solver uses at this size
+    const int zrtz = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::zr_tz(n, sms, oc.max_blocks) : 0;
+    if (zrtz > 0) {   // the kernel and launch shape the solver uses at this size
+        otm::k_stencil_zr<false, otm::FinNone><<<otm::zr_grid(n, zrtz), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
+            n, zrtz, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
+        return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
+    }
+    const int x2tz = sizeof(R) == 4 && otm::stencil_choice() == 3 ? otm::x2_tz(n, sms, oc.max_blocks) : 0;
+    if (x2tz > 0) {
         otm::k_stencil_x2<false, otm::FinNone><<<otm::x2_grid(n, x2tz), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
             n, x2tz, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
-        return finish(oc.st, "otm_op_apply_K");
+        return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
     }
-    const int tz = sizeof(R) == 4 && otm::stencil_choice() <= 1 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
+    const int tz = sizeof(R) == 4 && otm::stencil_choice() != 2 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
     if (tz > 0)
         otm::k_stencil_tiled<0, false, R, R, R, R, otm::FinNone>
             <<<(n / otm::kTX) * (n / otm::kTY) * (n / tz), dim3(otm::kTX, otm::kTY), 0, oc.st>>>(
@@ -160,7 +172,7 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     else
         otm::k_stencil_apply<0, false, R, R, R, R, otm::FinNone><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(
             n, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
-    return finish(oc.st, "otm_op_apply_K");
+    return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
 }
 
 template <class R>
@@ -268,6 +280,12 @@ otm_status otm_op_apply_K(int dtype, int n, const void* k, const void* u, void* 
     OP_CHECK(bad_dtype(dtype) || bad_n(n) || !k || !u || !Ku, "otm_op_apply_K: bad argument");
     if (dtype == OTM_FP64) return apply_K_t<double>(n, k, u, Ku, stream);
     return apply_K_t<float>(n, k, u, Ku, stream);
+}
+
+otm_status otm_op_apply_K_async(int dtype, int n, const void* k, const void* u, void* Ku, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !k || !u || !Ku, "otm_op_apply_K_async: bad argument");
+    if (dtype == OTM_FP64) return apply_K_t<double>(n, k, u, Ku, stream, false);
+    return apply_K_t<float>(n, k, u, Ku, stream, false);
 }
 
 otm_status otm_op_gs_colour(int dtype, int n, const void* k, const void* f, void* T, int colour, void* stream) {

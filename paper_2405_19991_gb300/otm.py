@@ -116,6 +116,7 @@ def _load():
         "otm_op_filter_transpose": [i, i, d, vp, vp, vp],
         "otm_op_macro_load": [i, i, vp, vp, vp],
         "otm_op_apply_K": [i, i, vp, vp, vp, vp],
+        "otm_op_apply_K_async": [i, i, vp, vp, vp, vp],
         "otm_op_gs_colour": [i, i, vp, vp, vp, i, vp],
         "otm_op_kappa_sens": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_op_oc_update": [i, i, d, d, d, d, vp, vp, vp, P(C.c_double), vp],
@@ -150,7 +151,7 @@ EXPORTED = [
     "otm_set_density", "otm_get_density", "otm_get_field", "otm_homogenize", "otm_step",
     "otm_run", "otm_design_batch", "otm_get_state", "otm_set_state", "otm_last_error",
     "otm_governor_init", "otm_governor_update", "otm_op_filter_simp", "otm_op_filter_transpose",
-    "otm_op_macro_load", "otm_op_apply_K", "otm_op_gs_colour", "otm_op_kappa_sens",
+    "otm_op_macro_load", "otm_op_apply_K", "otm_op_apply_K_async", "otm_op_gs_colour", "otm_op_kappa_sens",
     "otm_op_oc_update", "otm_op_kappa_sens_noalloc", "otm_unet_create", "otm_unet_destroy",
     "otm_unet_param_count", "otm_unet_get_params", "otm_unet_set_params", "otm_unet_forward",
     "otm_unet_backward", "otm_unet_train_step", "otm_unet_eval", "otm_set_predictor", "otm_op_conv3",
@@ -294,6 +295,10 @@ def otm_op_macro_load(dtype, n, k, f, stream=None):
 
 def otm_op_apply_K(dtype, n, k, u, Ku, stream=None):
     return check(lib.otm_op_apply_K(dtype, n, _p(k), _p(u), _p(Ku), stream))
+
+
+def otm_op_apply_K_async(dtype, n, k, u, Ku, stream=None):
+    return check(lib.otm_op_apply_K_async(dtype, n, _p(k), _p(u), _p(Ku), stream))
 
 
 def otm_op_gs_colour(dtype, n, k, f, T, colour, stream=None):

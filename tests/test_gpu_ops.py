@@ -216,3 +216,18 @@ def test_gs_group_pass_full_size_sampled(n):
     # nodes of the other groups are untouched
     other = np.setdiff1d(rng.choice(n ** 3, 2000, replace=False), nodes)
     assert np.array_equal(got[:, other], Th[:, other])
+
+
+@pytest.mark.parametrize("n", [16, 64, 128])
+def test_apply_K_async_is_the_same_operator(n):
+    otm = _otm()
+    import torch
+    k = _k(n, 8)
+    u = W.random_field(n, 9)
+    k_d, u_d = dev(k, torch.float32), dev(u.ravel(), torch.float32)
+    a, b = empty(3 * n ** 3, torch.float32), empty(3 * n ** 3, torch.float32)
+    otm.otm_op_apply_K(1, n, k_d, u_d, a)
+    st = torch.cuda.current_stream()
+    otm.otm_op_apply_K_async(1, n, k_d, u_d, b, st.cuda_stream)
+    st.synchronize()
+    assert torch.equal(a, b)
