@@ -75,12 +75,12 @@ inline TailLayout tail_layout(int lb, int L, const int* n, int minv_smem) {
         return o;
     };
     for (int l = lb; l <= L; ++l) {
-        const size_t m = 3 * (size_t)n[l] * n[l] * n[l] * sizeof(S);
-        t.T[l] = take(m);
-        t.F[l] = take(m);
-        t.A[l] = take(9 * m);
+        const size_t nodes = (size_t)n[l] * n[l] * n[l];
+        t.T[l] = take(4 * nodes * sizeof(S));
+        t.F[l] = take(4 * nodes * sizeof(S));
+        t.A[l] = take((size_t)cl_aw<S>() * nodes * sizeof(S));
     }
-    t.R = take(3 * (size_t)n[lb] * n[lb] * n[lb] * sizeof(S));
+    t.R = take(4 * (size_t)n[lb] * n[lb] * n[lb] * sizeof(S));
     const size_t q = (size_t)n[L] * n[L] * n[L] - 1;
     t.minv = off;
     if (minv_smem) take(q * q * sizeof(C));
@@ -102,10 +102,10 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
     S* Rs = reinterpret_cast<S*>(sm + a.tR);
     {
         const int nb = a.n[a.lb];
-        const int m = 3 * nb * nb * nb;
+        const int m = 4 * nb * nb * nb;
         for (int i = t0; i < m; i += ts) Fs(a.lb)[i] = a.F[a.lb][i];
         for (int l = a.lb; l <= a.L; ++l) {
-            const int ma = 27 * a.n[l] * a.n[l] * a.n[l];
+            const int ma = cl_aw<S>() * a.n[l] * a.n[l] * a.n[l];
             S* dst = reinterpret_cast<S*>(sm + a.tA[l]);
             for (int i = t0; i < ma; i += ts) dst[i] = a.A[l][i];
         }
@@ -125,7 +125,7 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
         __syncthreads();
         const int nc = n / 2;
         for (int t = t0; t < nc * nc * nc; t += ts)
-            restrict_node<S, S>(nc, t % nc, (t / nc) % nc, t / (nc * nc), Rs, Fs(l + 1));
+            restrict_node<S, S, true>(nc, t % nc, (t / nc) % nc, t / (nc * nc), Rs, Fs(l + 1));
         __syncthreads();
     }
     {
@@ -136,7 +136,7 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
     __syncthreads();
     for (int l = a.L - 1; l >= a.lb; --l) {
         const int n = a.n[l];
-        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), Ts(l + 1), Ts(l));
+        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S, true>(n, t % n, (t / n) % n, t / (n * n), Ts(l + 1), Ts(l));
         __syncthreads();
         for (int c = 7; c >= 0; --c) {
             cl_gs_pass<false, S>(n, c, As(l), Fs(l), Ts(l), t0, ts);
@@ -145,7 +145,7 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
     }
     {
         const int nb = a.n[a.lb];
-        const int m = 3 * nb * nb * nb;
+        const int m = 4 * nb * nb * nb;
         for (int i = t0; i < m; i += ts) a.T[a.lb][i] = Ts(a.lb)[i];
     }
 }
@@ -204,7 +204,7 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
         cluster_barrier();
         const int nc = n / 2;
         for (int t = t0; t < nc * nc * nc; t += ts)
-            restrict_node<S, S>(nc, t % nc, (t / nc) % nc, t / (nc * nc), a.Rr[l], a.F[l + 1]);
+            restrict_node<S, S, true>(nc, t % nc, (t / nc) % nc, t / (nc * nc), a.Rr[l], a.F[l + 1]);
         cluster_barrier();
     }
     // coarsest: dense solve in CTA 0, or the shared-memory tail lb..L
@@ -222,7 +222,7 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
     for (int l = lend - 1; l >= a.lc; --l) {
         const int n = a.n[l];
         S* Tcur = a.cheb ? a.T2[l] : a.T[l];
-        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S>(n, t % n, (t / n) % n, t / (n * n), a.T[l + 1], Tcur);
+        for (int t = t0; t < n * n * n; t += ts) prolong_node<S, S, true>(n, t % n, (t / n) % n, t / (n * n), a.T[l + 1], Tcur);
         cluster_barrier();
         if (a.cheb) {
             cheb_smooth(l, false);

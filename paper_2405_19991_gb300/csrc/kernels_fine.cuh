@@ -574,12 +574,17 @@ k_sub_mean(size_t N, R* __restrict__ f, const PcgScalars* __restrict__ ps) {
 
 // Restriction R = P^T of the trilinear prolongation: coarse node I gathers
 // the fine nodes 2I + d, d in {-1,0,1}^3, with weight prod (1 - |d|/2).
-template <class IT, class OT>
+// Restriction R = P^T: coarse node I gathers the 27 fine nodes around 2I with
+// weights w(dx) w(dy) w(dz), w = (1/2, 1, 1/2).  The fine residual is read
+// load-case-major ([3][Nf], the finest level) or node-major ([Nf][4], IN_AOS);
+// the coarse right-hand side is written node-major.
+template <class IT, class OT, bool IN_AOS>
 __device__ __forceinline__ void restrict_node(int nc, int X, int Y, int Z, const IT* __restrict__ rf,
                                               OT* __restrict__ fc) {
     using C = typename St<OT>::C;
+    using CI = typename St<IT>::C;
     const int nf = 2 * nc;
-    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    const size_t Nf = (size_t)nf * nf * nf;
     const size_t I = (size_t)X + (size_t)nc * (Y + (size_t)nc * Z);
     int xs[3], ys[3], zs[3];
 #pragma unroll
@@ -589,43 +594,49 @@ __device__ __forceinline__ void restrict_node(int nc, int X, int Y, int Z, const
         zs[d] = wrapd(2 * Z, d - 1, nf) * nf * nf;
     }
     const C w1[3] = {C(0.5), C(1), C(0.5)};
+    C acc[3] = {C(0), C(0), C(0)};
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const IT* r = rf + (size_t)i * Nf;
-        C acc = 0;
+    for (int dz = 0; dz < 3; ++dz) {
+        C az[3] = {C(0), C(0), C(0)};
 #pragma unroll
-        for (int dz = 0; dz < 3; ++dz) {
-            C az = 0;
+        for (int dy = 0; dy < 3; ++dy) {
+            C ay[3] = {C(0), C(0), C(0)};
 #pragma unroll
-            for (int dy = 0; dy < 3; ++dy) {
-                C ay = 0;
+            for (int dx = 0; dx < 3; ++dx) {
+                CI t[3];
+                ld_f3_any<IN_AOS, IT>(rf, Nf, (size_t)(xs[dx] + ys[dy] + zs[dz]), t);
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) ay += w1[dx] * St<IT>::ld(r, (size_t)(xs[dx] + ys[dy] + zs[dz]));
-                az += w1[dy] * ay;
+                for (int i = 0; i < 3; ++i) ay[i] += w1[dx] * (C)t[i];
             }
-            acc += w1[dz] * az;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) az[i] += w1[dy] * ay[i];
         }
-        St<OT>::st(fc + (size_t)i * Nc, I, acc);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) acc[i] += w1[dz] * az[i];
     }
+    st_f3<OT>(fc, I, acc[0], acc[1], acc[2]);
 }
 
-template <class IT, class OT>
+template <class IT, class OT, bool IN_AOS>
 __global__ void __launch_bounds__(256)
 k_restrict(int nc, const IT* __restrict__ rf, OT* __restrict__ fc) {
     pdl_enter();
     OTM_FOR_ROWS(row, nc * nc) {
         const int Y = row % nc, Z = row / nc;
-        OTM_FOR_X(X, nc) restrict_node<IT, OT>(nc, X, Y, Z, rf, fc);
+        OTM_FOR_X(X, nc) restrict_node<IT, OT, IN_AOS>(nc, X, Y, Z, rf, fc);
     }
 }
 
-// Prolongation and correction: T_v += sum_I P[v, I] Tc_I (trilinear).
-template <class CT, class TT>
+// Prolongation and correction: T_v += sum_I P[v, I] Tc_I (trilinear).  The
+// coarse field is node-major; the fine one is node-major (OUT_AOS, a coarse
+// level) or load-case-major (the finest level).
+template <class CT, class TT, bool OUT_AOS>
 __device__ __forceinline__ void prolong_node(int nf, int x, int y, int z, const CT* __restrict__ Tc,
                                              TT* __restrict__ T) {
     using C = typename St<TT>::C;
+    using CC = typename St<CT>::C;
     const int nc = nf / 2;
-    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    const size_t Nf = (size_t)nf * nf * nf;
     const size_t v = (size_t)x + (size_t)nf * (y + (size_t)nf * z);
     int xi[2], yi[2], zi[2];
     C wx[2], wy[2], wz[2];
@@ -636,27 +647,36 @@ __device__ __forceinline__ void prolong_node(int nf, int x, int y, int z, const 
     else { yi[0] = yi[1] = y >> 1; wy[0] = C(1); wy[1] = 0; cy = 1; }
     if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = C(0.5); cz = 2; }
     else { zi[0] = zi[1] = z >> 1; wz[0] = C(1); wz[1] = 0; cz = 1; }
+    C acc[3] = {C(0), C(0), C(0)};
+    for (int c = 0; c < cz; ++c)
+        for (int b = 0; b < cy; ++b)
+            for (int a = 0; a < cx; ++a) {
+                CC t[3];
+                ld_f3<CT>(Tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]), t);
+                const C w = wz[c] * wy[b] * wx[a];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const CT* tc = Tc + (size_t)i * Nc;
-        C acc = 0;
-        for (int c = 0; c < cz; ++c)
-            for (int b = 0; b < cy; ++b)
-                for (int a = 0; a < cx; ++a)
-                    acc += wz[c] * wy[b] * wx[a] *
-                           St<CT>::ld(tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]));
-        TT* t = T + (size_t)i * Nf;
-        St<TT>::st(t, v, St<TT>::ld(t, v) + acc);
+                for (int i = 0; i < 3; ++i) acc[i] += w * (C)t[i];
+            }
+    if (OUT_AOS) {
+        C t0[3];
+        ld_f3<TT>(T, v, t0);
+        st_f3<TT>(T, v, t0[0] + acc[0], t0[1] + acc[1], t0[2] + acc[2]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            TT* t = T + (size_t)i * Nf;
+            St<TT>::st(t, v, St<TT>::ld(t, v) + acc[i]);
+        }
     }
 }
 
-template <class CT, class TT>
+template <class CT, class TT, bool OUT_AOS>
 __global__ void __launch_bounds__(256)
 k_prolong_add(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
     pdl_enter();
     OTM_FOR_ROWS(row, nf * nf) {
         const int y = row % nf, z = row / nf;
-        OTM_FOR_X(x, nf) prolong_node<CT, TT>(nf, x, y, z, Tc, T);
+        OTM_FOR_X(x, nf) prolong_node<CT, TT, OUT_AOS>(nf, x, y, z, Tc, T);
     }
 }
 

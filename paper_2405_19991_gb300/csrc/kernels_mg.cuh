@@ -114,7 +114,7 @@ k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
             }
         }
 #pragma unroll
-        for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
+        for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
     }
     }
 }
@@ -147,7 +147,7 @@ k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
             }
         }
 #pragma unroll
-        for (int o = 0; o < 27; ++o) St<AT>::st(A, (size_t)o * N + v, acc[o]);
+        for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
     }
     }
 }
@@ -199,25 +199,30 @@ __device__ __forceinline__ void cheb_node(int n, size_t N, int x, int y, int z, 
         zs[d] = wrapd(z, d - 1, n) * n * n;
     }
     C a[27];
-#pragma unroll
-    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+    ld_arow<AT>(A, v, a);
     const C inv = C(1) / a[13];
+    C r[3];
+    ld_f3<FT>(f, v, r);
+    C t0[3] = {C(0), C(0), C(0)}, dv[3];
+    if (!ZERO) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        C r = St<FT>::ld(f + (size_t)i * N, v);
-        C t0 = C(0), dv;
-        if (!ZERO) {
-            const TT* Ti = Tin + (size_t)i * N;
+        for (int o = 0; o < 27; ++o) {
+            C t[3];
+            ld_f3<TT>(Tin, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t);
 #pragma unroll
-            for (int o = 0; o < 27; ++o) r -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
-            t0 = St<TT>::ld(Ti, v);
-            dv = C(c_d) * St<TT>::ld(D + (size_t)i * N, v) + C(c_r) * r * inv;
-        } else {
-            dv = C(c_r) * r * inv;
+            for (int i = 0; i < 3; ++i) r[i] -= a[o] * t[i];
         }
-        St<TT>::st(D + (size_t)i * N, v, dv);
-        St<TT>::st(Tout + (size_t)i * N, v, t0 + dv);
+        ld_f3<TT>(Tin, v, t0);
+        C d0[3];
+        ld_f3<TT>(D, v, d0);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv[i] = C(c_d) * d0[i] + C(c_r) * r[i] * inv;
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv[i] = C(c_r) * r[i] * inv;
     }
+    st_f3<TT>(D, v, dv[0], dv[1], dv[2]);
+    st_f3<TT>(Tout, v, t0[0] + dv[0], t0[1] + dv[1], t0[2] + dv[2]);
 }
 
 template <bool ZERO, class AT, class FT, class TT>
@@ -246,11 +251,11 @@ k_gershgorin(int n, const AT* __restrict__ A, float* __restrict__ lam) {
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
         C s = 0;
 #pragma unroll
-        for (int o = 0; o < 27; ++o) {
-            const C a = St<AT>::ld(A, (size_t)o * N + v);
-            s += a < C(0) ? -a : a;
-        }
-        g = fmaxf(g, (float)(s / St<AT>::ld(A, (size_t)13 * N + v)));
+        C a[27];
+        ld_arow<AT>(A, v, a);
+#pragma unroll
+        for (int o = 0; o < 27; ++o) s += a[o] < C(0) ? -a[o] : a[o];
+        g = fmaxf(g, (float)(s / a[13]));
     }
     for (int o = 16; o > 0; o >>= 1) g = fmaxf(g, __shfl_xor_sync(0xffffffffu, g, o));
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(lam), __float_as_int(g));
@@ -273,27 +278,27 @@ __device__ __forceinline__ void gs_stencil_node(int n, size_t N, int x, int y, i
         zs[d] = wrapd(z, d - 1, n) * n * n;
     }
     C a[27];
-#pragma unroll
-    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+    ld_arow<AT>(A, v, a);
     const C inv = C(1) / a[13];
+    C s[3];
+    ld_f3<FT>(f, v, s);
+    if (!ZERO) {
+        // per load case the same accumulation order as a scalar sweep over o
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        TT* Ti = T + (size_t)i * N;
-        C s = St<FT>::ld(f + (size_t)i * N, v);
-        if (!ZERO) {
+        for (int o = 0; o < 27; ++o) {
+            if (o == 13) continue;
+            C t[3];
+            ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t);
 #pragma unroll
-            for (int o = 0; o < 27; ++o) {
-                if (o == 13) continue;
-                s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
-            }
+            for (int i = 0; i < 3; ++i) s[i] -= a[o] * t[i];
         }
-        St<TT>::st(Ti, v, s * inv);
-        if (ZERO) {
+    }
+    st_f3<TT>(T, v, s[0] * inv, s[1] * inv, s[2] * inv);
+    if (ZERO) {
 #pragma unroll
-            for (int q = 1; q < 8; ++q) {
-                const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
-                St<TT>::st(Ti, w, C(0));
-            }
+        for (int q = 1; q < 8; ++q) {
+            const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
+            st_f3<TT>(T, w, C(0), C(0), C(0));
         }
     }
 }
@@ -326,19 +331,18 @@ __device__ __forceinline__ void residual_stencil_node(int n, size_t N, int x, in
         zs[d] = wrapd(z, d - 1, n) * n * n;
     }
     C a[27];
+    ld_arow<AT>(A, v, a);
+    C s[3];
+    ld_f3<FT>(f, v, s);
 #pragma unroll
-    for (int o = 0; o < 27; ++o) a[o] = St<AT>::ld(A, (size_t)o * N + v);
+    for (int o = 0; o < 27; ++o) {
+        C t[3];
+        ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        const TT* Ti = T + (size_t)i * N;
-        C s = St<FT>::ld(f + (size_t)i * N, v);
-#pragma unroll
-        for (int o = 0; o < 27; ++o)
-            s -= a[o] * St<TT>::ld(Ti, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]));
-        St<OT>::st(res + (size_t)i * N, v, s);
+        for (int i = 0; i < 3; ++i) s[i] -= a[o] * t[i];
     }
+    st_f3<OT>(res, v, s[0], s[1], s[2]);
 }
-
 template <class AT, class FT, class TT, class OT>
 __global__ void __launch_bounds__(256)
 k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, const TT* __restrict__ T,
@@ -374,7 +378,7 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
         for (int o = 0; o < 27; ++o) {
             const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
             if (c == 0) continue;
-            W[(size_t)(v - 1) * q + (c - 1)] += (C)St<AT>::ld(A, (size_t)o * m + v);
+            W[(size_t)(v - 1) * q + (c - 1)] += (C)St<AT>::ld(A, (size_t)v * cl_aw<AT>() + o);
         }
     }
     __syncthreads();
@@ -410,14 +414,17 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
 
 // T = Minv f with T_0 = 0, then shifted to zero mean.  Executed by every
 // thread of one CTA (block-level synchronisation only).
-template <class C, class FT, class TT>
+// AOS: f and T node-major [m][4] (a coarse level); else load-case-major [3][m]
+// (the fine grid of a single-level hierarchy).
+template <class C, class FT, class TT, bool AOS = true>
 __device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* __restrict__ f, TT* __restrict__ T) {
     const int m = n * n * n;
     const int q = m - 1;
     __shared__ C fs[3][343];
     __shared__ C ts[3][343];
     __shared__ double red[3][32];
-    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x) fs[i / m][i % m] = St<FT>::ld(f, i);
+    for (int i = threadIdx.x; i < 3 * m; i += blockDim.x)
+        fs[i / m][i % m] = St<FT>::ld(f, AOS ? (size_t)(i % m) * 4 + i / m : (size_t)i);
     __syncthreads();
     // Minv is symmetric, so row v-1 is read as column v-1: consecutive
     // threads read consecutive words.
@@ -446,7 +453,7 @@ __device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* 
     __syncthreads();
     for (int t = threadIdx.x; t < 3 * m; t += blockDim.x) {
         const int r = t / m, v = t % m;
-        St<TT>::st(T, (size_t)t, ts[r][v] - (C)red[r][0]);
+        St<TT>::st(T, AOS ? (size_t)v * 4 + r : (size_t)t, ts[r][v] - (C)red[r][0]);
     }
 }
 
@@ -460,13 +467,13 @@ __device__ __forceinline__ const C* stage_minv(const C* __restrict__ Minv_g, int
     return ms;
 }
 
-template <class C, class FT, class TT>
+template <class C, class FT, class TT, bool AOS = true>
 __global__ void __launch_bounds__(1024)
 k_coarse_solve(int n, const C* __restrict__ Minv_g, const FT* __restrict__ f, TT* __restrict__ T, int use_smem) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char cs_sm[];
     const C* Minv = stage_minv<C>(Minv_g, n * n * n - 1, use_smem, cs_sm);
-    coarse_solve_block<C, FT, TT>(n, Minv, f, T);
+    coarse_solve_block<C, FT, TT, AOS>(n, Minv, f, T);
 }
 
 }  // namespace otm

@@ -111,15 +111,16 @@ k_prolong_wr(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
         const size_t vb = (size_t)row * nf + (size_t)xb;
 #pragma unroll 1
         for (int i = 0; i < 3; ++i) {
-            const CT* tc = Tc + (size_t)i * Nc;
+            // the coarse field is node-major ([Nc][4])
+            auto tc = [&](size_t node) -> float { return (float)St<CT>::ld(Tc, node * 4 + i); };
             float s[3] = {0.f, 0.f, 0.f};
             for (int c = 0; c < cz; ++c)
                 for (int b = 0; b < cy; ++b) {
                     const size_t ro = (size_t)yi[b] * nc + (size_t)zi[c] * nc * nc;
-                    const float a0 = (float)St<CT>::ld(tc, ro + cxb);
-                    const float a1 = (float)St<CT>::ld(tc, ro + cxb + 1);
+                    const float a0 = tc(ro + cxb);
+                    const float a1 = tc(ro + cxb + 1);
                     float a2 = __shfl_sync(0xffffffffu, a0, (lane + 1) & 31);
-                    if (lane == 31 && wpr > 1) a2 = (float)St<CT>::ld(tc, ro + (size_t)(cxb + 2 == nc ? 0 : cxb + 2));
+                    if (lane == 31 && wpr > 1) a2 = tc(ro + (size_t)(cxb + 2 == nc ? 0 : cxb + 2));
                     const float wgt = wz[c] * wy[b];
                     s[0] += wgt * a0;
                     s[1] += wgt * a1;

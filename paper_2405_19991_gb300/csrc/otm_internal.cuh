@@ -106,6 +106,123 @@ template <> struct St<__nv_bfloat16> {
     static __device__ __forceinline__ float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
+// ---- coarse-level layouts (levels >= 1, and the stencil of a single-level
+// hierarchy): node-major, so one node's data is a few 16-byte vector loads.
+//   stencil A: [N][kAW<S>] (the 27 couplings o = (dx+1) + 3(dy+1) + 9(dz+1),
+//              padded to a 16-byte multiple),
+//   fields T, F, residual, and the smoother's buffers: [N][4] (load cases
+//              0..2, slot 3 zero).
+template <class S>
+struct CL {
+    static constexpr int AW = sizeof(S) == 2 ? 32 : 28;
+};
+template <class S>
+__host__ __device__ constexpr int cl_aw() { return CL<S>::AW; }
+
+// the 27 couplings of node v
+template <class S>
+__device__ __forceinline__ void ld_arow(const S* __restrict__ A, size_t v, typename St<S>::C (&a)[27]);
+template <>
+__device__ __forceinline__ void ld_arow<float>(const float* __restrict__ A, size_t v, float (&a)[27]) {
+    const float4* p = reinterpret_cast<const float4*>(A + v * 28);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const float4 w = p[q];
+        if (4 * q + 0 < 27) a[4 * q + 0] = w.x;
+        if (4 * q + 1 < 27) a[4 * q + 1] = w.y;
+        if (4 * q + 2 < 27) a[4 * q + 2] = w.z;
+        if (4 * q + 3 < 27) a[4 * q + 3] = w.w;
+    }
+}
+template <>
+__device__ __forceinline__ void ld_arow<double>(const double* __restrict__ A, size_t v, double (&a)[27]) {
+    const double2* p = reinterpret_cast<const double2*>(A + v * 28);
+#pragma unroll
+    for (int q = 0; q < 14; ++q) {
+        const double2 w = p[q];
+        if (2 * q + 0 < 27) a[2 * q + 0] = w.x;
+        if (2 * q + 1 < 27) a[2 * q + 1] = w.y;
+    }
+}
+template <>
+__device__ __forceinline__ void ld_arow<__nv_bfloat16>(const __nv_bfloat16* __restrict__ A, size_t v,
+                                                       float (&a)[27]) {
+    const uint4* p = reinterpret_cast<const uint4*>(A + v * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint4 w = p[q];
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const __nv_bfloat162 b2 = *reinterpret_cast<const __nv_bfloat162*>(&u[h]);
+            const int e = 8 * q + 2 * h;
+            if (e < 27) a[e] = __low2float(b2);
+            if (e + 1 < 27) a[e + 1] = __high2float(b2);
+        }
+    }
+}
+
+// the three load cases at node v of a [N][4] field
+template <class S>
+__device__ __forceinline__ void ld_f3(const S* __restrict__ T, size_t v, typename St<S>::C (&t)[3]);
+template <>
+__device__ __forceinline__ void ld_f3<float>(const float* __restrict__ T, size_t v, float (&t)[3]) {
+    const float4 w = *reinterpret_cast<const float4*>(T + 4 * v);
+    t[0] = w.x;
+    t[1] = w.y;
+    t[2] = w.z;
+}
+template <>
+__device__ __forceinline__ void ld_f3<double>(const double* __restrict__ T, size_t v, double (&t)[3]) {
+    const double2* p = reinterpret_cast<const double2*>(T + 4 * v);
+    const double2 a = p[0], b = p[1];
+    t[0] = a.x;
+    t[1] = a.y;
+    t[2] = b.x;
+}
+template <>
+__device__ __forceinline__ void ld_f3<__nv_bfloat16>(const __nv_bfloat16* __restrict__ T, size_t v, float (&t)[3]) {
+    const uint2 w = *reinterpret_cast<const uint2*>(T + 4 * v);
+    const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162*>(&w.x);
+    const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162*>(&w.y);
+    t[0] = __low2float(lo);
+    t[1] = __high2float(lo);
+    t[2] = __low2float(hi);
+}
+template <class S>
+__device__ __forceinline__ void st_f3(S* __restrict__ T, size_t v, typename St<S>::C t0, typename St<S>::C t1,
+                                      typename St<S>::C t2);
+template <>
+__device__ __forceinline__ void st_f3<float>(float* __restrict__ T, size_t v, float t0, float t1, float t2) {
+    *reinterpret_cast<float4*>(T + 4 * v) = make_float4(t0, t1, t2, 0.0f);
+}
+template <>
+__device__ __forceinline__ void st_f3<double>(double* __restrict__ T, size_t v, double t0, double t1, double t2) {
+    double2* p = reinterpret_cast<double2*>(T + 4 * v);
+    p[0] = make_double2(t0, t1);
+    p[1] = make_double2(t2, 0.0);
+}
+template <>
+__device__ __forceinline__ void st_f3<__nv_bfloat16>(__nv_bfloat16* __restrict__ T, size_t v, float t0, float t1,
+                                                     float t2) {
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(t0, t1), hi = __floats2bfloat162_rn(t2, 0.0f);
+    uint2 w;
+    w.x = *reinterpret_cast<const unsigned*>(&lo);
+    w.y = *reinterpret_cast<const unsigned*>(&hi);
+    *reinterpret_cast<uint2*>(T + 4 * v) = w;
+}
+// A field read either node-major ([N][4], AOS) or load-case-major ([3][N]).
+template <bool AOS, class S>
+__device__ __forceinline__ void ld_f3_any(const S* __restrict__ T, size_t N, size_t v, typename St<S>::C (&t)[3]) {
+    if (AOS) {
+        ld_f3<S>(T, v, t);
+    } else {
+        t[0] = St<S>::ld(T, v);
+        t[1] = St<S>::ld(T, N + v);
+        t[2] = St<S>::ld(T, 2 * N + v);
+    }
+}
+
 // Four consecutive values, loaded and stored with one vector access where
 // the storage type allows it (16 B for FP32, 8 B for BF16, two 16 B for FP64).
 template <class C>

@@ -375,17 +375,18 @@ class Solver : public SolverBase {
         if (std::is_same<R, S>::value) k_vc = (S*)kf;
         else OTM_TRY(alloc(k_vc, N));
         for (int l = 1; l < nlev; ++l) {
-            OTM_TRY(alloc(Tl[l], 3 * Nl[l]));
-            OTM_TRY(alloc(Fl[l], 3 * Nl[l]));
-            OTM_TRY(alloc(Rl[l], 3 * Nl[l]));
+            // coarse levels are node-major: fields [N][4], stencil [N][CL<S>::AW]
+            OTM_TRY(alloc(Tl[l], 4 * Nl[l]));
+            OTM_TRY(alloc(Fl[l], 4 * Nl[l]));
+            OTM_TRY(alloc(Rl[l], 4 * Nl[l]));
             if (pin.coarse_smoother == 1) {
-                OTM_TRY(alloc(T2l[l], 3 * Nl[l]));
-                OTM_TRY(alloc(Dl[l], 3 * Nl[l]));
+                OTM_TRY(alloc(T2l[l], 4 * Nl[l]));
+                OTM_TRY(alloc(Dl[l], 4 * Nl[l]));
             }
-            OTM_TRY(alloc(Al[l], 27 * Nl[l]));
+            OTM_TRY(alloc(Al[l], (size_t)CL<S>::AW * Nl[l]));
             OTM_TRY(alloc(Kel[l], 64 * Nl[l]));
         }
-        if (nlev == 1) OTM_TRY(alloc(Al[0], 27 * Nl[0]));
+        if (nlev == 1) OTM_TRY(alloc(Al[0], (size_t)CL<S>::AW * Nl[0]));
         const size_t m = Nl[nlev - 1];
         OTM_TRY(alloc(Wd, (m - 1) * (m - 1)));
         OTM_TRY(alloc(Minv, (m - 1) * (m - 1)));
@@ -643,7 +644,7 @@ class Solver : public SolverBase {
         const int L = nlev - 1;
         if (nlev == 1) {
             ++nl_;
-            launch_pdl_smem(k_coarse_solve<C, R, S>, 1, 1024, minv_smem_bytes(0), stream, sz[0], Minv, r, z, minv_smem_bytes(0) > 0 ? 1 : 0);
+            launch_pdl_smem(k_coarse_solve<C, R, S, false>, 1, 1024, minv_smem_bytes(0), stream, sz[0], Minv, r, z, minv_smem_bytes(0) > 0 ? 1 : 0);
             OTM_LAUNCH();
             return OTM_OK;
         }
@@ -663,7 +664,7 @@ class Solver : public SolverBase {
             launch_pdl(k_stencil_apply<1, false, S, S, R, S, FinNone>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, k_vc, z,
                        r, res0, rbuf(), FinNone{});
         ++nl_;
-        launch_pdl(k_restrict<S, S>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1])), stream, sz[1], res0, Fl[1]);
+        launch_pdl(k_restrict<S, S, false>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1])), stream, sz[1], res0, Fl[1]);
         OTM_LAUNCH();
         const int lc = cluster_lc();   // levels lc..L run in one cluster launch (lc > L: none)
         const int Lsep = lc <= L ? lc : L;
@@ -683,7 +684,7 @@ class Solver : public SolverBase {
             ++nl_;
             launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Al[l], Fl[l], (const S*)Tcur, Rl[l]);
             ++nl_;
-            launch_pdl(k_restrict<S, S>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1])), stream, sz[l + 1], Rl[l], Fl[l + 1]);
+            launch_pdl(k_restrict<S, S, true>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1])), stream, sz[l + 1], Rl[l], Fl[l + 1]);
             OTM_LAUNCH();
         }
         if (lc <= L) {
@@ -732,7 +733,7 @@ class Solver : public SolverBase {
         OTM_LAUNCH();
         for (int l = Lsep - 1; l >= 1; --l) {
             ++nl_;
-            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
+            launch_pdl(k_prolong_add<S, S, true>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
                        cheb_ ? T2l[l] : Tl[l]);
             if (cheb_) {
                 cheb_smooth(l, false);
@@ -748,7 +749,7 @@ class Solver : public SolverBase {
         if (wr_)
             launch_pdl(k_prolong_wr<S, S>, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const S*)Tl[1], z);
         else
-            launch_pdl(k_prolong_add<S, S>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
+            launch_pdl(k_prolong_add<S, S, false>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
         for (int gidx = 3; gidx >= 0; --gidx) {
             ++nl_;
             launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
