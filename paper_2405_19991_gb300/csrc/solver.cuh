@@ -640,6 +640,12 @@ class Solver : public SolverBase {
         }
     }
 
+    // One fine-grid Gauss-Seidel group pass.
+    void fine_gs_pass(int gidx) {
+        launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc, r,
+                   z);
+    }
+
     otm_status vcycle() {
         const int L = nlev - 1;
         if (nlev == 1) {
@@ -653,8 +659,7 @@ class Solver : public SolverBase {
         launch_pdl(k_gs_fine<true, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, 0, -1, k_vc, r, z);
         for (int gidx = 1; gidx < 4; ++gidx) {
             ++nl_;
-            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
-                           r, z);
+            fine_gs_pass(gidx);
         }
         ++nl_;
         if (tz_ > 0 && !std::is_same<S, double>::value)
@@ -752,8 +757,7 @@ class Solver : public SolverBase {
             launch_pdl(k_prolong_add<S, S, false>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, Tl[1], z);
         for (int gidx = 3; gidx >= 0; --gidx) {
             ++nl_;
-            launch_pdl(k_gs_fine<false, S, R, S>, OTM_ROWS_CFG(rl(n, (n / 2) * (n / 2))), stream, n, gidx, -1, k_vc,
-                       r, z);
+            fine_gs_pass(gidx);
         }
         OTM_LAUNCH();
         return OTM_OK;
