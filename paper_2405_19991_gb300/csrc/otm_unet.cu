@@ -3,6 +3,7 @@
 // the two operator-level convolution entry points.
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -60,10 +61,47 @@ std::atomic<long long> g_launches{0};
 
 int pick_bn(int cout) { return cout % 64 == 0 ? 64 : (cout % 32 == 0 ? 32 : 16); }
 
+// Opt in to the brick kernel's dynamic shared memory: once per kernel
+// instantiation and device (the attribute belongs to each instantiation;
+// this translation unit is the only one that launches them).
+template <int BN, bool RL>
+cudaError_t tile_prepare() {
+    static std::mutex m;
+    static bool granted[64] = {};
+    std::lock_guard<std::mutex> lock(m);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (granted[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(otm::nn::k_conv3_tile<BN, RL>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)otm::nn::conv3_tile_smem(BN));
+    if (e == cudaSuccess) granted[dev] = true;
+    return e;
+}
+
 // out = act(conv3(in) + bias)
 otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const float* bias, bool relu, bf16* out,
                  cudaStream_t st) {
     const size_t N = (size_t)n * n * n;
+    if (otm::nn::conv3_tile_ok(n) && cout % 16 == 0 && cin % 16 == 0) {
+        const int tb = cout % 32 == 0 ? 32 : 16;
+        const dim3 grid((unsigned)((n / otm::nn::kBX) * (n / otm::nn::kBY) * (n / otm::nn::kBZ)), (unsigned)(cout / tb));
+        const size_t smem = otm::nn::conv3_tile_smem(tb);
+        cudaError_t e = cudaSuccess;
+#define TILE_CASE(BN, RL)                                                                                  \
+    if (tb == BN && relu == RL) {                                                                          \
+        e = tile_prepare<BN, RL>();                                                                        \
+        if (e == cudaSuccess)                                                                              \
+            otm::nn::k_conv3_tile<BN, RL><<<grid, 256, smem, st>>>(n, cin, cout, in, w, bias, out);        \
+    }
+        TILE_CASE(16, true) TILE_CASE(16, false) TILE_CASE(32, true) TILE_CASE(32, false)
+#undef TILE_CASE
+        if (e != cudaSuccess) return ufail(OTM_ECUDA, std::string("conv3 shared-memory opt-in: ") + cudaGetErrorString(e));
+        g_launches += 1;
+        U_LAUNCH();
+        return OTM_OK;
+    }
     const int bn = pick_bn(cout);
     dim3 grid((unsigned)((N + otm::nn::kCM - 1) / otm::nn::kCM), (unsigned)(cout / bn));
 #define CONV_CASE(BN)                                                                                  \

@@ -401,3 +401,115 @@ static __global__ void k_pack_w(int a, int ap, int b, const float* __restrict__ 
 
 }  // namespace nn
 }  // namespace otm
+
+namespace otm {
+namespace nn {
+
+// Brick-tiled 3x3x3 circular convolution (same contract as k_conv3).  A CTA
+// of 8 warps computes an 8 x 8 x 4 brick of output voxels (M = 256) for BN
+// output channels.  Per 16-channel input chunk it stages the brick's input
+// halo (10 x 10 x 6 voxels, each row padded by 8 BF16 so that ldmatrix rows
+// fall on distinct banks) and the chunk's weights for all 27 taps in shared
+// memory, then every warp runs the 27 taps -- one ldmatrix of B per tap, one
+// ldmatrix of A and BN / 8 MMAs per 16-voxel row block -- without a barrier
+// inside the tap loop.  Requires n % 8 == 0 and 4 | n.
+constexpr int kBX = 8, kBY = 8, kBZ = 4;
+constexpr int kHX = kBX + 2, kHY = kBY + 2, kHZ = kBZ + 2;
+constexpr int kHalo = kHX * kHY * kHZ;          // 600 voxels
+constexpr int kHRow = 16 + 8;                   // one chunk's channels, padded
+
+inline size_t conv3_tile_smem(int bn) { return (size_t)kHalo * kHRow * 2 + (size_t)27 * 16 * (bn + 8) * 2; }
+inline bool conv3_tile_ok(int n) { return n >= kBX && n % kBX == 0 && n % kBZ == 0; }
+
+template <int BN, bool RELU>
+__global__ void __launch_bounds__(256)
+k_conv3_tile(int n, int Cin, int Cout, const bf16* __restrict__ in, const bf16* __restrict__ W,
+             const float* __restrict__ bias, bf16* __restrict__ out) {
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char conv_sm[];
+    bf16* halo = reinterpret_cast<bf16*>(conv_sm);                      // [kHalo][kHRow]
+    bf16* ws = halo + kHalo * kHRow;                                      // [27][16][BN + 8]
+    constexpr int WROW = BN + 8;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nbx = n / kBX, nby = n / kBY;
+    const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+    const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * kBZ;
+    const int co0 = blockIdx.y * BN;
+    // two 16-voxel row blocks per warp: voxel vi = 16 m + r of the brick,
+    // (vi % 8, (vi / 8) % 8, vi / 64)
+    float acc[2][BN / 8][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
+    // this lane's A row (voxel) of each row block, as a halo index at tap (0,0,0)
+    int hrow[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+        const int vi = (warp * 2 + m) * 16 + (lane & 15);
+        const int vx = vi % kBX, vy = (vi / kBX) % kBY, vz = vi / (kBX * kBY);
+        hrow[m] = (vx + 1) + kHX * ((vy + 1) + kHY * (vz + 1));
+    }
+    const int achunk = (lane >> 4) * 8;   // channel half of the A fragment
+    for (int c0 = 0; c0 < Cin; c0 += 16) {
+        __syncthreads();   // the previous chunk's tiles are no longer read
+        for (int e = tid; e < kHalo * 2; e += 256) {
+            const int hv = e >> 1, h = e & 1;
+            const int hx = hv % kHX, hy = (hv / kHX) % kHY, hz = hv / (kHX * kHY);
+            const size_t g = (size_t)wrapd(x0, hx - 1, n) +
+                             (size_t)n * ((size_t)wrapd(y0, hy - 1, n) + (size_t)n * wrapd(z0, hz - 1, n));
+            *reinterpret_cast<uint4*>(halo + hv * kHRow + h * 8) =
+                *reinterpret_cast<const uint4*>(in + g * Cin + c0 + h * 8);
+        }
+        constexpr int WCH = BN / 8;
+        for (int e = tid; e < 27 * 16 * WCH; e += 256) {
+            const int t = e / (16 * WCH), r = (e / WCH) % 16, cc = e % WCH;
+            *reinterpret_cast<uint4*>(ws + (t * 16 + r) * WROW + cc * 8) =
+                *reinterpret_cast<const uint4*>(W + ((size_t)t * Cin + c0 + r) * Cout + co0 + cc * 8);
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int t = 0; t < 27; ++t) {
+            const int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
+            const int hoff = dx + kHX * (dy + kHY * dz);
+            unsigned bfr[BN / 16][4];
+#pragma unroll
+            for (int j = 0; j < BN / 16; ++j)
+                ldsm_x4_t(bfr[j], ws + (t * 16 + (lane & 15)) * WROW + j * 16 + (lane >> 4) * 8);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                unsigned af[4];
+                ldsm_x4(af, halo + (hrow[m] + hoff) * kHRow + achunk);
+#pragma unroll
+                for (int j = 0; j < BN / 16; ++j) {
+                    mma_bf16(acc[m][2 * j], af, bfr[j][0], bfr[j][1]);
+                    mma_bf16(acc[m][2 * j + 1], af, bfr[j][2], bfr[j][3]);
+                }
+            }
+        }
+    }
+    // epilogue: bias, activation, BF16 store
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int vi = (warp * 2 + m) * 16 + (lane >> 2) + 8 * h;
+            const int vx = vi % kBX, vy = (vi / kBX) % kBY, vz = vi / (kBX * kBY);
+            const size_t g = (size_t)(x0 + vx) + (size_t)n * ((size_t)(y0 + vy) + (size_t)n * (z0 + vz));
+#pragma unroll
+            for (int j = 0; j < BN / 8; ++j) {
+                const int co = co0 + j * 8 + (lane & 3) * 2;
+                float y0v = acc[m][j][2 * h] + (bias ? bias[co] : 0.f);
+                float y1v = acc[m][j][2 * h + 1] + (bias ? bias[co + 1] : 0.f);
+                if (RELU) {
+                    y0v = fmaxf(y0v, 0.f);
+                    y1v = fmaxf(y1v, 0.f);
+                }
+                *reinterpret_cast<__nv_bfloat162*>(out + g * Cout + co) = __floats2bfloat162_rn(y0v, y1v);
+            }
+        }
+    }
+}
+
+}  // namespace nn
+}  // namespace otm

@@ -87,7 +87,8 @@ def _unflat(vec, widths):
 
 
 @pytest.mark.parametrize("n,cin,cout,relu", [(4, 16, 16, 1), (6, 16, 32, 0), (8, 48, 16, 1),
-                                             (5, 32, 64, 1), (8, 128, 64, 0), (3, 64, 128, 1)])
+                                             (5, 32, 64, 1), (8, 128, 64, 0), (3, 64, 128, 1),
+                                             (16, 16, 16, 1), (16, 48, 16, 0), (24, 32, 32, 1), (32, 16, 32, 0)])
 def test_conv3_matches_definition(n, cin, cout, relu):
     otm = _otm()
     torch = _torch()
