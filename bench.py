@@ -186,6 +186,27 @@ def cpu_sample(wl, budget_s=25.0, chunk=10, steps=None, warmup=0, log=None):
                 cg_needed=n_needed, res_reached=hist[-1][1], per_step=per_step, t_oc=t_oc)
 
 
+# ------------------------------------------------------------- replicas
+def replica_seed(wl, rank):
+    """Replicas only: rank r designs its own cell from seed + r."""
+    return wl.seed + rank
+
+
+def max_over_ranks(x, world, device):
+    """The slowest rank's value (the timing protocol's MAX over ranks)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds_max
+
+
 # ------------------------------------------------------------------ forms
 def timed_steps(otm, ctx, stream, steps, warmup):
     """Device time of `steps` OC iterations after `warmup` untimed ones."""
@@ -246,6 +267,43 @@ def run_batch(otm, args, count=64, iters=10):
     return rec
 
 
+def unet_flops(n, widths):
+    """Algorithmic FLOPs of one U-Net forward (2 per multiply-add; the
+    3x3x3 convolutions of the seven blocks and the 1x1 head)."""
+    c0, c1, c2, c3 = widths
+    blocks = [(0, 1, c0), (1, c0, c1), (2, c1, c2), (3, c2, c3), (2, c3 + c2, c2), (1, c2 + c1, c1), (0, c1 + c0, c0)]
+    f = 0
+    for lev, a, b in blocks:
+        vox = (n >> lev) ** 3
+        f += 2 * vox * 27 * (a * b + b * b)
+    return f + 2 * n ** 3 * c0 * 3
+
+
+def unet_rate(otm, unet, n, widths, buf, stream, reps=10):
+    """U-Net forward throughput at the design resolution, CUDA events around
+    the forward call, against the measured BF16 tensor peak."""
+    import torch
+    y = torch.empty(3 * n ** 3, dtype=torch.float32, device=buf.x.device)
+    for _ in range(2):
+        otm.otm_unet_forward(unet, buf.x[0].data_ptr(), y.data_ptr(), stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        otm.otm_unet_forward(unet, buf.x[0].data_ptr(), y.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = unet_flops(n, widths)
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        peak = 1900.0
+    tf = flops / (ms * 1e-3) / 1e12
+    return {"ms": ms, "gflop": flops / 1e9, "tflops": tf, "peak_tflops": peak, "frac": tf / peak,
+            "note": "whole forward incl. pooling, concatenation and head kernels; BF16 mma.sync"}
+
+
 def run_forms(args, wl, dev, stream, rank, plain_value):
     """Cold start, BF16 V-cycle, and learned warm start + BF16 V-cycle on the
     benchmark workload; the warm-start network (widths 16/32/64/128) is
@@ -260,7 +318,7 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
                                       cg_maxit=500, precision=prec, warm_start=ws, stream=stream.cuda_stream,
                                       device=dev)
 
-    rho0 = W.initial_density(wl.n, wl.volfrac, wl.seed + rank).astype(np.float32)
+    rho0 = W.initial_density(wl.n, wl.volfrac, replica_seed(wl, rank)).astype(np.float32)
     out = {}
 
     def form(name, prec, ws, unet=None, scale=1.0):
@@ -310,6 +368,8 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
         warmstart.collect(params(1, otm.OTM_WS_PREV), rho0, 4, held)
         held_loss = warmstart.evaluate(unet, held, scale, stream.cuda_stream)
         form("learned_start_mixed_bf16_vcycle", 2, otm.OTM_WS_LEARNED, unet, scale)
+        out["learned_start_mixed_bf16_vcycle"]["unet_forward"] = unet_rate(otm, unet, wl.n, (16, 32, 64, 128),
+                                                                           held, stream)
         out["learned_start_mixed_bf16_vcycle"]["training"] = {
             "pairs": buf.count, "histories": list(seeds), "iters_per_history": hist_iters,
             "collect_s": t_collect, "adam_steps": args.train_steps, "lr": 1e-3, "train_s": t_train,
@@ -335,7 +395,7 @@ def run_ours(args, rank, world):
                                cg_maxit=500, precision=prec, warm_start=otm.OTM_WS_PREV,
                                stream=stream.cuda_stream, device=dev)
     ctx = otm.otm_create_ex(p)
-    rho0 = W.initial_density(wl.n, wl.volfrac, wl.seed + rank).astype(np.float32)
+    rho0 = W.initial_density(wl.n, wl.volfrac, replica_seed(wl, rank)).astype(np.float32)
     rho_h = torch.from_numpy(rho0).pin_memory()
     rho_d = rho_h.to(f"cuda:{dev}")
     otm.otm_set_density(ctx, rho_d.data_ptr(), 1)
@@ -366,10 +426,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{dev}")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, f"cuda:{dev}")
 
     # ---- end to end through the public API with host-resident state:
     # each step ships the design state (density + previous corrector) in
@@ -392,10 +449,7 @@ def run_ours(args, rank, world):
         otm.check(otm.lib.otm_get_state(ctx, ctypes.c_void_p(host_out.data_ptr()), ctypes.byref(ln)), ctx)
         host_in, host_out = host_out, host_in
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{dev}")
-    if world > 1:
-        torch.distributed.all_reduce(e2e_t, op=torch.distributed.ReduceOp.MAX)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, f"cuda:{dev}")
 
     # ---- roofline of the dominant kernel: the 3-RHS stencil K(k) u of the
     # PCG, launched through its operator entry point on this context's own
@@ -437,8 +491,7 @@ def run_ours(args, rank, world):
     except (OSError, ValueError):
         traffic = None
 
-    steps_total = args.steps * world
-    value = steps_total / (ms_max * 1e-3)
+    value = aggregate_rate(args.steps, world, ms_max * 1e-3)
     cg = [list(i.cg_iters) for i in infos]
     result = {
         "metric": METRIC,
@@ -459,7 +512,7 @@ def run_ours(args, rank, world):
                    "warm_start": "previous iterate", "parallelism": f"replicas{world}",
                    "l2": "per-step working set (~0.4 GB of fields, ~0.7 GB moved per PCG iteration) exceeds the 129 MB L2",
                    "mean_cg_iters": float(np.mean(cg)), "max_true_resid": float(max(max(i.resid) for i in infos))},
-        "e2e": {"value": e_steps * world / float(e2e_t.item()), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": aggregate_rate(e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes,
                 "path": "otm_set_state (pinned host) -> otm_step -> otm_get_state (pinned host)"},
         "gpu_launches": launches,
