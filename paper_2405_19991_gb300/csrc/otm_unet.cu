@@ -116,10 +116,51 @@ otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const 
     return OTM_OK;
 }
 
+template <int BN>
+cudaError_t dw_tile_prepare() {
+    static std::mutex m;
+    static bool granted[64] = {};
+    std::lock_guard<std::mutex> lock(m);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (granted[dev]) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(otm::nn::k_conv3_dw_tile<BN>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)otm::nn::conv3_dw_tile_smem(BN));
+    if (e == cudaSuccess) granted[dev] = true;
+    return e;
+}
+
 // dW[27][ca][cout] += ..., db += ... (in stored with cin >= ca channels)
 otm_status conv3_wgrad(int n, int cin, int ca, int cout, const bf16* in, const bf16* g, float* dw, float* db,
                        cudaStream_t st) {
     const size_t N = (size_t)n * n * n;
+    if (otm::nn::conv3_tile_ok(n) && cin % 16 == 0 && cout % 16 == 0) {
+        const int tb = cout % 32 == 0 ? 32 : 16;
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int nbricks = (n / otm::nn::kBX) * (n / otm::nn::kBY) * (n / otm::nn::kBZ);
+        const int per = (cin / 16) * (cout / tb);
+        int P = (3 * (sms > 0 ? sms : 1) + per - 1) / per;
+        if (P > nbricks) P = nbricks;
+        if (P < 1) P = 1;
+        const dim3 grid((unsigned)P, (unsigned)(cin / 16), (unsigned)(cout / tb));
+        const size_t smem = otm::nn::conv3_dw_tile_smem(tb);
+        cudaError_t e;
+        if (tb == 32) {
+            e = dw_tile_prepare<32>();
+            if (e == cudaSuccess) otm::nn::k_conv3_dw_tile<32><<<grid, 256, smem, st>>>(n, cin, ca, cout, in, g, dw, db);
+        } else {
+            e = dw_tile_prepare<16>();
+            if (e == cudaSuccess) otm::nn::k_conv3_dw_tile<16><<<grid, 256, smem, st>>>(n, cin, ca, cout, in, g, dw, db);
+        }
+        if (e != cudaSuccess) return ufail(OTM_ECUDA, std::string("conv3_wgrad shared-memory opt-in: ") + cudaGetErrorString(e));
+        g_launches += 1;
+        U_LAUNCH();
+        return OTM_OK;
+    }
     const int bn = pick_bn(cout);
     const long long per = 27LL * (cin / 16) * (cout / bn);
     int sms = 0, dev = 0;

@@ -513,3 +513,115 @@ k_conv3_tile(int n, int Cin, int Cout, const bf16* __restrict__ in, const bf16* 
 
 }  // namespace nn
 }  // namespace otm
+
+namespace otm {
+namespace nn {
+
+// Brick-tiled weight gradient (same contract as k_conv3_dw):
+//   dW[t][ci][co] += sum_v in[v + d_t][ci] g[v][co],  db[co] += sum_v g[v][co].
+// Grid (P, Cin / 16, Cout / BN).  CTA p walks the bricks p, p + P, ... of the
+// n^3 grid (8 x 8 x 4 voxels each): it stages the brick's input halo for its
+// 16-channel chunk and the brick's output gradient for its BN channels, and
+// warp w accumulates the taps w, w + 8, w + 16, w + 24 (< 27) as 16 x BN
+// products over the brick's 256 voxels (16 k-steps of 16 voxels; A = the
+// shifted input transposed, B = the gradient, both by ldmatrix.trans).  The
+// per-tap partials stay in registers across the CTA's bricks and are added
+// to dW once, at the end.  Requires n % 8 == 0 and 4 | n.
+constexpr int kDwTaps = 4;
+
+inline size_t conv3_dw_tile_smem(int bn) { return (size_t)kHalo * kHRow * 2 + (size_t)kBX * kBY * kBZ * (bn + 8) * 2; }
+
+template <int BN>
+__global__ void __launch_bounds__(256)
+k_conv3_dw_tile(int n, int Cin, int Ca, int Cout, const bf16* __restrict__ in, const bf16* __restrict__ g,
+                float* __restrict__ dW, float* __restrict__ db) {
+    pdl_enter();
+    extern __shared__ __align__(16) unsigned char dw_sm[];
+    bf16* halo = reinterpret_cast<bf16*>(dw_sm);        // [kHalo][kHRow]
+    bf16* gs = halo + kHalo * kHRow;                      // [256][BN + 8]
+    constexpr int GROW = BN + 8;
+    constexpr int NV = kBX * kBY * kBZ;                   // 256 voxels per brick
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ci0 = blockIdx.y * 16, co0 = blockIdx.z * BN;
+    const int nbx = n / kBX, nby = n / kBY, nbz = n / kBZ;
+    const int nbricks = nbx * nby * nbz;
+    float acc[kDwTaps][BN / 8][4];
+#pragma unroll
+    for (int q = 0; q < kDwTaps; ++q)
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j) acc[q][j][0] = acc[q][j][1] = acc[q][j][2] = acc[q][j][3] = 0.f;
+    float bsum = 0.f;
+    const bool do_db = db != nullptr && blockIdx.y == 0 && tid < BN;
+    // this lane's voxel (A^T row block: 16 voxels per k-step) and channel half
+    const int lr = (lane & 7) + ((lane >> 4) << 3), lc = ((lane >> 3) & 1) * 8;
+    for (int b = blockIdx.x; b < nbricks; b += gridDim.x) {
+        const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+        const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * kBZ;
+        __syncthreads();   // the previous brick's tiles are no longer read
+        for (int e = tid; e < kHalo * 2; e += 256) {
+            const int hv = e >> 1, h = e & 1;
+            const int hx = hv % kHX, hy = (hv / kHX) % kHY, hz = hv / (kHX * kHY);
+            const size_t gv = (size_t)wrapd(x0, hx - 1, n) +
+                              (size_t)n * ((size_t)wrapd(y0, hy - 1, n) + (size_t)n * wrapd(z0, hz - 1, n));
+            *reinterpret_cast<uint4*>(halo + hv * kHRow + h * 8) =
+                *reinterpret_cast<const uint4*>(in + gv * Cin + ci0 + h * 8);
+        }
+        constexpr int GCH = BN / 8;
+        for (int e = tid; e < NV * GCH; e += 256) {
+            const int vi = e / GCH, cc = e % GCH;
+            const int vx = vi % kBX, vy = (vi / kBX) % kBY, vz = vi / (kBX * kBY);
+            const size_t gv = (size_t)(x0 + vx) + (size_t)n * ((size_t)(y0 + vy) + (size_t)n * (z0 + vz));
+            *reinterpret_cast<uint4*>(gs + vi * GROW + cc * 8) =
+                *reinterpret_cast<const uint4*>(g + gv * Cout + co0 + cc * 8);
+        }
+        __syncthreads();
+        if (do_db)
+            for (int r = 0; r < NV; ++r) bsum += __bfloat162float(gs[r * GROW + tid]);
+#pragma unroll 1
+        for (int ks = 0; ks < NV / 16; ++ks) {
+            unsigned bfr[BN / 16][4];
+#pragma unroll
+            for (int j = 0; j < BN / 16; ++j)
+                ldsm_x4_t(bfr[j], gs + (ks * 16 + (lane & 15)) * GROW + j * 16 + (lane >> 4) * 8);
+            // this lane's voxel of the k-step, as a halo index at tap (0, 0, 0)
+            const int vi = ks * 16 + lr;
+            const int hv0 = (vi % kBX + 1) + kHX * (((vi / kBX) % kBY + 1) + kHY * (vi / (kBX * kBY) + 1));
+#pragma unroll
+            for (int q = 0; q < kDwTaps; ++q) {
+                const int t = warp + 8 * q;
+                if (t < 27) {
+                    const int hoff = (t % 3 - 1) + kHX * ((t / 3) % 3 - 1 + kHY * (t / 9 - 1));
+                    unsigned af[4];
+                    ldsm_x4_t(af, halo + (hv0 + hoff) * kHRow + lc);
+#pragma unroll
+                    for (int j = 0; j < BN / 16; ++j) {
+                        mma_bf16(acc[q][2 * j], af, bfr[j][0], bfr[j][1]);
+                        mma_bf16(acc[q][2 * j + 1], af, bfr[j][2], bfr[j][3]);
+                    }
+                }
+            }
+        }
+    }
+    // add the partials: rows ci (lane >> 2, + 8), columns co
+#pragma unroll
+    for (int q = 0; q < kDwTaps; ++q) {
+        const int t = warp + 8 * q;
+        if (t >= 27) continue;
+#pragma unroll
+        for (int j = 0; j < BN / 8; ++j) {
+            const int c = co0 + j * 8 + (lane & 3) * 2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ci = ci0 + (lane >> 2) + 8 * h;
+                if (ci < Ca) {
+                    atomicAdd(dW + ((size_t)t * Ca + ci) * Cout + c, acc[q][j][2 * h]);
+                    atomicAdd(dW + ((size_t)t * Ca + ci) * Cout + c + 1, acc[q][j][2 * h + 1]);
+                }
+            }
+        }
+    }
+    if (do_db) atomicAdd(db + co0 + tid, bsum);
+}
+
+}  // namespace nn
+}  // namespace otm

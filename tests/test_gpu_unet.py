@@ -112,7 +112,8 @@ def test_conv3_matches_definition(n, cin, cout, relu):
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
 
 
-@pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32)])
+@pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32), (16, 48, 16),
+                                        (16, 16, 32), (32, 32, 32), (24, 16, 16)])
 def test_conv3_weight_gradient_matches_definition(n, cin, cout):
     otm = _otm()
     torch = _torch()
