@@ -217,3 +217,49 @@ def test_256_anisotropic_error_per_precision():
     print(f"256^3 kappa error vs the FP64 path: FP32 {e32:.2e}, mixed {emx:.2e}")
     assert e32 <= 1e-6
     assert emx <= 1e-4
+
+
+@pytest.mark.parametrize("n,precision", [(24, 1), (48, 1), (48, 2), (64, 1)])
+def test_batch_sizes_match_oracle(n, precision):
+    """The hierarchy shapes of the batched workload's sizes (24 -> 12 -> 6,
+    48 -> ... -> 6, 64 -> ... -> 4: standalone, cluster and shared-memory tail
+    levels, 6^3 and 4^3 coarsest solves) against the oracle's tensor."""
+    rho = W.initial_density(n, 0.3, 300 + n).astype(np.float32)
+    ctx, otm = _ctx(n, precision, 1e-6, rmin=2.0)
+    try:
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        assert max(info.resid) <= 1e-6 * 1.0001
+    finally:
+        otm.otm_destroy(ctx)
+    rf = design.density_filter(n, rho.astype(np.float64), 2.0)
+    ref = fem.homogenize(n, design.simp(rf, 3.0, 1.0, 1e-3), tol=1e-12)
+    assert rel_fro(kap, ref["kappa"]) <= TOL[precision]
+
+
+def test_96_sampled_residual():
+    """n = 96 (96 -> 48 -> 24 -> 12 -> 6): the oracle's residual at sampled
+    nodes from the GPU's own k and corrector."""
+    otm = _otm()
+    n, N = 96, 96 ** 3
+    p = otm.otm_params_default(n=n, precision=1, cg_tol=1e-6, rmin=2.0, kappa_target=W.TARGET_ORTHOTROPIC)
+    ctx = otm.otm_create_ex(p)
+    try:
+        rho = W.initial_density(n, 0.35, 7).astype(np.float32)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        k = np.empty(N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_K, k.ctypes.data, N, 0)
+        chi = np.empty(3 * N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * N, 0)
+        k = k.astype(np.float64)
+        chi = chi.reshape(3, N).astype(np.float64)
+        f = fem.macro_load(n, k)
+        nodes = np.random.default_rng(5).choice(N, 300, replace=False)
+        r = f[:, nodes] - fem.apply_operator_at(n, k, chi, nodes)
+        for i in range(3):
+            assert np.max(np.abs(r[i])) <= 1.5e-6 * np.linalg.norm(f[i] - f[i].mean())
+        E = fem.element_energies(n, chi)
+        assert rel_fro(kap, fem.kappa_from_energies(k, E)) <= 1e-6
+    finally:
+        otm.otm_destroy(ctx)
