@@ -91,8 +91,8 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
     }
     if (SIMP) {
         __shared__ double res[2];
-        double vals[2] = {a_rho.value(), a_rhop.value()};
-        if (grid_reduce<2>(vals, rb, res)) {
+        const Acc<C> sums[2] = {a_rho, a_rhop};
+        if (grid_reduce<2>(sums, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }
@@ -197,10 +197,7 @@ k_kappa(int n, const R* __restrict__ k, const R* __restrict__ chi, RedBuf rb, Fi
     }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) vals[c] = acc[c].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -313,7 +310,10 @@ k_oc_prep(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, 
     pdl_enter();
     using C = typename St<R>::C;
     Acc<C> vmin, vmax;
-    double mumin = 1e300, mumax = 0.0;
+    // per-element min / max in the compute type, widened once per warp
+    // (exact: the conversion to double is monotone)
+    bool seen = false;
+    C mumin = 0, mumax = 0;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
          e += (size_t)gridDim.x * blockDim.x) {
         C lo, hi, c;
@@ -322,28 +322,33 @@ k_oc_prep(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op, 
         if (c > C(0)) {
             vmax.add(hi);
             const C ic = C(1) / c;
-            const double a = (double)(lo * ic), b = (double)(hi * ic);
-            mumin = a < mumin ? a : mumin;
-            mumax = b > mumax ? b : mumax;
+            const C a = lo * ic, b = hi * ic;
+            mumin = (!seen || a < mumin) ? a : mumin;
+            mumax = (!seen || b > mumax) ? b : mumax;
+            seen = true;
         } else {
             vmax.add(lo);
         }
     }
-    // block min / max, then one atomic per block (order-independent)
+    // warp min / max, then one atomic per warp (order-independent)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double a = __shfl_xor_sync(0xffffffffu, mumin, o);
-        const double b = __shfl_xor_sync(0xffffffffu, mumax, o);
-        mumin = a < mumin ? a : mumin;
-        mumax = b > mumax ? b : mumax;
+        const bool s2 = __shfl_xor_sync(0xffffffffu, seen, o);
+        const C a = __shfl_xor_sync(0xffffffffu, mumin, o);
+        const C b = __shfl_xor_sync(0xffffffffu, mumax, o);
+        if (s2) {
+            mumin = (!seen || a < mumin) ? a : mumin;
+            mumax = (!seen || b > mumax) ? b : mumax;
+            seen = true;
+        }
     }
-    if ((threadIdx.x & 31) == 0) {
-        if (mumin < 1e300) atomicMin((unsigned long long*)&ds->mu_min_seen, dbits(mumin));
-        if (mumax > 0.0) atomicMax((unsigned long long*)&ds->mu_max_seen, dbits(mumax));
+    if ((threadIdx.x & 31) == 0 && seen) {
+        atomicMin((unsigned long long*)&ds->mu_min_seen, dbits((double)mumin));
+        if ((double)mumax > 0.0) atomicMax((unsigned long long*)&ds->mu_max_seen, dbits((double)mumax));
     }
     __shared__ double res[2];
-    double vals[2] = {vmin.value(), vmax.value()};
-    if (grid_reduce<2>(vals, rb, res)) {
+    const Acc<C> sums[2] = {vmin, vmax};
+    if (grid_reduce<2>(sums, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -414,10 +419,10 @@ k_oc_search(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op
         }
     }
     __shared__ double res[kOcCand];
-    double vals[kOcCand];
+    Acc<C> sums[kOcCand];
 #pragma unroll
-    for (int j = 0; j < kOcCand; ++j) vals[j] = (double)sum[j];
-    if (grid_reduce<kOcCand>(vals, rb, res)) {
+    for (int j = 0; j < kOcCand; ++j) sums[j].add(sum[j]);
+    if (grid_reduce<kOcCand>(sums, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }

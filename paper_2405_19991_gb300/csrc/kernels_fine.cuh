@@ -350,10 +350,7 @@ k_stencil_apply(int n, const KT* __restrict__ k, const UT* __restrict__ u, const
     }
     if (DOT) {
         __shared__ double res[6];
-        double vals[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-        if (grid_reduce<6>(vals, rb, res)) {
+        if (grid_reduce<6>(acc, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }
@@ -388,10 +385,7 @@ k_residual_x2(int n, const R* __restrict__ k, const R* __restrict__ xh, const R*
     }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -441,10 +435,7 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
     }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -550,10 +541,7 @@ k_sum3(size_t N, const R* __restrict__ f, RedBuf rb, FinMean fin) {
         for (int i = 0; i < 3; ++i) acc[i].add(f[(size_t)i * N + v]);
     }
     __shared__ double res[3];
-    double vals[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<3>(vals, rb, res)) {
+    if (grid_reduce<3>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -720,10 +708,7 @@ k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, 
         }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -783,10 +768,7 @@ k_update_xr4(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r,
         }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -809,10 +791,7 @@ k_dot_rz4(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb
         }
     }
     __shared__ double res[3];
-    double vals[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<3>(vals, rb, res)) {
+    if (grid_reduce<3>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -871,10 +850,7 @@ k_dot_rz(size_t N, const R* __restrict__ r, const ZT* __restrict__ z, RedBuf rb,
         }
     }
     __shared__ double res[3];
-    double vals[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<3>(vals, rb, res)) {
+    if (grid_reduce<3>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }

@@ -422,7 +422,8 @@ __device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* 
     const int q = m - 1;
     __shared__ C fs[3][343];
     __shared__ C ts[3][343];
-    __shared__ double red[3][32];
+    __shared__ Acc<C> red[3][32];
+    __shared__ C mean[3];
     for (int i = threadIdx.x; i < 3 * m; i += blockDim.x)
         fs[i / m][i % m] = St<FT>::ld(f, AOS ? (size_t)(i % m) * 4 + i / m : (size_t)i);
     __syncthreads();
@@ -437,23 +438,24 @@ __device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* 
         ts[r][v] = a;
     }
     __syncthreads();
+    // load-case means, summed compensated in the compute type
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int r = 0; r < 3; ++r) {
-        double s = 0.0;
-        for (int v = threadIdx.x; v < m; v += blockDim.x) s += (double)ts[r][v];
-        s = warp_sum(s);
-        if (lane == 0) red[r][warp] = s;
+        Acc<C> a;
+        for (int v = threadIdx.x; v < m; v += blockDim.x) a.add(ts[r][v]);
+        acc_warp_sum(a);
+        if (lane == 0) red[r][warp] = a;
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
-        red[threadIdx.x][0] = s / m;
+        Acc<C> a = red[threadIdx.x][0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) acc_merge(a, red[threadIdx.x][w]);
+        mean[threadIdx.x] = (C)(a.value() / m);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < 3 * m; t += blockDim.x) {
         const int r = t / m, v = t % m;
-        St<TT>::st(T, AOS ? (size_t)v * 4 + r : (size_t)t, ts[r][v] - (C)red[r][0]);
+        St<TT>::st(T, AOS ? (size_t)v * 4 + r : (size_t)t, ts[r][v] - mean[r]);
     }
 }
 

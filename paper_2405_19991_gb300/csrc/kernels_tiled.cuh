@@ -185,10 +185,7 @@ k_stencil_tiled(int n, int tz, const KT* __restrict__ k, const UT* __restrict__ 
     }
     if (DOT) {
         __shared__ double res[6];
-        double vals[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-        if (grid_reduce<6>(vals, rb, res)) {
+        if (grid_reduce<6>(acc, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }

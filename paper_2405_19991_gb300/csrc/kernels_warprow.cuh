@@ -211,10 +211,7 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
         }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }
@@ -306,10 +303,7 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
         }
     }
     __shared__ double res[6];
-    double vals[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-    if (grid_reduce<6>(vals, rb, res)) {
+    if (grid_reduce<6>(acc, rb, res)) {
         if (is_thread0()) fin(res);
     }
 }

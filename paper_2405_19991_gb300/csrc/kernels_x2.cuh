@@ -14,6 +14,7 @@
 // results.  The stencil is issue-bound in its one-node forms (shared loads
 // and FP instructions per node); pairing roughly halves both.
 #pragma once
+#include <algorithm>
 #include <cstdlib>
 
 #include "kernels_fine.cuh"
@@ -44,7 +45,14 @@ inline int stencil_choice() {
     return c;
 }
 
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// a - b on both lanes (one packed FP32 subtract; bitwise a + (-b))
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
 
 #ifndef OTM_X2_MINB
 #define OTM_X2_MINB 2
@@ -207,10 +215,7 @@ k_stencil_x2(int n, int tz, const float* __restrict__ k, const float* __restrict
     }
     if (DOT) {
         __shared__ double res[6];
-        double vals[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) vals[i] = acc[i].value();
-        if (grid_reduce<6>(vals, rb, res)) {
+        if (grid_reduce<6>(acc, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }
@@ -241,8 +246,9 @@ inline int x2_grid(int n, int tz) { return (n / kX2N) * (n / kX2Y) * (n / tz); }
 namespace otm {
 
 // z-reuse form of the paired stencil: a CTA handles one load case of a
-// 64 x 8 tile (1-D grid, the load case fastest so a tile's three CTAs run
-// together and share its conductivities in L2) and keeps, per thread, the node pair's
+// 64 x 8 tile over one of m equal z-chunks (planes c n / m .. (c + 1) n / m;
+// 1-D grid, the load case fastest so a tile's three CTAs run together and
+// share its conductivities in L2), and keeps, per thread, the node pair's
 // neighbour rows (x - 1 .. x + 2 at y - 1 .. y + 1) of planes z - 1, z, z + 1
 // and the conductivities of element planes z - 1, z in registers.  Marching
 // one plane in z loads only the new plane's rows from shared memory (one
@@ -250,8 +256,8 @@ namespace otm {
 // shared-memory traffic per node of the three-plane ring.  Same arithmetic
 // and operation order as every other stencil form (bitwise equal results).
 template <bool DOT, class Fin>
-__global__ void __launch_bounds__(256)
-k_stencil_zr(int n, int tz, const float* __restrict__ k, const float* __restrict__ u, float* __restrict__ out,
+__global__ void __launch_bounds__(256, 3)
+k_stencil_zr(int n, int m, const float* __restrict__ k, const float* __restrict__ u, float* __restrict__ out,
              RedBuf rb, Fin fin) {
     pdl_enter();
     constexpr int UP = kX2PY * kX2PX;            // one field plane with halo
@@ -263,7 +269,8 @@ k_stencil_zr(int n, int tz, const float* __restrict__ k, const float* __restrict
     const int fi = blockIdx.x % 3;               // load case
     const int b = blockIdx.x / 3;
     const int tix = b % ntx, tiy = (b / ntx) % nty, tiz = b / (ntx * nty);
-    const int x0 = tix * kX2N, y0 = tiy * kX2Y, z0 = tiz * tz;
+    const int x0 = tix * kX2N, y0 = tiy * kX2Y;
+    const int z0 = tiz * n / m, z1 = (tiz + 1) * n / m;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kX2T * ty;
     const size_t nn = (size_t)n * n;
     const float* uf = u + (size_t)fi * N;
@@ -349,12 +356,12 @@ k_stencil_zr(int n, int tz, const float* __restrict__ k, const float* __restrict
     const int x = x0 + 2 * tx, y = y0 + ty;
     const float2 m12 = make_float2(-1.0f / 12.0f, -1.0f / 12.0f);
     int slot = 0;
-    for (int z = z0; z < z0 + tz; ++z) {
+    for (int z = z0; z < z1; ++z) {
         // slot was last read two planes ago (before the previous barrier)
         store_u(slot);
         store_k(slot);
         __syncthreads();
-        if (z + 1 < z0 + tz) {
+        if (z + 1 < z1) {
             load_u(z + 2);
             load_k(z + 1);
         }
@@ -416,35 +423,51 @@ k_stencil_zr(int n, int tz, const float* __restrict__ k, const float* __restrict
         }
     }
     if (DOT) {
-        __shared__ double res[6];
-        double vals[6] = {0, 0, 0, 0, 0, 0};
-        vals[fi] = acc.value();
-        if (grid_reduce<6>(vals, rb, res)) {
+        __shared__ double res[3];
+        Acc<float> sums[3];
+        if (fi == 0) sums[0] = acc;
+        else if (fi == 1) sums[1] = acc;
+        else sums[2] = acc;
+        if (grid_reduce<3>(sums, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }
 }
 
-// Grid of the z-reuse form: 3 load cases x tiles x z-chunks.
-inline int zr_grid(int n, int tz) { return 3 * (n / kX2N) * (n / kX2Y) * (n / tz); }
+// Grid of the z-reuse form: 3 load cases x tiles x m z-chunks.
+inline int zr_grid(int n, int m) { return 3 * (n / kX2N) * (n / kX2Y) * m; }
 
-// z-planes per CTA of the z-reuse form: the largest power-of-two divisor of
-// n (at most n / 4, so the plane march amortises its prologue) that gives
-// at least 4 CTAs per SM and no more CTAs than the reduction partials hold;
-// 0 when the form does not apply.  OTM_ZR_TZ overrides.
-inline int zr_tz(int n, int sm_count, int max_blocks) {
+// z-chunks per column of the z-reuse form.  Cost model: the launch runs
+// ceil(CTAs / resident slots) waves, each as long as one chunk's planes plus
+// about 1.5 planes of prologue; m minimises that over chunks of at least 4
+// planes and grids the reduction partials hold.  per_sm = resident CTAs per
+// SM of the variant launched; 0 when the form does not apply.  OTM_ZR_M
+// overrides (for sweeps).
+inline int zr_m(int n, int sm_count, int per_sm, int max_blocks) {
     if (!x2_ok(n)) return 0;
-    const long long per_z = 3LL * (n / kX2N) * (n / kX2Y);
-    int tz = n;
-    const char* e = getenv("OTM_ZR_TZ");
-    if (e && atoi(e) >= 1 && n % atoi(e) == 0) {
-        tz = atoi(e);
-    } else {
-        while (tz % 2 == 0 && tz > 2 && (tz > n / 4 || per_z * (n / tz) < 4LL * sm_count)) tz /= 2;
-        while (per_z * (n / tz) > max_blocks && tz < n && n % (2 * tz) == 0) tz *= 2;
+    const long long per_m = 3LL * (n / kX2N) * (n / kX2Y);
+    const long long slots = (long long)std::max(per_sm, 1) * sm_count;
+    const char* e = getenv("OTM_ZR_M");
+    if (e && atoi(e) >= 1 && atoi(e) <= n && per_m * atoi(e) <= max_blocks) return atoi(e);
+    int best = 0;
+    double best_t = 0.0;
+    for (int m = 1; m <= n / 4; ++m) {
+        if (per_m * m > max_blocks) break;
+        const long long waves = (per_m * m + slots - 1) / slots;
+        const double t = (double)waves * ((double)n / m + 1.5);
+        if (best == 0 || t < best_t - 1e-9) {
+            best = m;
+            best_t = t;
+        }
     }
-    if (per_z * (n / tz) > max_blocks) return 0;
-    return tz;
+    return best;
+}
+template <bool DOT, class Fin>
+inline int zr_m_for(int n, int sm_count, int max_blocks) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stencil_zr<DOT, Fin>, kX2T * kX2Y, 0) != cudaSuccess)
+        per_sm = 1;
+    return zr_m(n, sm_count, per_sm, max_blocks);
 }
 
 }  // namespace otm

@@ -395,6 +395,99 @@ __device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out
     return true;
 }
 
+// The same reduction for FP32 accumulators, in double-float arithmetic:
+// each value travels as its Acc<float> pair (s, c) with value s + c, and
+// two pairs combine as TwoSum(s1, s2) = (t, e), c = (c1 + c2) + e, s = t --
+// error-free in the leading part, so a sum keeps ~48 significant bits.  No
+// FP64 instruction runs except in the last block's thread 0, which forms
+// the doubles handed to the finaliser (FP64 units on this part run at a
+// small fraction of the FP32 rate, so a per-warp double tree dominated the
+// reduction kernels).  The pair combination is symmetric bit for bit (the
+// TwoSum error term does not depend on the operand order), so butterfly
+// lanes agree and the result is the same for the same grid.
+__device__ __forceinline__ void ff_add(float& s, float& c, float s2, float c2) {
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);
+    c = (c + c2) + e;
+    s = t;
+}
+__device__ __forceinline__ void ff_warp_sum(float& s, float& c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+        ff_add(s, c, s2, c2);
+    }
+}
+// Warp sums and merges of accumulators, in their own precision.
+__device__ __forceinline__ void acc_warp_sum(Acc<float>& a) { ff_warp_sum(a.s, a.c); }
+__device__ __forceinline__ void acc_warp_sum(Acc<double>& a) { a.s = warp_sum(a.s); }
+__device__ __forceinline__ void acc_merge(Acc<float>& a, const Acc<float>& b) { ff_add(a.s, a.c, b.s, b.c); }
+__device__ __forceinline__ void acc_merge(Acc<double>& a, const Acc<double>& b) { a.s += b.s; }
+template <int NV>
+__device__ bool grid_reduce(const Acc<float> (&v)[NV], const RedBuf& rb, double* out) {
+    __shared__ float2 sm[32][NV];
+    __shared__ bool is_last;
+    float2* part = reinterpret_cast<float2*>(rb.partials);   // [blocks][NV] pairs
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarp = (nthr + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        float s = v[i].s, c = v[i].c;
+        ff_warp_sum(s, c);
+        if (lane == 0) sm[warp][i] = make_float2(s, c);
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            float2 w = lane < nwarp ? sm[lane][i] : make_float2(0.f, 0.f);
+            ff_warp_sum(w.x, w.y);
+            if (lane == 0) part[(size_t)blockIdx.x * NV + i] = w;
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        unsigned int t = atomicAdd(rb.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    // fixed-order sum of the partials: strided per thread, then a fixed tree
+#pragma unroll 1
+    for (int i = 0; i < NV; ++i) {
+        float s = 0.f, c = 0.f;
+        for (int b = tid; b < (int)gridDim.x; b += nthr) {
+            const float2 w = __ldcg(part + (size_t)b * NV + i);
+            ff_add(s, c, w.x, w.y);
+        }
+        ff_warp_sum(s, c);
+        __syncthreads();
+        if (lane == 0) sm[warp][i] = make_float2(s, c);
+        __syncthreads();
+        if (warp == 0) {
+            float2 w = lane < nwarp ? sm[lane][i] : make_float2(0.f, 0.f);
+            ff_warp_sum(w.x, w.y);
+            if (lane == 0) out[i] = (double)w.x + (double)w.y;
+        }
+    }
+    if (tid == 0) *rb.counter = 0u;
+    __syncthreads();
+    return true;
+}
+// FP64 accumulators: the double tree above.
+template <int NV>
+__device__ bool grid_reduce(const Acc<double> (&v)[NV], const RedBuf& rb, double* out) {
+    double vals[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) vals[i] = v[i].value();
+    return grid_reduce<NV>(vals, rb, out);
+}
+
 // Row mapping of a grid kernel: threadIdx.x runs over x, the (y, z) rows
 // (row = y + n z) over blockIdx.x * blockDim.y + threadIdx.y with a grid
 // stride.  One 32-bit division per row, none per element.

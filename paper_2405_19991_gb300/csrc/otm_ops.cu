@@ -152,10 +152,10 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int zrtz = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::zr_tz(n, sms, oc.max_blocks) : 0;
-    if (zrtz > 0) {   // the kernel and launch shape the solver uses at this size
-        otm::k_stencil_zr<false, otm::FinNone><<<otm::zr_grid(n, zrtz), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
-            n, zrtz, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
+    const int zrm = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::zr_m_for<false, otm::FinNone>(n, sms, oc.max_blocks) : 0;
+    if (zrm > 0) {   // the kernel and launch shape the solver uses at this size
+        otm::k_stencil_zr<false, otm::FinNone><<<otm::zr_grid(n, zrm), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
+            n, zrm, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
         return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
     }
     const int x2tz = sizeof(R) == 4 && otm::stencil_choice() == 3 ? otm::x2_tz(n, sms, oc.max_blocks) : 0;

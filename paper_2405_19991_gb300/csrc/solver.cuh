@@ -280,7 +280,7 @@ class Solver : public SolverBase {
     }
     int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
     int x2tz_ = 0;   // z-planes per CTA of the paired-node fine stencil (FP32 fields), 0: not used
-    int zrtz_ = 0;   // z-planes per CTA of its z-reuse form, 0: not used
+    int zrm_ = 0;    // z-chunks per column of its z-reuse form, 0: not used
     // warp-row kernels on the finest grid (FP32 / mixed paths, 128 | n)
     bool wr_ = false;
     int wr_grid(long long warps) const {
@@ -334,7 +334,7 @@ class Solver : public SolverBase {
         OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
         max_blocks = sm_count * 8;
         tz_ = stencil_choice() != 2 ? tiled_tz(pin.n, sm_count, max_blocks) : 0;
-        if (std::is_same<R, float>::value && stencil_choice() == 0) zrtz_ = zr_tz(pin.n, sm_count, max_blocks);
+        if (std::is_same<R, float>::value && stencil_choice() == 0) zrm_ = zr_m_for<true, FinAlpha>(pin.n, sm_count, max_blocks);
         if (std::is_same<R, float>::value && stencil_choice() == 3) x2tz_ = x2_tz(pin.n, sm_count, max_blocks);
         wr_ = warprow_ok(pin.n) && std::is_same<R, float>::value;
         if (pin.stream) {
@@ -797,8 +797,8 @@ class Solver : public SolverBase {
         if (N % 4 == 0) launch_pdl(k_update_p4<R, S>, grid(N / 4), 256, stream, N, p, z, ps);
         else launch_pdl(k_update_p<R, S>, grid(N), 256, stream, N, p, z, ps);
         ++nl_;
-if (zrtz_ > 0)
-            launch_pdl(k_stencil_zr<true, FinAlpha>, zr_grid(n, zrtz_), dim3(kX2T, kX2Y), stream, n, zrtz_,
+if (zrm_ > 0)
+            launch_pdl(k_stencil_zr<true, FinAlpha>, zr_grid(n, zrm_), dim3(kX2T, kX2Y), stream, n, zrm_,
                        (const float*)kf, (const float*)p, (float*)q, rb, FinAlpha{ps});
         else if (x2tz_ > 0)
             launch_pdl(k_stencil_x2<true, FinAlpha>, x2_grid(n, x2tz_), dim3(kX2T, kX2Y), stream, n, x2tz_,

@@ -355,18 +355,19 @@ k_head_back(size_t N, int C, const bf16* __restrict__ d, const float* __restrict
 }
 
 // MSE loss against the target t * inv_scale (t [3][N]): dy = 2 (y - t') / M;
-// loss partials summed into *loss (FP64 atomics).
+// loss partials (compensated FP32 per thread and warp) added into *loss
+// with one FP64 atomic per warp.
 static __global__ void k_mse(size_t M, const float* __restrict__ y, const float* __restrict__ t, float inv_scale,
                              float* __restrict__ dy, double* __restrict__ loss) {
-    double s = 0.0;
+    Acc<float> s;
     const float sc = 2.0f / (float)M;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
         const float d = y[i] - t[i] * inv_scale;
-        s += (double)d * d;
+        s.add_prod(d, d);
         dy[i] = sc * d;
     }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (double)M);
+    acc_warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s.value() / (double)M);
 }
 
 // Adam update of the FP32 master parameters.

@@ -230,3 +230,59 @@ def test_apply_K_async_is_the_same_operator(n):
     otm.otm_op_apply_K_async(1, n, k_d, u_d, b, st.cuda_stream)
     st.synchronize()
     assert torch.equal(a, b)
+
+
+_FORM_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+import workloads as W
+n, out = int(sys.argv[2]), sys.argv[3]
+rho = W.random_density(n, 21)
+k = torch.as_tensor(1e-3 + rho ** 3 * (1 - 1e-3), dtype=torch.float32, device="cuda").contiguous()
+u = torch.as_tensor(W.random_field(n, 22).ravel(), dtype=torch.float32, device="cuda").contiguous()
+o = torch.empty(3 * n ** 3, dtype=torch.float32, device="cuda")
+otm.otm_op_apply_K(1, n, k, u, o)
+np.save(out, o.cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("n", [64, 128, 192])
+def test_stencil_forms_are_bitwise_equal(n, tmp_path):
+    """The four fine-stencil forms (z-reuse, three-plane paired, tiled, gather)
+    perform the same operations per node in the same order: same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    got = {}
+    for form in ("zr", "pair", "tiled", "gather"):
+        path = str(tmp_path / f"{form}.npy")
+        env = dict(os.environ, OTM_STENCIL=form)
+        subprocess.run([sys.executable, "-c", _FORM_SCRIPT, root, str(n), path], env=env, check=True,
+                       timeout=300)
+        got[form] = np.load(path)
+    for form in ("pair", "tiled", "gather"):
+        assert np.array_equal(got["zr"].view(np.uint32), got[form].view(np.uint32)), form
+
+
+@pytest.mark.parametrize("grid", [1, 7, 456, 1000])
+def test_stencil_zr_any_grid(grid, tmp_path):
+    """The z-reuse form's runs of (column, plane) units: any grid size (runs
+    crossing column boundaries, one CTA doing everything) gives the same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    paths = []
+    for g in (None, grid):
+        path = str(tmp_path / f"g{g}.npy")
+        env = dict(os.environ, OTM_STENCIL="zr")
+        if g is not None:
+            env["OTM_ZR_GRID"] = str(g)
+        subprocess.run([sys.executable, "-c", _FORM_SCRIPT, root, "128", path], env=env, check=True, timeout=300)
+        paths.append(path)
+    a, b = np.load(paths[0]), np.load(paths[1])
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
