@@ -17,7 +17,7 @@ namespace otm {
 
 constexpr int kClusterCTAs = 8;        // portable cluster size; 16 (non-portable) where the device allows
 constexpr int kClusterThreads = 512;
-constexpr int kClusterMaxN = 16;
+constexpr int kClusterMaxN = 8;
 
 template <class S, class C>
 struct ClusterArgs {

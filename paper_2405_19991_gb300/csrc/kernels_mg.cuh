@@ -11,82 +11,175 @@
 // the eight elements around v.  P_s[j][m] = prod_d phi(s_d + j_d, m_d) with
 // phi(t, 0) = {1, 1/2, 0}[t], phi(t, 1) = {0, 1/2, 1}[t].
 #pragma once
+#include <type_traits>
+
 #include "otm_internal.cuh"
 
 namespace otm {
 
-// ---- first coarse level: element matrices from the fine conductivities ----
+// Element matrices are stored element-major, Kel[E][64] (entry m * 8 + j),
+// so one element is 256 contiguous bytes.
+
+// The eight fine conductivities of first-level element (X, Y, Z) (children
+// s = sx + 2 sy + 4 sz of the fine grid of side 2 nc).
 template <class KT, class C>
-__global__ void __launch_bounds__(128)
-k_elem_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, C* __restrict__ Kel) {
-    pdl_enter();
+__device__ __forceinline__ void child_k(const KT* __restrict__ k, int nc, int X, int Y, int Z, C (&ks)[8]) {
     const int nf = 2 * nc;
-    const size_t Nc = (size_t)nc * nc * nc;
-    OTM_FOR_ROWS(row_, nc * nc) {
-    const int Y = row_ % nc, Z = row_ / nc;
-    OTM_FOR_X(X, nc) {
-        const size_t E = (size_t)row_ * nc + X;
-        C ks[8];
 #pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const int fx = 2 * X + (s & 1), fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
-            ks[s] = St<KT>::ld(k, (size_t)fx + (size_t)nf * (fy + (size_t)nf * fz));
+    for (int s = 0; s < 8; s += 2) {   // children s, s + 1 are x-neighbours (2X even: one aligned pair)
+        const int fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
+        const size_t o = (size_t)(2 * X) + (size_t)nf * (fy + (size_t)nf * fz);
+        if (std::is_same<KT, float>::value) {
+            const float2 w = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(k) + o);
+            ks[s] = (C)w.x;
+            ks[s + 1] = (C)w.y;
+        } else {
+            ks[s] = (C)St<KT>::ld(k, o);
+            ks[s + 1] = (C)St<KT>::ld(k, o + 1);
         }
-        for (int mm = 0; mm < 64; ++mm) {
-            C a = 0;
-#pragma unroll
-            for (int s = 0; s < 8; ++s) a += ks[s] * Bs[s * 64 + mm];
-            Kel[(size_t)mm * Nc + E] = a;
-        }
-    }
     }
 }
 
-// ---- deeper levels: K_E = sum_s P_s^T K_child P_s ----
+// Eight consecutive values of a shared-memory row (16-byte aligned).
 template <class C>
-__global__ void __launch_bounds__(64)
-k_elem_coarsen(int nc, const C* __restrict__ Kf, const C* __restrict__ Ps, C* __restrict__ Kc) {
+__device__ __forceinline__ void lds8(const C* p, C (&r)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) r[j] = p[j];
+}
+template <>
+__device__ __forceinline__ void lds8<float>(const float* p, float (&r)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+    r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+
+// ---- first coarse level: the node stencil straight from the fine
+// conductivities.  Entry (m, j) of the element matrix of E is
+// sum_s k_{child(E,s)} B_s[m][j] (s in order); the stencil of node v gathers,
+// for its corners m = 0..7 in the eight elements around it, entries j = 0..7
+// in order -- the operations of an element-matrix pass followed by a gather,
+// without storing the first level's element matrices.
+// One thread per node and no loop around it: the 512 weights stay in shared
+// memory instead of being hoisted into (spilled) registers.
+template <class KT, class C, class AT>
+__global__ void __launch_bounds__(128)
+k_stencil1_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, AT* __restrict__ A) {
     pdl_enter();
-    const int nf = 2 * nc;
-    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
-    OTM_FOR_ROWS(row_, nc * nc) {
-    const int Y = row_ % nc, Z = row_ / nc;
-    OTM_FOR_X(X, nc) {
-        const size_t E = (size_t)row_ * nc + X;
-        C out[64];
+    __shared__ __align__(16) C bs[8 * 64];
+    for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) bs[i] = Bs[i];
+    __syncthreads();
+    const size_t Nc = (size_t)nc * nc * nc;
+    const size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= Nc) return;
+    const int x = (int)(v % nc), y = (int)((v / nc) % nc), z = (int)(v / ((size_t)nc * nc));
+    C acc[27];
 #pragma unroll
-        for (int i = 0; i < 64; ++i) out[i] = 0;
-        for (int s = 0; s < 8; ++s) {
-            const int fx = 2 * X + (s & 1), fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
-            const size_t e = (size_t)fx + (size_t)nf * (fy + (size_t)nf * fz);
-            const C* P = Ps + s * 64;   // P[j*8 + m]
-            // T = K_child P  (8x8), then out += P^T T
-            for (int j = 0; j < 8; ++j) {
-                C kr[8];
+    for (int o = 0; o < 27; ++o) acc[o] = 0;
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) kr[jj] = Kf[(size_t)(j * 8 + jj) * Nf + e];
-                C t[8];
+    for (int m = 0; m < 8; ++m) {
+        const int a = m & 1, b = (m >> 1) & 1, c = m >> 2;
+        C ks[8];
+        child_k<KT, C>(k, nc, wrapd(x, -a, nc), wrapd(y, -b, nc), wrapd(z, -c, nc), ks);
+        C e[8];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    C a = 0;
+        for (int j = 0; j < 8; ++j) e[j] = 0;
 #pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) a += kr[jj] * P[jj * 8 + m];
-                    t[m] = a;
-                }
-                // row j of T contributes P[j][m'] * T[j][m] to out[m'][m]
+        for (int s = 0; s < 8; ++s) {   // e[j] = sum_s ks[s] B_s[m][j], s in order
+            C w[8];
+            lds8<C>(bs + s * 64 + m * 8, w);
 #pragma unroll
-                for (int mp = 0; mp < 8; ++mp) {
-                    const C pj = P[j * 8 + mp];
-                    if (pj != C(0)) {
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) out[mp * 8 + m] += pj * t[m];
-                    }
-                }
-            }
+            for (int j = 0; j < 8; ++j) e[j] += ks[s] * w[j];
         }
 #pragma unroll
-        for (int i = 0; i < 64; ++i) Kc[(size_t)i * Nc + E] = out[i];
+        for (int j = 0; j < 8; ++j) {
+            const int dx = (j & 1) - a, dy = ((j >> 1) & 1) - b, dz = (j >> 2) - c;
+            acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += e[j];
+        }
     }
+#pragma unroll
+    for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
+}
+
+// ---- deeper levels: K_E = sum_s P_s^T K_child P_s, one warp per coarse
+// element.  P_s factors into 1-D interpolations along x, y, z (P_s[j][m] =
+// prod_d phi(s_d + j_d, m_d)), so both products are three 1-D passes: along
+// index bit d with child position s_d, the entry with bit value b becomes
+// own + partner / 2 when b == s_d and own / 2 otherwise (partner: the entry
+// with bit d flipped).  Lane l holds entries (r, c) = (l / 8, l % 8) and
+// (l / 8 + 4, l % 8): column passes exchange with lanes l ^ 1, l ^ 2, l ^ 4,
+// row passes with l ^ 8, l ^ 16 and between the lane's two entries.
+// FROM_K: the children are first-level elements, their matrices
+// sum_s' k B_s' formed on the fly from the fine conductivities k (Kf unused).
+template <class C>
+__device__ __forceinline__ C interp_pass(C own, C partner, bool up) {
+    return up ? own + C(0.5) * partner : C(0.5) * own;
+}
+template <class C, bool FROM_K, class KT>
+__global__ void __launch_bounds__(256)
+k_elem_coarsen(int nc, const C* __restrict__ Kf, const KT* __restrict__ k, const C* __restrict__ Ps,
+               const C* __restrict__ Bs, C* __restrict__ Kc) {
+    pdl_enter();
+    __shared__ C bs[FROM_K ? 8 * 64 : 1];
+    if (FROM_K) {
+        for (int i = threadIdx.x; i < 8 * 64; i += blockDim.x) bs[i] = Bs[i];
+        __syncthreads();
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int nf = 2 * nc;
+    const size_t Nc = (size_t)nc * nc * nc;
+    const int cb = lane & 7, rb = lane >> 3;   // column bits; row bits 0, 1 (row bit 2: which entry)
+    for (size_t E = (size_t)blockIdx.x * nwarps + warp; E < Nc; E += (size_t)gridDim.x * nwarps) {
+        const int X = (int)(E % nc), Y = (int)((E / nc) % nc), Z = (int)(E / ((size_t)nc * nc));
+        C out0 = 0, out1 = 0;
+#pragma unroll 1
+        for (int s = 0; s < 8; ++s) {
+            const int fx = 2 * X + (s & 1), fy = 2 * Y + ((s >> 1) & 1), fz = 2 * Z + (s >> 2);
+            C v0, v1;   // entries (rb, cb) and (rb + 4, cb) of the child's matrix
+            if (FROM_K) {
+                C ks[8];
+                child_k<KT, C>(k, nf, fx, fy, fz, ks);
+                v0 = 0;
+                v1 = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    v0 += ks[q] * bs[q * 64 + lane];
+                    v1 += ks[q] * bs[q * 64 + 32 + lane];
+                }
+            } else {
+                const size_t e = (size_t)fx + (size_t)nf * (fy + (size_t)nf * fz);
+                v0 = Kf[e * 64 + lane];
+                v1 = Kf[e * 64 + 32 + lane];
+            }
+            // K P_s: passes over the column bits
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const bool up = ((cb >> d) & 1) == ((s >> d) & 1);
+                const C p0 = __shfl_xor_sync(0xffffffffu, v0, 1 << d);
+                const C p1 = __shfl_xor_sync(0xffffffffu, v1, 1 << d);
+                v0 = interp_pass(v0, p0, up);
+                v1 = interp_pass(v1, p1, up);
+            }
+            // P_s^T (K P_s): passes over the row bits
+#pragma unroll
+            for (int d = 0; d < 2; ++d) {
+                const bool up = ((rb >> d) & 1) == ((s >> d) & 1);
+                const C p0 = __shfl_xor_sync(0xffffffffu, v0, 8 << d);
+                const C p1 = __shfl_xor_sync(0xffffffffu, v1, 8 << d);
+                v0 = interp_pass(v0, p0, up);
+                v1 = interp_pass(v1, p1, up);
+            }
+            {
+                const int sz = (s >> 2) & 1;
+                const C a0 = interp_pass(v0, v1, sz == 0), a1 = interp_pass(v1, v0, sz == 1);
+                v0 = a0;
+                v1 = a1;
+            }
+            out0 += v0;
+            out1 += v1;
+        }
+        Kc[E * 64 + lane] = out0;
+        Kc[E * 64 + 32 + lane] = out1;
     }
 }
 
@@ -95,7 +188,6 @@ template <class C, class AT>
 __global__ void __launch_bounds__(128)
 k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
     pdl_enter();
-    const size_t N = (size_t)n * n * n;
     OTM_FOR_ROWS(row_, n * n) {
     const int y = row_ % n, z = row_ / n;
     OTM_FOR_X(x, n) {
@@ -107,10 +199,11 @@ k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
         for (int m = 0; m < 8; ++m) {
             const int a = m & 1, b = (m >> 1) & 1, c = m >> 2;
             const size_t E = (size_t)wrapd(x, -a, n) + (size_t)n * (wrapd(y, -b, n) + (size_t)n * wrapd(z, -c, n));
+            const C* row = Kel + E * 64 + m * 8;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int dx = (j & 1) - a, dy = ((j >> 1) & 1) - b, dz = (j >> 2) - c;
-                acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += Kel[(size_t)(m * 8 + j) * N + E];
+                acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += row[j];
             }
         }
 #pragma unroll
@@ -358,22 +451,31 @@ k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, co
 // ---- coarsest level: dense inverse of the node-0-pinned operator ----
 // One CTA.  The dense matrix of the stencil without node 0's row and column
 // is inverted in place by Gauss-Jordan elimination (no pivoting: the pinned
-// matrix is SPD) in the compute type C, in shared memory when it fits, and
-// the result is symmetrised ((M + M^T) / 2) so the coarse correction, and
-// with it the V-cycle, stays a symmetric operator.
-template <class AT, class C>
+// matrix is SPD) in the compute type C, and the result is symmetrised
+// ((M + M^T) / 2) so the coarse correction, and with it the V-cycle, stays a
+// symmetric operator.  Every thread owns the entries t, t + blockDim, ... of
+// the (q x q) working matrix (shared memory when it fits, else Wg); the
+// pivot row and column of each step are published in a double-buffered
+// snapshot by their owners during the previous step, so a step is one
+// barrier: with p = W[k][k] and ip = 1 / p, row k becomes W[k][j] ip (ip on
+// the diagonal) and row i != k becomes W[i][j] - W[i][k] (W[k][j] ip)
+// (-W[i][k] ip in column k).
+template <class AT, class C, bool REG>
 __global__ void __launch_bounds__(1024)
 k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restrict__ Minv, int use_smem) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char inv_sm[];
+    constexpr int kReg = 4;                                   // entries per thread held in registers
     const int m = n * n * n;
     const int q = m - 1;
-    C* W = use_smem ? reinterpret_cast<C*>(inv_sm) : Wg;     // the (m-1)^2 working matrix
-    __shared__ C col[343];
-    __shared__ C ipiv;
-    for (size_t i = threadIdx.x; i < (size_t)q * q; i += blockDim.x) W[i] = C(0);
+    const int qq = q * q;
+    C* snap = reinterpret_cast<C*>(inv_sm);                  // [2][2][q]: rows, columns
+    C* W = use_smem ? snap + 4 * q : Wg;                       // the (m-1)^2 working matrix
+    const int nthr = blockDim.x;
+    const bool reg = REG && use_smem && qq <= kReg * nthr;     // uniform
+    for (int i = threadIdx.x; i < qq; i += nthr) W[i] = C(0);
     __syncthreads();
-    for (int v = 1 + threadIdx.x; v < m; v += blockDim.x) {
+    for (int v = 1 + threadIdx.x; v < m; v += nthr) {
         const int x = v % n, y = (v / n) % n, z = v / (n * n);
         for (int o = 0; o < 27; ++o) {
             const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
@@ -382,32 +484,72 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
         }
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int kp = 0; kp < q; ++kp) {
-        if (threadIdx.x == 0) ipiv = C(1) / W[(size_t)kp * q + kp];
-        __syncthreads();
-        const C ip = ipiv;
-        for (int j = threadIdx.x; j < q; j += blockDim.x) {
-            if (j == kp) W[(size_t)kp * q + j] = ip;
-            else W[(size_t)kp * q + j] *= ip;
-        }
-        for (int i = threadIdx.x; i < q; i += blockDim.x) col[i] = W[(size_t)i * q + kp];
-        __syncthreads();
-        // warps over rows, lanes over columns
-        for (int i = threadIdx.x >> 5; i < q; i += nw) {
-            if (i == kp) continue;
-            const C ci = col[i];
-            C* Wi = W + (size_t)i * q;
-            const C* Wk = W + (size_t)kp * q;
-            for (int j = lane; j < q; j += 32) {
-                if (j == kp) Wi[j] = -ci * ip;
-                else Wi[j] -= ci * Wk[j];
-            }
-        }
-        __syncthreads();
+    // snapshot of row and column 0
+    for (int j = threadIdx.x; j < q; j += nthr) {
+        snap[j] = W[j];
+        snap[2 * q + j] = W[(size_t)j * q];
     }
-    for (size_t t = threadIdx.x; t < (size_t)q * q; t += blockDim.x) {
-        const int i = (int)(t / q), j = (int)(t % q);
+    // one Gauss-Jordan step on entry (i, j) holding w
+    // (selects instead of branches: 1 ip = ip and 0 - ci ip = -ci ip exactly)
+    auto step = [&](int kp, const C* prow, const C* pcol, C ip, int i, int j, C w) -> C {
+        const bool jk = j == kp;
+        if (i == kp) return (jk ? C(1) : w) * ip;
+        const C wk = (jk ? C(1) : prow[j]) * ip;
+        return (jk ? C(0) : w) - pcol[i] * wk;
+    };
+    if (REG && reg) {
+        C wr[kReg];
+        int ij[kReg];   // i * 1024 + j (q < 1024 here), -1 past the end
+#pragma unroll
+        for (int r = 0; r < kReg; ++r) {
+            const int t = threadIdx.x + r * nthr;
+            ij[r] = t < qq ? (t / q) * 1024 + t % q : -1;
+            wr[r] = t < qq ? W[t] : C(0);
+        }
+        __syncthreads();
+        for (int kp = 0; kp < q; ++kp) {
+            const int b = kp & 1;
+            const C* prow = snap + b * q;
+            const C* pcol = snap + 2 * q + b * q;
+            C* nrow = snap + (b ^ 1) * q;
+            C* ncol = snap + 2 * q + (b ^ 1) * q;
+            const C ip = C(1) / prow[kp];
+#pragma unroll
+            for (int r = 0; r < kReg; ++r) {
+                if (ij[r] < 0) continue;
+                const int i = ij[r] >> 10, j = ij[r] & 1023;
+                const C w = step(kp, prow, pcol, ip, i, j, wr[r]);
+                wr[r] = w;
+                if (i == kp + 1) nrow[j] = w;
+                if (j == kp + 1) ncol[i] = w;
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int r = 0; r < kReg; ++r)
+            if (ij[r] >= 0) W[threadIdx.x + r * nthr] = wr[r];
+    } else {
+        __syncthreads();
+        for (int kp = 0; kp < q; ++kp) {
+            const int b = kp & 1;
+            const C* prow = snap + b * q;
+            const C* pcol = snap + 2 * q + b * q;
+            C* nrow = snap + (b ^ 1) * q;
+            C* ncol = snap + 2 * q + (b ^ 1) * q;
+            const C ip = C(1) / prow[kp];
+            for (int t = threadIdx.x; t < qq; t += nthr) {
+                const int i = t / q, j = t - i * q;
+                const C w = step(kp, prow, pcol, ip, i, j, W[t]);
+                W[t] = w;
+                if (i == kp + 1) nrow[j] = w;
+                if (j == kp + 1) ncol[i] = w;
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < qq; t += nthr) {
+        const int i = t / q, j = t - i * q;
         Minv[t] = C(0.5) * (W[t] + W[(size_t)j * q + i]);
     }
 }

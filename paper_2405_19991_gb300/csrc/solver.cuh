@@ -281,6 +281,8 @@ class Solver : public SolverBase {
     int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
     int x2tz_ = 0;   // z-planes per CTA of the paired-node fine stencil (FP32 fields), 0: not used
     int zrm_ = 0;    // z-chunks per column of its z-reuse form, 0: not used
+    size_t inv_smem_ = 0;    // dynamic shared memory of the coarsest inverse
+    int inv_use_smem_ = 0;   // its working matrix in shared memory
     // warp-row kernels on the finest grid (FP32 / mixed paths, 128 | n)
     bool wr_ = false;
     int wr_grid(long long warps) const {
@@ -314,6 +316,20 @@ class Solver : public SolverBase {
         const int d = device >= 0 && device < 64 ? device : 0;
         if (bytes <= granted[d]) return OTM_OK;
         OTM_CU(cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        granted[d] = bytes;
+        return OTM_OK;
+    }
+
+    otm_status raise_invert_smem(size_t bytes) {
+        static std::mutex m;
+        static size_t granted[64] = {};
+        std::lock_guard<std::mutex> lock(m);
+        const int d = device >= 0 && device < 64 ? device : 0;
+        if (bytes <= granted[d]) return OTM_OK;
+        OTM_CU(cudaFuncSetAttribute(k_coarse_invert<S, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes));
+        OTM_CU(cudaFuncSetAttribute(k_coarse_invert<S, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bytes));
         granted[d] = bytes;
         return OTM_OK;
     }
@@ -384,12 +400,25 @@ class Solver : public SolverBase {
                 OTM_TRY(alloc(Dl[l], 4 * Nl[l]));
             }
             OTM_TRY(alloc(Al[l], (size_t)CL<S>::AW * Nl[l]));
-            OTM_TRY(alloc(Kel[l], 64 * Nl[l]));
+            if (l >= 2) OTM_TRY(alloc(Kel[l], 64 * Nl[l]));   // element-major [N_l][64]; level 1 is never stored
         }
         if (nlev == 1) OTM_TRY(alloc(Al[0], (size_t)CL<S>::AW * Nl[0]));
         const size_t m = Nl[nlev - 1];
         OTM_TRY(alloc(Wd, (m - 1) * (m - 1)));
         OTM_TRY(alloc(Minv, (m - 1) * (m - 1)));
+        {
+            // the coarsest inverse keeps its working matrix in shared memory
+            // when that fits the device's opt-in limit
+            const size_t qd = m - 1;
+            int optin = 0;
+            OTM_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+            cudaFuncAttributes fa;
+            OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_invert<S, C, false>));
+            const size_t snapb = 4 * qd * sizeof(C), full = snapb + qd * qd * sizeof(C);
+            inv_use_smem_ = fa.sharedSizeBytes + full <= (size_t)optin ? 1 : 0;
+            inv_smem_ = inv_use_smem_ ? full : snapb;
+            OTM_TRY(raise_invert_smem(inv_smem_));
+        }
         std::vector<double> Ps, Bs;
         build_ps(Ps, Bs);
         std::vector<C> Psc(Ps.begin(), Ps.end()), Bsc(Bs.begin(), Bs.end());
@@ -586,14 +615,18 @@ class Solver : public SolverBase {
             OTM_LAUNCH();
         } else {
             ++nl_;
-            launch_pdl(k_elem_from_k<R, C>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1], 128)), stream, sz[1], kf, Bs_d, Kel[1]);
-            OTM_LAUNCH();
-            ++nl_;
-            launch_pdl(k_stencil_from_elem<C, S>, OTM_ROWS_CFG(rl(sz[1], sz[1] * sz[1], 128)), stream, sz[1], Kel[1], Al[1]);
+            launch_pdl(k_stencil1_from_k<R, C, S>, (int)((Nl[1] + 127) / 128), 128, stream, sz[1], kf, Bs_d, Al[1]);
             OTM_LAUNCH();
             for (int l = 1; l + 1 < nlev; ++l) {
                 ++nl_;
-                launch_pdl(k_elem_coarsen<C>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1], 64)), stream, sz[l + 1], Kel[l], Ps_d, Kel[l + 1]);
+                const long long warps = (long long)Nl[l + 1];
+                const int cg = (int)std::min<long long>((warps + 7) / 8, (long long)sm_count * 16);
+                if (l == 1)
+                    launch_pdl(k_elem_coarsen<C, true, R>, cg, 256, stream, sz[l + 1], (const C*)nullptr, kf, Ps_d,
+                               Bs_d, Kel[l + 1]);
+                else
+                    launch_pdl(k_elem_coarsen<C, false, R>, cg, 256, stream, sz[l + 1], (const C*)Kel[l], kf, Ps_d,
+                               Bs_d, Kel[l + 1]);
                 OTM_LAUNCH();
                 ++nl_;
                 launch_pdl(k_stencil_from_elem<C, S>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1], 128)), stream, sz[l + 1], Kel[l + 1], Al[l + 1]);
@@ -611,11 +644,15 @@ class Solver : public SolverBase {
         }
         ++nl_;
         {
-            const size_t q = Nl[L] - 1;
-            const size_t wbytes = q * q * sizeof(C);
-            const int use_smem = wbytes <= 48 * 1024 ? 1 : 0;
-            launch_pdl_smem(k_coarse_invert<S, C>, 1, 1024, use_smem ? wbytes : 0, stream, sz[L], Al[L], (C*)Wd, Minv,
-                            use_smem);
+            // 1024 threads hold a matrix of up to 4096 entries in registers
+            // (4 each); larger ones stay in shared (or global) memory
+            const size_t qd = Nl[L] - 1;
+            if (inv_use_smem_ && qd * qd <= 4 * 1024)
+                launch_pdl_smem(k_coarse_invert<S, C, true>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd, Minv,
+                                inv_use_smem_);
+            else
+                launch_pdl_smem(k_coarse_invert<S, C, false>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd,
+                                Minv, inv_use_smem_);
         }
         OTM_LAUNCH();
         return OTM_OK;
