@@ -17,7 +17,7 @@ namespace otm {
 
 constexpr int kClusterCTAs = 8;        // portable cluster size; 16 (non-portable) where the device allows
 constexpr int kClusterThreads = 512;
-constexpr int kClusterMaxN = 8;
+constexpr int kClusterMaxN = 16;
 
 template <class S, class C>
 struct ClusterArgs {
@@ -156,7 +156,9 @@ __global__ void __launch_bounds__(kClusterThreads)
 k_coarse_cluster(ClusterArgs<S, C> a) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char cl_sm[];
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+    // node index t runs over the CTAs fastest, so a small pass spreads over
+    // every SM of the cluster instead of filling CTA 0 first
+    const int t0 = threadIdx.x * gridDim.x + blockIdx.x;
     const int ts = gridDim.x * blockDim.x;
     const int lend = a.lb <= a.L ? a.lb : a.L;   // first level not swept by the whole cluster
     static_assert(kChebDeg % 2 == 1, "the Chebyshev buffers alternate: an odd degree ends in T2");

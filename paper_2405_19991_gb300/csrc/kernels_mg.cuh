@@ -453,26 +453,27 @@ k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, co
 // is inverted in place by Gauss-Jordan elimination (no pivoting: the pinned
 // matrix is SPD) in the compute type C, and the result is symmetrised
 // ((M + M^T) / 2) so the coarse correction, and with it the V-cycle, stays a
-// symmetric operator.  Every thread owns the entries t, t + blockDim, ... of
-// the (q x q) working matrix (shared memory when it fits, else Wg); the
-// pivot row and column of each step are published in a double-buffered
-// snapshot by their owners during the previous step, so a step is one
-// barrier: with p = W[k][k] and ip = 1 / p, row k becomes W[k][j] ip (ip on
+// symmetric operator.  Warp w owns rows w, w + warps, ... and lane l columns
+// l, l + 32, ... of the (q x q) working matrix (shared memory when it fits,
+// else Wg).  The pivot row and column of each step are published in a
+// double-buffered snapshot by their owners during the previous step, so a
+// step is one barrier: with ip = 1 / W[k][k], row k becomes W[k][j] ip (ip on
 // the diagonal) and row i != k becomes W[i][j] - W[i][k] (W[k][j] ip)
-// (-W[i][k] ip in column k).
-template <class AT, class C, bool REG>
+// (-W[i][k] ip in column k); each lane forms its columns' W[k][j] ip once
+// per step.
+template <class AT, class C>
 __global__ void __launch_bounds__(1024)
 k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restrict__ Minv, int use_smem) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char inv_sm[];
-    constexpr int kReg = 4;                                   // entries per thread held in registers
+    constexpr int kCols = 8;                                  // columns per lane kept in registers
     const int m = n * n * n;
     const int q = m - 1;
     const int qq = q * q;
     C* snap = reinterpret_cast<C*>(inv_sm);                  // [2][2][q]: rows, columns
     C* W = use_smem ? snap + 4 * q : Wg;                       // the (m-1)^2 working matrix
     const int nthr = blockDim.x;
-    const bool reg = REG && use_smem && qq <= kReg * nthr;     // uniform
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nthr >> 5;
     for (int i = threadIdx.x; i < qq; i += nthr) W[i] = C(0);
     __syncthreads();
     for (int v = 1 + threadIdx.x; v < m; v += nthr) {
@@ -489,65 +490,52 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
         snap[j] = W[j];
         snap[2 * q + j] = W[(size_t)j * q];
     }
-    // one Gauss-Jordan step on entry (i, j) holding w
-    // (selects instead of branches: 1 ip = ip and 0 - ci ip = -ci ip exactly)
-    auto step = [&](int kp, const C* prow, const C* pcol, C ip, int i, int j, C w) -> C {
-        const bool jk = j == kp;
-        if (i == kp) return (jk ? C(1) : w) * ip;
-        const C wk = (jk ? C(1) : prow[j]) * ip;
-        return (jk ? C(0) : w) - pcol[i] * wk;
-    };
-    if (REG && reg) {
-        C wr[kReg];
-        int ij[kReg];   // i * 1024 + j (q < 1024 here), -1 past the end
-#pragma unroll
-        for (int r = 0; r < kReg; ++r) {
-            const int t = threadIdx.x + r * nthr;
-            ij[r] = t < qq ? (t / q) * 1024 + t % q : -1;
-            wr[r] = t < qq ? W[t] : C(0);
-        }
-        __syncthreads();
-        for (int kp = 0; kp < q; ++kp) {
-            const int b = kp & 1;
-            const C* prow = snap + b * q;
-            const C* pcol = snap + 2 * q + b * q;
-            C* nrow = snap + (b ^ 1) * q;
-            C* ncol = snap + 2 * q + (b ^ 1) * q;
-            const C ip = C(1) / prow[kp];
-#pragma unroll
-            for (int r = 0; r < kReg; ++r) {
-                if (ij[r] < 0) continue;
-                const int i = ij[r] >> 10, j = ij[r] & 1023;
-                const C w = step(kp, prow, pcol, ip, i, j, wr[r]);
-                wr[r] = w;
-                if (i == kp + 1) nrow[j] = w;
-                if (j == kp + 1) ncol[i] = w;
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int r = 0; r < kReg; ++r)
-            if (ij[r] >= 0) W[threadIdx.x + r * nthr] = wr[r];
-    } else {
-        __syncthreads();
-        for (int kp = 0; kp < q; ++kp) {
-            const int b = kp & 1;
-            const C* prow = snap + b * q;
-            const C* pcol = snap + 2 * q + b * q;
-            C* nrow = snap + (b ^ 1) * q;
-            C* ncol = snap + 2 * q + (b ^ 1) * q;
-            const C ip = C(1) / prow[kp];
-            for (int t = threadIdx.x; t < qq; t += nthr) {
-                const int i = t / q, j = t - i * q;
-                const C w = step(kp, prow, pcol, ip, i, j, W[t]);
-                W[t] = w;
-                if (i == kp + 1) nrow[j] = w;
-                if (j == kp + 1) ncol[i] = w;
-            }
-            __syncthreads();
-        }
-    }
     __syncthreads();
+    for (int kp = 0; kp < q; ++kp) {
+        const int b = kp & 1;
+        const C* prow = snap + b * q;            // row kp (before this step)
+        const C* pcol = snap + 2 * q + b * q;    // column kp (before this step)
+        C* nrow = snap + (b ^ 1) * q;            // row kp + 1 (after this step)
+        C* ncol = snap + 2 * q + (b ^ 1) * q;    // column kp + 1 (after this step)
+        const C ip = C(1) / prow[kp];
+        // W[k][j] ip of this lane's columns (1 ip = ip exactly in column k)
+        C wk[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) {
+            const int j = lane + 32 * c;
+            wk[c] = j < q ? (j == kp ? C(1) : prow[j]) * ip : C(0);
+        }
+        for (int i = warp; i < q; i += nw) {
+            C* Wi = W + (size_t)i * q;
+            if (i == kp) {
+                for (int j = lane; j < q; j += 32) {
+                    const C w = (j == kp ? C(1) : Wi[j]) * ip;
+                    Wi[j] = w;
+                    if (j == kp + 1) ncol[i] = w;
+                }
+                continue;
+            }
+            const C ci = pcol[i];
+            const bool rn = i == kp + 1;
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+                const int j = lane + 32 * c;
+                if (j >= q) break;
+                const C w = (j == kp ? C(0) : Wi[j]) - ci * wk[c];   // 0 - ci ip = -ci ip exactly
+                Wi[j] = w;
+                if (rn) nrow[j] = w;
+                if (j == kp + 1) ncol[i] = w;
+            }
+            for (int j = lane + 32 * kCols; j < q; j += 32) {
+                const C wkj = (j == kp ? C(1) : prow[j]) * ip;
+                const C w = (j == kp ? C(0) : Wi[j]) - ci * wkj;
+                Wi[j] = w;
+                if (rn) nrow[j] = w;
+                if (j == kp + 1) ncol[i] = w;
+            }
+        }
+        __syncthreads();
+    }
     for (int t = threadIdx.x; t < qq; t += nthr) {
         const int i = t / q, j = t - i * q;
         Minv[t] = C(0.5) * (W[t] + W[(size_t)j * q + i]);

@@ -326,9 +326,7 @@ class Solver : public SolverBase {
         std::lock_guard<std::mutex> lock(m);
         const int d = device >= 0 && device < 64 ? device : 0;
         if (bytes <= granted[d]) return OTM_OK;
-        OTM_CU(cudaFuncSetAttribute(k_coarse_invert<S, C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)bytes));
-        OTM_CU(cudaFuncSetAttribute(k_coarse_invert<S, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        OTM_CU(cudaFuncSetAttribute(k_coarse_invert<S, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)bytes));
         granted[d] = bytes;
         return OTM_OK;
@@ -413,7 +411,7 @@ class Solver : public SolverBase {
             int optin = 0;
             OTM_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
             cudaFuncAttributes fa;
-            OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_invert<S, C, false>));
+            OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_invert<S, C>));
             const size_t snapb = 4 * qd * sizeof(C), full = snapb + qd * qd * sizeof(C);
             inv_use_smem_ = fa.sharedSizeBytes + full <= (size_t)optin ? 1 : 0;
             inv_smem_ = inv_use_smem_ ? full : snapb;
@@ -644,15 +642,8 @@ class Solver : public SolverBase {
         }
         ++nl_;
         {
-            // 1024 threads hold a matrix of up to 4096 entries in registers
-            // (4 each); larger ones stay in shared (or global) memory
-            const size_t qd = Nl[L] - 1;
-            if (inv_use_smem_ && qd * qd <= 4 * 1024)
-                launch_pdl_smem(k_coarse_invert<S, C, true>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd, Minv,
-                                inv_use_smem_);
-            else
-                launch_pdl_smem(k_coarse_invert<S, C, false>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd,
-                                Minv, inv_use_smem_);
+            launch_pdl_smem(k_coarse_invert<S, C>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd, Minv,
+                            inv_use_smem_);
         }
         OTM_LAUNCH();
         return OTM_OK;
