@@ -450,33 +450,45 @@ k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, co
 
 // ---- coarsest level: dense inverse of the node-0-pinned operator ----
 // One CTA.  The dense matrix of the stencil without node 0's row and column
-// is inverted in place by Gauss-Jordan elimination (no pivoting: the pinned
-// matrix is SPD) in the compute type C, and the result is symmetrised
+// is inverted in place by Gauss-Jordan elimination without pivoting (the
+// pinned matrix is SPD, so every pivot -- a Schur-complement diagonal -- is
+// positive), in the compute type C, and the result is symmetrised
 // ((M + M^T) / 2) so the coarse correction, and with it the V-cycle, stays a
-// symmetric operator.  Warp w owns rows w, w + warps, ... and lane l columns
-// l, l + 32, ... of the (q x q) working matrix (shared memory when it fits,
-// else Wg).  The pivot row and column of each step are published in a
-// double-buffered snapshot by their owners during the previous step, so a
-// step is one barrier: with ip = 1 / W[k][k], row k becomes W[k][j] ip (ip on
-// the diagonal) and row i != k becomes W[i][j] - W[i][k] (W[k][j] ip)
-// (-W[i][k] ip in column k); each lane forms its columns' W[k][j] ip once
-// per step.
+// symmetric operator.  The pivots are taken kInvB at a time: sweeping the
+// pivot block K of the current matrix W (D = W[K][K]) is
+//   W[K][K] <- D^-1,            W[K][j] <- D^-1 W[K][j],
+//   W[i][K] <- -W[i][K] D^-1,   W[i][j] <- W[i][j] - W[i][K] D^-1 W[K][j]
+// for i, j outside K -- the same as kInvB single-pivot steps, with the bulk
+// as a rank-kInvB update that each thread applies to its entries in
+// registers (warp w: rows w, w + warps, ...; lane l: columns l, l + 32, ...).
+// D^-1 itself comes from single-pivot steps by one warp.  W lives in shared
+// memory when it fits the opt-in limit, else in Wg.
+constexpr int kInvB = 8;
+constexpr int kInvThreads = 512;
+inline size_t invert_smem_bytes(int q, int elem, bool with_w) {
+    return (size_t)elem * ((size_t)kInvB * kInvB + 3 * (size_t)kInvB * q + (with_w ? (size_t)q * q : 0));
+}
 template <class AT, class C>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(kInvThreads)
 k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restrict__ Minv, int use_smem) {
     pdl_enter();
     extern __shared__ __align__(16) unsigned char inv_sm[];
-    constexpr int kCols = 8;                                  // columns per lane kept in registers
+    constexpr int B = kInvB;
+    constexpr int kCols = 8;                   // columns per lane held in registers (q <= 256)
     const int m = n * n * n;
     const int q = m - 1;
     const int qq = q * q;
-    C* snap = reinterpret_cast<C*>(inv_sm);                  // [2][2][q]: rows, columns
-    C* W = use_smem ? snap + 4 * q : Wg;                       // the (m-1)^2 working matrix
-    const int nthr = blockDim.x;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nthr >> 5;
-    for (int i = threadIdx.x; i < qq; i += nthr) W[i] = C(0);
+    C* Dp = reinterpret_cast<C*>(inv_sm);      // [B][B]: D, then D^-1
+    C* Prow = Dp + B * B;                      // [B][q]: panel rows, then D^-1 W[K][j]
+    C* Pcol = Prow + (size_t)B * q;            // [q][B]: panel columns
+    C* Cn = Pcol + (size_t)q * B;              // [q][B]: -W[i][K] D^-1
+    C* W = use_smem ? Cn + (size_t)q * B : Wg;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+    for (int i = tid; i < qq; i += nthr) W[i] = C(0);
+    for (int i = tid; i < B * B; i += nthr) Dp[i] = C(0);   // entries past a short last panel stay finite
     __syncthreads();
-    for (int v = 1 + threadIdx.x; v < m; v += nthr) {
+    for (int v = 1 + tid; v < m; v += nthr) {
         const int x = v % n, y = (v / n) % n, z = v / (n * n);
         for (int o = 0; o < 27; ++o) {
             const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
@@ -485,58 +497,126 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
         }
     }
     __syncthreads();
-    // snapshot of row and column 0
-    for (int j = threadIdx.x; j < q; j += nthr) {
-        snap[j] = W[j];
-        snap[2 * q + j] = W[(size_t)j * q];
-    }
-    __syncthreads();
-    for (int kp = 0; kp < q; ++kp) {
-        const int b = kp & 1;
-        const C* prow = snap + b * q;            // row kp (before this step)
-        const C* pcol = snap + 2 * q + b * q;    // column kp (before this step)
-        C* nrow = snap + (b ^ 1) * q;            // row kp + 1 (after this step)
-        C* ncol = snap + 2 * q + (b ^ 1) * q;    // column kp + 1 (after this step)
-        const C ip = C(1) / prow[kp];
-        // W[k][j] ip of this lane's columns (1 ip = ip exactly in column k)
-        C wk[kCols];
-#pragma unroll
-        for (int c = 0; c < kCols; ++c) {
-            const int j = lane + 32 * c;
-            wk[c] = j < q ? (j == kp ? C(1) : prow[j]) * ip : C(0);
+    for (int k0 = 0; k0 < q; k0 += B) {
+        const int b = min(B, q - k0);
+        auto inK = [&](int i) { return (unsigned)(i - k0) < (unsigned)b; };
+        // 1. panel rows and columns (before this sweep), and D
+        for (int t = tid; t < b * q; t += nthr) {
+            const int c = t / q, j = t - c * q;
+            Prow[c * q + j] = W[(size_t)(k0 + c) * q + j];
         }
-        for (int i = warp; i < q; i += nw) {
-            C* Wi = W + (size_t)i * q;
-            if (i == kp) {
-                for (int j = lane; j < q; j += 32) {
-                    const C w = (j == kp ? C(1) : Wi[j]) * ip;
-                    Wi[j] = w;
-                    if (j == kp + 1) ncol[i] = w;
-                }
-                continue;
-            }
-            const C ci = pcol[i];
-            const bool rn = i == kp + 1;
+        for (int t = tid; t < q * b; t += nthr) {
+            const int i = t / b, c = t - i * b;
+            Pcol[i * B + c] = W[(size_t)i * q + k0 + c];
+        }
+        for (int t = tid; t < b * b; t += nthr) {
+            const int r = t / b, c = t - r * b;
+            Dp[r * B + c] = W[(size_t)(k0 + r) * q + k0 + c];
+        }
+        __syncthreads();
+        // D^-1 by single-pivot steps (one warp, two entries per lane)
+        if (warp == 0) {
+            for (int p = 0; p < b; ++p) {
+                const C ip = C(1) / Dp[p * B + p];
+                C nv[2];
 #pragma unroll
-            for (int c = 0; c < kCols; ++c) {
-                const int j = lane + 32 * c;
-                if (j >= q) break;
-                const C w = (j == kp ? C(0) : Wi[j]) - ci * wk[c];   // 0 - ci ip = -ci ip exactly
-                Wi[j] = w;
-                if (rn) nrow[j] = w;
-                if (j == kp + 1) ncol[i] = w;
-            }
-            for (int j = lane + 32 * kCols; j < q; j += 32) {
-                const C wkj = (j == kp ? C(1) : prow[j]) * ip;
-                const C w = (j == kp ? C(0) : Wi[j]) - ci * wkj;
-                Wi[j] = w;
-                if (rn) nrow[j] = w;
-                if (j == kp + 1) ncol[i] = w;
+                for (int h = 0; h < 2; ++h) {
+                    const int e = lane + 32 * h, r = e / B, c = e % B;
+                    nv[h] = C(0);
+                    if (r < b && c < b) {
+                        const C w = Dp[r * B + c];
+                        if (r == p) {
+                            nv[h] = (c == p ? C(1) : w) * ip;
+                        } else {
+                            const C wk = (c == p ? C(1) : Dp[p * B + c]) * ip;
+                            nv[h] = (c == p ? C(0) : w) - Dp[r * B + p] * wk;
+                        }
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int e = lane + 32 * h, r = e / B, c = e % B;
+                    if (r < b && c < b) Dp[r * B + c] = nv[h];
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
+        // 2. R = D^-1 W[K][j] (in place, zero inside K) and Cn = -W[i][K] D^-1
+        for (int j = tid; j < q; j += nthr) {
+            C xr[B];
+#pragma unroll
+            for (int d = 0; d < B; ++d) xr[d] = d < b ? Prow[d * q + j] : C(0);
+            const bool k_col = inK(j);
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                if (c >= b) break;
+                C r = 0;
+#pragma unroll
+                for (int d = 0; d < B; ++d) r += Dp[c * B + d] * xr[d];
+                Prow[c * q + j] = k_col ? C(0) : r;
+            }
+        }
+        for (int i = tid; i < q; i += nthr) {
+            if (inK(i)) continue;
+            C xc[B];   // this row's panel entries; zero past the panel's b columns
+#pragma unroll
+            for (int d = 0; d < B; ++d) xc[d] = d < b ? Pcol[i * B + d] : C(0);
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                C r = 0;
+#pragma unroll
+                for (int d = 0; d < B; ++d) r += xc[d] * Dp[d * B + c];
+                Cn[i * B + c] = -r;
+            }
+        }
+        __syncthreads();
+        // 3. rank-b update of the rows outside K (columns inside K see R = 0)
+        {
+            C Rr[kCols][B];
+#pragma unroll
+            for (int cc = 0; cc < kCols; ++cc) {
+                const int j = lane + 32 * cc;
+#pragma unroll
+                for (int c = 0; c < B; ++c) Rr[cc][c] = (j < q && c < b) ? Prow[c * q + j] : C(0);
+            }
+            for (int i = warp; i < q; i += nw) {
+                if (inK(i)) continue;
+                C pc[B];
+#pragma unroll
+                for (int c = 0; c < B; ++c) pc[c] = c < b ? Pcol[i * B + c] : C(0);
+                C* Wi = W + (size_t)i * q;
+#pragma unroll
+                for (int cc = 0; cc < kCols; ++cc) {
+                    const int j = lane + 32 * cc;
+                    if (j >= q) break;
+                    C w = Wi[j];
+#pragma unroll
+                    for (int c = 0; c < B; ++c) w -= pc[c] * Rr[cc][c];
+                    Wi[j] = w;
+                }
+                for (int j = lane + 32 * kCols; j < q; j += 32) {
+                    C w = Wi[j];
+#pragma unroll
+                    for (int c = 0; c < B; ++c) w -= pc[c] * (c < b ? Prow[c * q + j] : C(0));
+                    Wi[j] = w;
+                }
+            }
+        }
+        __syncthreads();
+        // 4. the swept panel: rows D^-1 W[K][j], columns -W[i][K] D^-1, block D^-1
+        for (int t = tid; t < b * q; t += nthr) {
+            const int c = t / q, j = t - c * q;
+            W[(size_t)(k0 + c) * q + j] = inK(j) ? Dp[c * B + (j - k0)] : Prow[c * q + j];
+        }
+        for (int t = tid; t < q * b; t += nthr) {
+            const int i = t / b, c = t - i * b;
+            if (!inK(i)) W[(size_t)i * q + k0 + c] = Cn[i * B + c];
+        }
+        __syncthreads();
     }
-    for (int t = threadIdx.x; t < qq; t += nthr) {
+    for (int t = tid; t < qq; t += nthr) {
         const int i = t / q, j = t - i * q;
         Minv[t] = C(0.5) * (W[t] + W[(size_t)j * q + i]);
     }

@@ -412,9 +412,9 @@ class Solver : public SolverBase {
             OTM_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
             cudaFuncAttributes fa;
             OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_invert<S, C>));
-            const size_t snapb = 4 * qd * sizeof(C), full = snapb + qd * qd * sizeof(C);
+            const size_t full = invert_smem_bytes((int)qd, (int)sizeof(C), true);
             inv_use_smem_ = fa.sharedSizeBytes + full <= (size_t)optin ? 1 : 0;
-            inv_smem_ = inv_use_smem_ ? full : snapb;
+            inv_smem_ = inv_use_smem_ ? full : invert_smem_bytes((int)qd, (int)sizeof(C), false);
             OTM_TRY(raise_invert_smem(inv_smem_));
         }
         std::vector<double> Ps, Bs;
@@ -642,7 +642,7 @@ class Solver : public SolverBase {
         }
         ++nl_;
         {
-            launch_pdl_smem(k_coarse_invert<S, C>, 1, 1024, inv_smem_, stream, sz[L], Al[L], (C*)Wd, Minv,
+            launch_pdl_smem(k_coarse_invert<S, C>, 1, kInvThreads, inv_smem_, stream, sz[L], Al[L], (C*)Wd, Minv,
                             inv_use_smem_);
         }
         OTM_LAUNCH();

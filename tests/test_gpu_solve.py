@@ -263,3 +263,23 @@ def test_96_sampled_residual():
         assert rel_fro(kap, fem.kappa_from_energies(k, E)) <= 1e-6
     finally:
         otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n", [4, 5, 6, 7])
+def test_single_level_direct_inverse_is_exact(precision, n):
+    """On a single-level hierarchy (n < 8, or odd) the preconditioner is the
+    coarsest dense inverse itself, so PCG from a zero start must finish in one
+    or two iterations: an inaccurate inverse (e.g. a wrong entry in the last,
+    short pivot panel of q = n^3 - 1 unknowns) shows up as extra iterations
+    long before it shows up in the tensor."""
+    tol = 1e-10 if precision == 0 else 1e-6
+    ctx, otm = _ctx(n, precision, tol, rmin=1.5)
+    try:
+        rho = W.initial_density(n, 0.35, 400 + n).astype(np.float32)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        assert max(info.cg_iters) <= 2, list(info.cg_iters)
+        assert max(info.resid) <= tol * 1.0001
+    finally:
+        otm.otm_destroy(ctx)
