@@ -396,9 +396,11 @@ def run_ours(args, rank, world):
                                stream=stream.cuda_stream, device=dev)
     ctx = otm.otm_create_ex(p)
     rho0 = W.initial_density(wl.n, wl.volfrac, replica_seed(wl, rank)).astype(np.float32)
+    launch_cfg = None
     rho_h = torch.from_numpy(rho0).pin_memory()
     rho_d = rho_h.to(f"cuda:{dev}")
     otm.otm_set_density(ctx, rho_d.data_ptr(), 1)
+    launch_cfg = otm.otm_get_config(ctx)   # the (auto-tuned) launch configuration, chosen before warm-up
     for _ in range(args.warmup):
         otm.otm_step(ctx)
     torch.cuda.synchronize()
@@ -511,7 +513,8 @@ def run_ours(args, rank, world):
                    "cg_tol": wl.cg_tol, "precision": {1: "fp32", 2: "mixed-bf16"}[prec],
                    "warm_start": "previous iterate", "parallelism": f"replicas{world}",
                    "l2": "per-step working set (~0.4 GB of fields, ~0.7 GB moved per PCG iteration) exceeds the 129 MB L2",
-                   "mean_cg_iters": float(np.mean(cg)), "max_true_resid": float(max(max(i.resid) for i in infos))},
+                   "mean_cg_iters": float(np.mean(cg)), "max_true_resid": float(max(max(i.resid) for i in infos)),
+                   "launch_config": launch_cfg},
         "e2e": {"value": aggregate_rate(e_steps, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes,
                 "path": "otm_set_state (pinned host) -> otm_step -> otm_get_state (pinned host)"},

@@ -192,6 +192,39 @@ OTM_API otm_status otm_set_density(otm_ctx* ctx, const float* rho, int on_device
 /* Copy the current density (n^3 floats) out. */
 OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
 
+/* The launch configuration a context runs with (Alg. 3's V-cycle and the
+ * Sec. 2.4 stencil).  Reading it builds the step's CUDA graphs first (as
+ * otm_step would), so an automatic choice has been made.
+ *   stencil_form    fine stencil: 0 z-reuse paired, 1 tiled, 2 gather,
+ *                   3 paired three-plane ring (OTM_STENCIL)
+ *   stencil_chunks  z-chunks per column of the z-reuse form (0: not used)
+ *   levels, coarsest_n   the hierarchy: level count and the coarsest side
+ *   cluster_maxn    levels with at most this many nodes per side run in one
+ *                   thread-block cluster launch (0: no cluster)
+ *   cluster_ctas    CTAs of that cluster
+ *   tail_maxn       levels with at most this many nodes per side run in
+ *                   shared memory of the cluster's first CTA
+ *   autotuned       1 when cluster_maxn and cluster_ctas were chosen by
+ *                   timing V-cycles on this device (OTM_AUTOTUNE, default on;
+ *                   the candidates apply the same operations to every node,
+ *                   so the choice never changes a result, only its time)
+ *   tune_us         measured time of one V-cycle per candidate, in the order
+ *                   (maxn 8, 8 CTAs), (8, 16), (16, 8), (16, 16); 0 when not
+ *                   measured
+ * Errors: OTM_EINVAL for NULL arguments; CUDA errors as OTM_ECUDA. */
+typedef struct {
+    int stencil_form;
+    int stencil_chunks;
+    int levels;
+    int coarsest_n;
+    int cluster_maxn;
+    int cluster_ctas;
+    int tail_maxn;
+    int autotuned;
+    double tune_us[4];
+} otm_config;
+OTM_API otm_status otm_get_config(otm_ctx* ctx, otm_config* out);
+
 /* Copy one of the OTM_FIELD_* arrays (as of the last homogenize or step) out
  * as floats; `count` must equal its length (n^3 or 3 n^3). */
 OTM_API otm_status otm_get_field(otm_ctx* ctx, int which, float* out, size_t count, int on_device);

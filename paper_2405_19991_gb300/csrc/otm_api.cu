@@ -191,6 +191,12 @@ otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device) {
     return ctx->s->get_density(rho, on_device != 0);
 }
 
+otm_status otm_get_config(otm_ctx* ctx, otm_config* out) {
+    CTX_CHECK(ctx);
+    if (!out) return ctx_fail(ctx, OTM_EINVAL, "otm_get_config: out is NULL");
+    return ctx->s->get_config(out);
+}
+
 otm_status otm_get_field(otm_ctx* ctx, int which, float* out, size_t count, int on_device) {
     CTX_CHECK(ctx);
     if (!out) return ctx_fail(ctx, OTM_EINVAL, "otm_get_field: out is NULL");

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -49,6 +51,7 @@ struct SolverBase {
     // Build the step's CUDA graphs now (they are otherwise built by the first
     // step); graph construction is serialised process-wide.
     virtual otm_status prepare() = 0;
+    virtual otm_status get_config(otm_config* out) = 0;
     std::string err;
     otm_params prm;
     cudaStream_t stream = nullptr;
@@ -240,6 +243,12 @@ class Solver : public SolverBase {
     bool use_cluster = true;
     int cluster_maxn = kClusterMaxN;   // OTM_CLUSTER_MAXN overrides
     int cl_ctas_ = kClusterCTAs;       // CTAs of the coarse-level cluster
+    bool cl16_ok_ = false;             // a 16-CTA cluster is schedulable here
+    bool maxn_fixed_ = false, ctas_fixed_ = false;   // set by OTM_CLUSTER_MAXN / OTM_CLUSTER_CTAS
+    bool autotune_on_ = true;          // OTM_AUTOTUNE=0 disables the measured choice
+    bool tuned_ = false;
+    int autotuned_ = 0;
+    double tune_us_[4] = {0, 0, 0, 0};
     int cluster_lc() const {
         const int L = nlev - 1;
         if (!use_cluster || nlev < 2) return L + 1;
@@ -365,7 +374,12 @@ class Solver : public SolverBase {
             const char* nc = getenv("OTM_NO_CLUSTER");
             use_cluster = !(nc && nc[0] == '1');
             const char* cm = getenv("OTM_CLUSTER_MAXN");
-            if (cm) cluster_maxn = atoi(cm);
+            if (cm) {
+                cluster_maxn = atoi(cm);
+                maxn_fixed_ = true;
+            }
+            const char* at = getenv("OTM_AUTOTUNE");
+            autotune_on_ = !(at && at[0] == '0');
             const char* tm = getenv("OTM_TAIL_MAXN");
             if (tm) tail_maxn = atoi(tm);
         }
@@ -443,11 +457,14 @@ class Solver : public SolverBase {
             // them with this shared memory, else the portable 8; OTM_CLUSTER_CTAS
             // (8 or 16) overrides
             int want = 16;
-            if (const char* e = getenv("OTM_CLUSTER_CTAS")) want = atoi(e) == 8 ? 8 : 16;
+            if (const char* e = getenv("OTM_CLUSTER_CTAS")) {
+                want = atoi(e) == 8 ? 8 : 16;
+                ctas_fixed_ = true;
+            }
             cl_ctas_ = kClusterCTAs;
-            if (want == 16 &&
-                cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                    cudaSuccess) {
+            cl16_ok_ = false;
+            if (cudaFuncSetAttribute(k_coarse_cluster<S, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                cudaSuccess) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(16, 1, 1);
                 cfg.blockDim = dim3(kClusterThreads, 1, 1);
@@ -462,7 +479,8 @@ class Solver : public SolverBase {
                 int clusters = 0;
                 if (cudaOccupancyMaxActiveClusters(&clusters, k_coarse_cluster<S, C>, &cfg) == cudaSuccess &&
                     clusters >= 1)
-                    cl_ctas_ = 16;
+                    cl16_ok_ = true;
+                if (cl16_ok_ && want == 16) cl_ctas_ = 16;
             }
             cudaGetLastError();
         }
@@ -1026,9 +1044,113 @@ if (zrm_ > 0)
         return OTM_OK;
     }
 
-    otm_status prepare() override { return use_graphs ? ensure_graphs() : OTM_OK; }
+    otm_status prepare() override {
+        OTM_TRY(autotune());
+        return use_graphs ? ensure_graphs() : OTM_OK;
+    }
+
+    // Measured choice of the coarse-level launch configuration: which levels
+    // run in the cluster kernel (at most 8 or 16 nodes per side) and its CTA
+    // count (8, or 16 where a 16-CTA cluster is schedulable).  Every candidate
+    // applies the same per-node operations, so the choice changes no result;
+    // it is made once per device, grid size and precision in the process
+    // (the first context times V-cycles on its own fields after an eager
+    // setup; later ones reuse the choice).
+    struct TuneKey {
+        int device, n, rbytes, sbytes, cheb;
+        bool operator<(const TuneKey& o) const {
+            return std::tie(device, n, rbytes, sbytes, cheb) < std::tie(o.device, o.n, o.rbytes, o.sbytes, o.cheb);
+        }
+    };
+    struct TuneVal {
+        int maxn, ctas;
+        double us[4];
+    };
+    static std::mutex& tune_mutex() {
+        static std::mutex m;
+        return m;
+    }
+    static std::map<TuneKey, TuneVal>& tune_cache() {
+        static std::map<TuneKey, TuneVal> c;
+        return c;
+    }
+    otm_status autotune() {
+        if (tuned_) return OTM_OK;
+        tuned_ = true;
+        if (!autotune_on_ || !use_cluster || nlev < 3 || (maxn_fixed_ && ctas_fixed_)) return OTM_OK;
+        const TuneKey key{device, n, (int)sizeof(R), (int)sizeof(S), cheb_ ? 1 : 0};
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it == tune_cache().end()) {
+            const int cand[4][2] = {{8, 8}, {8, 16}, {16, 8}, {16, 16}};
+            const int keep_maxn = cluster_maxn, keep_ctas = cl_ctas_;
+            OTM_TRY(enqueue_setup());
+            cudaEvent_t e0, e1;
+            OTM_CU(cudaEventCreate(&e0));
+            OTM_CU(cudaEventCreate(&e1));
+            TuneVal best{keep_maxn, keep_ctas, {0, 0, 0, 0}};
+            double best_us = 0.0;
+            otm_status st = OTM_OK;
+            for (int c = 0; c < 4 && st == OTM_OK; ++c) {
+                if (maxn_fixed_ && cand[c][0] != keep_maxn) continue;
+                if (ctas_fixed_ && cand[c][1] != keep_ctas) continue;
+                if (cand[c][1] == 16 && !cl16_ok_) continue;
+                cluster_maxn = cand[c][0];
+                cl_ctas_ = cand[c][1];
+                for (int w = 0; w < 2 && st == OTM_OK; ++w) st = vcycle();
+                if (st != OTM_OK) break;
+                if (cudaEventRecord(e0, stream) != cudaSuccess) st = OTM_ECUDA;
+                for (int r = 0; r < 4 && st == OTM_OK; ++r) st = vcycle();
+                if (st == OTM_OK && cudaEventRecord(e1, stream) != cudaSuccess) st = OTM_ECUDA;
+                if (st == OTM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = OTM_ECUDA;
+                float ms = 0.f;
+                if (st == OTM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = OTM_ECUDA;
+                if (st != OTM_OK) break;
+                const double us = 1000.0 * ms / 4.0;
+                best.us[c] = us;
+                if (best_us == 0.0 || us < best_us) {
+                    best_us = us;
+                    best.maxn = cand[c][0];
+                    best.ctas = cand[c][1];
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cluster_maxn = keep_maxn;
+            cl_ctas_ = keep_ctas;
+            if (st != OTM_OK) {
+                if (err.empty()) err = "autotune: a timing call failed";
+                return st;
+            }
+            it = tune_cache().emplace(key, best).first;
+        }
+        cluster_maxn = it->second.maxn;
+        cl_ctas_ = it->second.ctas;
+        for (int c = 0; c < 4; ++c) tune_us_[c] = it->second.us[c];
+        autotuned_ = 1;
+        return OTM_OK;
+    }
+
+    otm_status get_config(otm_config* out) override {
+        OTM_TRY(prepare());
+        memset(out, 0, sizeof(*out));
+        out->stencil_form = stencil_choice();
+        if (out->stencil_form == 0 && zrm_ == 0) out->stencil_form = tz_ > 0 ? 1 : 2;
+        if (out->stencil_form == 3 && x2tz_ == 0) out->stencil_form = tz_ > 0 ? 1 : 2;
+        if (out->stencil_form == 1 && tz_ == 0) out->stencil_form = 2;
+        out->stencil_chunks = zrm_;
+        out->levels = nlev;
+        out->coarsest_n = sz[nlev - 1];
+        out->cluster_maxn = use_cluster && nlev > 1 ? cluster_maxn : 0;
+        out->cluster_ctas = use_cluster && nlev > 1 ? cl_ctas_ : 0;
+        out->tail_maxn = tail_maxn;
+        out->autotuned = autotuned_;
+        for (int c = 0; c < 4; ++c) out->tune_us[c] = tune_us_[c];
+        return OTM_OK;
+    }
 
     otm_status ensure_graphs() {
+        OTM_TRY(autotune());
         if (gx_first) return OTM_OK;
         std::lock_guard<std::mutex> lock(graph_build_mutex());
         OTM_TRY(capture_pass(true, 0, &gx_first, &nlg_first));
@@ -1049,6 +1171,7 @@ if (zrm_ > 0)
     // Setup + solve.  Returns OTM_OK / OTM_ENOCONV; fills iterations and the
     // checked residuals.
     otm_status setup_and_solve(bool warm, otm_step_info* info, bool learned = false) {
+        OTM_TRY(autotune());
         if (!warm) {
             OTM_CU(cudaMemsetAsync(x, 0, 3 * N * sizeof(R), stream));
             if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));

@@ -50,6 +50,23 @@ class otm_params(C.Structure):
     ]
 
 
+class otm_config(C.Structure):
+    _fields_ = [
+        ("stencil_form", C.c_int),
+        ("stencil_chunks", C.c_int),
+        ("levels", C.c_int),
+        ("coarsest_n", C.c_int),
+        ("cluster_maxn", C.c_int),
+        ("cluster_ctas", C.c_int),
+        ("tail_maxn", C.c_int),
+        ("autotuned", C.c_int),
+        ("tune_us", C.c_double * 4),
+    ]
+
+    def as_dict(self):
+        return {f: (list(getattr(self, f)) if f == "tune_us" else getattr(self, f)) for f, _ in self._fields_}
+
+
 class otm_step_info(C.Structure):
     _fields_ = [
         ("g", C.c_double),
@@ -104,6 +121,7 @@ def _load():
         "otm_set_density": [vp, vp, i],
         "otm_get_density": [vp, vp, i],
         "otm_get_field": [vp, i, vp, sz, i],
+        "otm_get_config": [vp, P(otm_config)],
         "otm_homogenize": [vp, vp, i, P(C.c_double), P(otm_step_info)],
         "otm_step": [vp, P(otm_step_info)],
         "otm_run": [vp, i, P(otm_step_info)],
@@ -148,7 +166,7 @@ lib = _load()
 # Entry points whose declarations in include/otm.h the binding mirrors.
 EXPORTED = [
     "otm_params_default", "otm_check_target", "otm_create", "otm_create_ex", "otm_destroy",
-    "otm_set_density", "otm_get_density", "otm_get_field", "otm_homogenize", "otm_step",
+    "otm_set_density", "otm_get_density", "otm_get_field", "otm_get_config", "otm_homogenize", "otm_step",
     "otm_run", "otm_design_batch", "otm_get_state", "otm_set_state", "otm_last_error",
     "otm_governor_init", "otm_governor_update", "otm_op_filter_simp", "otm_op_filter_transpose",
     "otm_op_macro_load", "otm_op_apply_K", "otm_op_apply_K_async", "otm_op_gs_colour", "otm_op_kappa_sens",
@@ -212,6 +230,12 @@ def otm_set_density(ctx, ptr, on_device):
 
 def otm_get_density(ctx, ptr, on_device):
     return check(lib.otm_get_density(ctx, ptr, int(on_device)), ctx)
+
+
+def otm_get_config(ctx):
+    cfg = otm_config()
+    check(lib.otm_get_config(ctx, C.byref(cfg)), ctx)
+    return cfg.as_dict()
 
 
 def otm_get_field(ctx, which, ptr, count, on_device):

@@ -252,3 +252,53 @@ def test_contexts_of_different_sizes_coexist(monkeypatch):
     finally:
         for ctx in made:
             otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("n,precision", [(64, 1), (48, 2), (128, 1)])
+def test_autotuned_configuration_is_valid(n, precision):
+    """The measured coarse-level choice: one of the candidates, with the
+    candidates' V-cycle times recorded, and the solve still converging."""
+    ctx, otm = _make(n, precision, 1e-6, rmin=2.0, target=W.TARGET_ORTHOTROPIC)
+    try:
+        rho0 = W.initial_density(n, 0.3, 5).astype(np.float32)
+        otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+        cfg = otm.otm_get_config(ctx)
+        assert cfg["levels"] >= 3 and cfg["autotuned"] == 1, cfg
+        assert cfg["cluster_maxn"] in (8, 16) and cfg["cluster_ctas"] in (8, 16), cfg
+        us = cfg["tune_us"]
+        assert us[0] > 0 and us[2] > 0 and all(u >= 0 for u in us), cfg
+        chosen = {(8, 8): 0, (8, 16): 1, (16, 8): 2, (16, 16): 3}[(cfg["cluster_maxn"], cfg["cluster_ctas"])]
+        assert us[chosen] == min(u for u in us if u > 0), cfg
+        if n % 64 == 0:
+            assert cfg["stencil_form"] == 0 and cfg["stencil_chunks"] >= 1, cfg
+        info, st = otm.otm_step(ctx)
+        assert st == otm.OTM_OK and max(info.resid) <= 1e-6 * 1.0001
+    finally:
+        otm.otm_destroy(ctx)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_coarse_launch_configurations_are_bitwise_equal(precision, monkeypatch):
+    """Every configuration the tuner chooses among applies the same operations
+    to every node: the design trajectory is the same to the bit."""
+    n = 64
+    rho0 = W.initial_density(n, 0.3, 6).astype(np.float32)
+    outs = []
+    for maxn, ctas in ((8, 8), (16, 16), (16, 8)):
+        monkeypatch.setenv("OTM_CLUSTER_MAXN", str(maxn))
+        monkeypatch.setenv("OTM_CLUSTER_CTAS", str(ctas))
+        ctx, otm = _make(n, precision, 1e-6, rmin=2.0, target=W.TARGET_ORTHOTROPIC)
+        try:
+            otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+            cfg = otm.otm_get_config(ctx)
+            assert (cfg["cluster_maxn"], cfg["autotuned"]) == (maxn, 0), cfg
+            infos, st = otm.otm_run(ctx, 3)
+            chi = np.empty(3 * n ** 3, np.float32)
+            otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * n ** 3, 0)
+            outs.append((_rho(ctx, otm, n), chi, [i.g for i in infos]))
+        finally:
+            otm.otm_destroy(ctx)
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0])
+        assert np.array_equal(outs[0][1].view(np.uint32), o[1].view(np.uint32))
+        assert outs[0][2] == o[2]
