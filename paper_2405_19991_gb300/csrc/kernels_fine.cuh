@@ -89,6 +89,55 @@ __device__ __forceinline__ C nb_sum(const UT* __restrict__ u, const Nbr& g, cons
     return acc;
 }
 
+// nb_sum split into its loads (in use order) and its arithmetic, so a
+// caller can issue the loads of several load cases before any of the sums.
+template <class UT, class C>
+__device__ __forceinline__ void nb_load(const UT* __restrict__ u, const Nbr& g, C (&w)[20]) {
+    int t = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) w[t++] = (C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.Z[c]));
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) w[t++] = (C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.zc));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) w[t++] = (C)St<UT>::ld(u, (size_t)(g.X[a] + g.yc + g.Z[c]));
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) w[t++] = (C)St<UT>::ld(u, (size_t)(g.xc + g.Y[b] + g.Z[c]));
+}
+template <class C>
+__device__ __forceinline__ C nb_from(const C (&w)[20], const C (&kk)[2][2][2]) {
+    C acc = 0;
+    int t = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) acc += kk[c][b][a] * w[t++];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) acc += (kk[0][b][a] + kk[1][b][a]) * w[t++];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) acc += (kk[c][0][a] + kk[c][1][a]) * w[t++];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc += (kk[c][b][0] + kk[c][b][1]) * w[t++];
+    return acc;
+}
+
 // Difference form of the same sum: nd(u) = sum coef (u_w - u_v) = nb(u) - 4 sum(k) u_v,
 // so 12 [K u]_v = -nd(u).  Constant fields cancel exactly, which keeps the
 // rounding error of K u proportional to the local differences of u instead
@@ -444,6 +493,9 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
 // and, when xpar >= 0, x%2 == xpar.  ZERO: the relaxed field starts at zero;
 // the pass also zeroes the other nodes of each 2x2 (y, z) cell, so no
 // separate clear is needed (only valid for group 0, xpar < 0).
+#ifndef OTM_GS_PRELOAD
+#define OTM_GS_PRELOAD 1
+#endif
 template <bool ZERO, class KT, class FT, class TT>
 __global__ void __launch_bounds__(256)
 k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __restrict__ f,
@@ -463,12 +515,25 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
         load_k8<KT, C>(k, g, kk);
         const C inv4k = C(1) / (C(4) * ksum8(kk));
         const size_t v = (size_t)(g.xc + g.yc + g.zc);
+#if OTM_GS_PRELOAD
+        // all three load cases' neighbour values in flight before any sum
+        // (the stores below could alias them as far as the compiler knows)
+        C w[3][20];
+        if (!ZERO) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) nb_load<TT, C>(T + (size_t)i * N, g, w[i]);
+        }
+#endif
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             TT* Ti = T + (size_t)i * N;
             const C fv = St<FT>::ld(f + (size_t)i * N, v);
             C nb = 0;
+#if OTM_GS_PRELOAD
+            if (!ZERO) nb = nb_from<C>(w[i], kk);
+#else
             if (!ZERO) nb = nb_sum<TT, C>(Ti, g, kk);
+#endif
             St<TT>::st(Ti, v, (C(12) * fv + nb) * inv4k);
             if (ZERO) {
                 const size_t y1 = (size_t)(y + 1) * n, z1 = (size_t)(z + 1) * n * n;
