@@ -109,29 +109,42 @@ k_prolong_wr(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
         if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = 0.5f; cz = 2; }
         else { zi[0] = zi[1] = z >> 1; wz[0] = 1.f; wz[1] = 0.f; }
         const size_t vb = (size_t)row * nf + (size_t)xb;
-#pragma unroll 1
-        for (int i = 0; i < 3; ++i) {
-            // the coarse field is node-major ([Nc][4])
-            auto tc = [&](size_t node) -> float { return (float)St<CT>::ld(Tc, node * 4 + i); };
-            float s[3] = {0.f, 0.f, 0.f};
-            for (int c = 0; c < cz; ++c)
-                for (int b = 0; b < cy; ++b) {
-                    const size_t ro = (size_t)yi[b] * nc + (size_t)zi[c] * nc * nc;
-                    const float a0 = tc(ro + cxb);
-                    const float a1 = tc(ro + cxb + 1);
-                    float a2 = __shfl_sync(0xffffffffu, a0, (lane + 1) & 31);
-                    if (lane == 31 && wpr > 1) a2 = tc(ro + (size_t)(cxb + 2 == nc ? 0 : cxb + 2));
-                    const float wgt = wz[c] * wy[b];
-                    s[0] += wgt * a0;
-                    s[1] += wgt * a1;
-                    s[2] += wgt * a2;
+        // the coarse field is node-major ([Nc][4]): one load brings a node's
+        // three load cases; per load case the sums run in the same order
+        float s[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        auto tc3 = [&](size_t node, float (&a)[3]) {
+            typename St<CT>::C q[3];
+            ld_f3<CT>(Tc, node, q);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) a[i] = (float)q[i];
+        };
+        for (int c = 0; c < cz; ++c)
+            for (int b = 0; b < cy; ++b) {
+                const size_t ro = (size_t)yi[b] * nc + (size_t)zi[c] * nc * nc;
+                float a0[3], a1[3], a2[3];
+                tc3(ro + cxb, a0);
+                tc3(ro + cxb + 1, a1);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) a2[i] = __shfl_sync(0xffffffffu, a0[i], (lane + 1) & 31);
+                if (lane == 31 && wpr > 1) tc3(ro + (size_t)(cxb + 2 == nc ? 0 : cxb + 2), a2);
+                const float wgt = wz[c] * wy[b];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    s[i][0] += wgt * a0[i];
+                    s[i][1] += wgt * a1[i];
+                    s[i][2] += wgt * a2[i];
                 }
-            Q4<float> t = ld4f(T + (size_t)i * Nf, vb);
-            t.v[0] += s[0];
-            t.v[1] += 0.5f * (s[0] + s[1]);
-            t.v[2] += s[1];
-            t.v[3] += 0.5f * (s[1] + s[2]);
-            st4f(T + (size_t)i * Nf, vb, t);
+            }
+        Q4<float> t[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) t[i] = ld4f(T + (size_t)i * Nf, vb);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            t[i].v[0] += s[i][0];
+            t[i].v[1] += 0.5f * (s[i][0] + s[i][1]);
+            t[i].v[2] += s[i][1];
+            t[i].v[3] += 0.5f * (s[i][1] + s[i][2]);
+            st4f(T + (size_t)i * Nf, vb, t[i]);
         }
     }
 }
