@@ -116,8 +116,8 @@ __device__ __forceinline__ C interp_pass(C own, C partner, bool up) {
 }
 template <class C, bool FROM_K, class KT>
 __global__ void __launch_bounds__(256)
-k_elem_coarsen(int nc, const C* __restrict__ Kf, const KT* __restrict__ k, const C* __restrict__ Ps,
-               const C* __restrict__ Bs, C* __restrict__ Kc) {
+k_elem_coarsen(int nc, const C* __restrict__ Kf, const KT* __restrict__ k, const C* __restrict__ Bs,
+               C* __restrict__ Kc) {
     pdl_enter();
     __shared__ C bs[FROM_K ? 8 * 64 : 1];
     if (FROM_K) {
@@ -218,7 +218,6 @@ template <class KT, class C, class AT>
 __global__ void __launch_bounds__(128)
 k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
     pdl_enter();
-    const size_t N = (size_t)n * n * n;
     OTM_FOR_ROWS(row_, n * n) {
     const int y = row_ % n, z = row_ / n;
     OTM_FOR_X(x, n) {
@@ -343,7 +342,6 @@ k_gershgorin(int n, const AT* __restrict__ A, float* __restrict__ lam) {
     float g = 0.0f;
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
         C s = 0;
-#pragma unroll
         C a[27];
         ld_arow<AT>(A, v, a);
 #pragma unroll

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256)
 k_prolong_wr(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
     pdl_enter();
     const int nc = nf / 2;
-    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
+    const size_t Nf = (size_t)nf * nf * nf;
     const int lane = threadIdx.x & 31;
     const int wpr = nf / 128;
     const long long nwarps = (long long)nf * nf * wpr;

@@ -119,7 +119,6 @@ otm_status filter_simp_t(int n, double rmin, double penal, double ks, double kv,
     OpCtx oc(stream);
     Scratch sc;
     if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_filter_simp: scratch");
-    const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
     otm::launch_filter<R, true>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), 1, (const R*)rho, (R*)rho_f, (R*)k,
                                 simp_p(penal, ks, kv), rb, otm::FinFilter{sc.ds});
@@ -129,7 +128,6 @@ otm_status filter_simp_t(int n, double rmin, double penal, double ks, double kv,
 template <class R>
 otm_status filter_t_t(int n, double rmin, const void* s_f, void* s, void* stream) {
     OpCtx oc(stream);
-    const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{nullptr, nullptr, 0};
     otm::launch_filter<R, false>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), -1, (const R*)s_f, (R*)s, (R*)nullptr,
                                  simp_p(3, 1, 1e-3), rb, otm::FinFilter{nullptr});
@@ -139,7 +137,6 @@ otm_status filter_t_t(int n, double rmin, const void* s_f, void* s, void* stream
 template <class R>
 otm_status macro_load_t(int n, const void* k, void* f, void* stream) {
     OpCtx oc(stream);
-    const size_t N = (size_t)n * n * n;
     otm::k_macro_load<R, R><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(n, (const R*)k, (R*)f);
     return finish(oc.st, "otm_op_macro_load");
 }
@@ -147,7 +144,6 @@ otm_status macro_load_t(int n, const void* k, void* f, void* stream) {
 template <class R>
 otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream, bool sync = true) {
     OpCtx oc(stream);
-    const size_t N = (size_t)n * n * n;
     otm::RedBuf rb{nullptr, nullptr, 0};
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -167,7 +163,7 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     const int tz = sizeof(R) == 4 && otm::stencil_choice() != 2 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
     if (tz > 0)
         otm::k_stencil_tiled<0, false, R, R, R, R, otm::FinNone>
-            <<<(n / otm::kTX) * (n / otm::kTY) * (n / tz), dim3(otm::kTX, otm::kTY), 0, oc.st>>>(
+            <<<(n / otm::kTX) * (n / otm::kTY) * (n / (tz > 0 ? tz : 1)), dim3(otm::kTX, otm::kTY), 0, oc.st>>>(
                 n, tz, (const R*)k, (const R*)u, (const R*)nullptr, (R*)Ku, rb, otm::FinNone{});
     else
         otm::k_stencil_apply<0, false, R, R, R, R, otm::FinNone><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(

@@ -166,7 +166,7 @@ class Solver : public SolverBase {
     float* lam_d = nullptr;                          // per-level Gershgorin bounds of D^-1 A
     bool cheb_ = false;                              // coarse levels smoothed by Chebyshev (coarse_smoother = 1)
     C *Kel[kMaxLevels] = {};
-    C *Bs_d = nullptr, *Ps_d = nullptr, *Minv = nullptr;
+    C *Bs_d = nullptr, *Minv = nullptr;
     double* Wd = nullptr;
     // reductions and scalars
     double* partials = nullptr;
@@ -211,7 +211,7 @@ class Solver : public SolverBase {
         if (cap2) cudaStreamDestroy(cap2);
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
-        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Ps_d, Minv, Wd,
+        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
                         partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
@@ -433,10 +433,8 @@ class Solver : public SolverBase {
         }
         std::vector<double> Ps, Bs;
         build_ps(Ps, Bs);
-        std::vector<C> Psc(Ps.begin(), Ps.end()), Bsc(Bs.begin(), Bs.end());
-        OTM_TRY(alloc(Ps_d, 8 * 64));
+        std::vector<C> Bsc(Bs.begin(), Bs.end());
         OTM_TRY(alloc(Bs_d, 8 * 64));
-        OTM_CU(cudaMemcpyAsync(Ps_d, Psc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
         OTM_CU(cudaMemcpyAsync(Bs_d, Bsc.data(), 8 * 64 * sizeof(C), cudaMemcpyHostToDevice, stream));
         {
             // Opt in to exactly the dynamic shared memory the cluster kernel
@@ -638,10 +636,10 @@ class Solver : public SolverBase {
                 const long long warps = (long long)Nl[l + 1];
                 const int cg = (int)std::min<long long>((warps + 7) / 8, (long long)sm_count * 16);
                 if (l == 1)
-                    launch_pdl(k_elem_coarsen<C, true, R>, cg, 256, stream, sz[l + 1], (const C*)nullptr, kf, Ps_d,
+                    launch_pdl(k_elem_coarsen<C, true, R>, cg, 256, stream, sz[l + 1], (const C*)nullptr, kf,
                                Bs_d, Kel[l + 1]);
                 else
-                    launch_pdl(k_elem_coarsen<C, false, R>, cg, 256, stream, sz[l + 1], (const C*)Kel[l], kf, Ps_d,
+                    launch_pdl(k_elem_coarsen<C, false, R>, cg, 256, stream, sz[l + 1], (const C*)Kel[l], kf,
                                Bs_d, Kel[l + 1]);
                 OTM_LAUNCH();
                 ++nl_;
