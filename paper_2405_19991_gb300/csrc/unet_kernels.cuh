@@ -194,57 +194,102 @@ k_conv3_dw(int n, int Cin, int Ca, int Cout, int chunk, const bf16* __restrict__
     if (db && blockIdx.y == 0 && t == 0 && tid < BN) atomicAdd(db + n0 + tid, bsum);
 }
 
-// g = g * (y > 0): ReLU backward, y the block output.
+// The channel-wise kernels below move 8 channels (16 bytes) per thread and
+// step (channel counts are multiples of 16), with 32-bit indices (fewer than
+// 2^31 voxel-channels).  Per channel the arithmetic and its order are those
+// of a one-element-per-thread loop.
+__device__ __forceinline__ void bf8_load(const bf16* p, float (&f)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+        f[2 * i] = __low2float(h);
+        f[2 * i + 1] = __high2float(h);
+    }
+}
+__device__ __forceinline__ void bf8_store(bf16* p, const float (&f)[8]) {
+    unsigned w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const __nv_bfloat162 h = __halves2bfloat162(__float2bfloat16_rn(f[2 * i]), __float2bfloat16_rn(f[2 * i + 1]));
+        w[i] = *reinterpret_cast<const unsigned*>(&h);
+    }
+    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+__device__ __forceinline__ void copy8(bf16* d, const bf16* s) {
+    *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(s);
+}
+
+// g = g * (y > 0): ReLU backward, y the block output (count a multiple of 8).
 static __global__ void k_relu_mask(size_t count, bf16* __restrict__ g, const bf16* __restrict__ y) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-        if (!(__bfloat162float(y[i]) > 0.f)) g[i] = __float2bfloat16_rn(0.f);
+    const unsigned n8 = (unsigned)(count / 8);
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n8; e += gridDim.x * blockDim.x) {
+        float gv[8], yv[8];
+        bf8_load(g + 8 * (size_t)e, gv);
+        bf8_load(y + 8 * (size_t)e, yv);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (!(yv[i] > 0.f)) gv[i] = 0.f;
+        bf8_store(g + 8 * (size_t)e, gv);
+    }
 }
 
 // 2x2x2 average pooling, [8 Nc][C] -> [Nc][C] (coarse grid nc per side).
 static __global__ void k_pool(int nc, int C, const bf16* __restrict__ in, bf16* __restrict__ out) {
-    const size_t Nc = (size_t)nc * nc * nc;
-    const int nf = 2 * nc;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nc * C; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t V = e / C;
-        const int c = (int)(e % C);
-        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((size_t)nc * nc));
-        float s = 0.f;
+    const unsigned Nc = (unsigned)nc * nc * nc;
+    const int nf = 2 * nc, C8 = C / 8;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < Nc * C8; e += gridDim.x * blockDim.x) {
+        const unsigned V = e / C8;
+        const int c = (int)(e - V * C8) * 8;
+        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((unsigned)nc * nc));
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < 8; ++q) {
-            const size_t f = (size_t)(2 * X + (q & 1)) + (size_t)nf * ((2 * Y + ((q >> 1) & 1)) + (size_t)nf * (2 * Z + (q >> 2)));
-            s += __bfloat162float(in[f * C + c]);
+            const unsigned f = (unsigned)(2 * X + (q & 1)) + (unsigned)nf * ((2 * Y + ((q >> 1) & 1)) + (unsigned)nf * (2 * Z + (q >> 2)));
+            float w[8];
+            bf8_load(in + (size_t)f * C + c, w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += w[i];
         }
-        out[e] = __float2bfloat16_rn(0.125f * s);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s[i] *= 0.125f;
+        bf8_store(out + (size_t)V * C + c, s);
     }
 }
 
 // din[v][c] += dout[v / 2][c] / 8 (adjoint of the pooling), fine grid nf.
 static __global__ void k_pool_back_add(int nf, int C, const bf16* __restrict__ dout, bf16* __restrict__ din) {
-    const size_t Nf = (size_t)nf * nf * nf;
-    const int nc = nf / 2;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * C; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = e / C;
-        const int c = (int)(e % C);
-        const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
-        const size_t V = (size_t)(x >> 1) + (size_t)nc * ((y >> 1) + (size_t)nc * (z >> 1));
-        din[e] = __float2bfloat16_rn(__bfloat162float(din[e]) + 0.125f * __bfloat162float(dout[V * C + c]));
+    const unsigned Nf = (unsigned)nf * nf * nf;
+    const int nc = nf / 2, C8 = C / 8;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < Nf * C8; e += gridDim.x * blockDim.x) {
+        const unsigned v = e / C8;
+        const int c = (int)(e - v * C8) * 8;
+        const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((unsigned)nf * nf));
+        const unsigned V = (unsigned)(x >> 1) + (unsigned)nc * ((y >> 1) + (unsigned)nc * (z >> 1));
+        float a[8], d[8];
+        bf8_load(din + (size_t)v * C + c, a);
+        bf8_load(dout + (size_t)V * C + c, d);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) a[i] = a[i] + 0.125f * d[i];
+        bf8_store(din + (size_t)v * C + c, a);
     }
 }
 
 // cat[v][0..Cu) = up(coarse)[v], cat[v][Cu..Cu+Cs) = skip[v]  (fine grid nf)
 static __global__ void k_up_cat(int nf, int Cu, int Cs, const bf16* __restrict__ coarse, const bf16* __restrict__ skip,
-                         bf16* __restrict__ cat) {
-    const size_t Nf = (size_t)nf * nf * nf;
+                                bf16* __restrict__ cat) {
+    const unsigned Nf = (unsigned)nf * nf * nf;
     const int nc = nf / 2;
-    const int Ct = Cu + Cs;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * Ct; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = e / Ct;
-        const int c = (int)(e % Ct);
-        if (c < Cu) {
-            const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((size_t)nf * nf));
-            const size_t V = (size_t)(x >> 1) + (size_t)nc * ((y >> 1) + (size_t)nc * (z >> 1));
-            cat[e] = coarse[V * Cu + c];
+    const int Ct = Cu + Cs, T8 = Ct / 8, U8 = Cu / 8;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < Nf * T8; e += gridDim.x * blockDim.x) {
+        const unsigned v = e / T8;
+        const int j = (int)(e - v * T8);
+        if (j < U8) {
+            const int x = (int)(v % nf), y = (int)((v / nf) % nf), z = (int)(v / ((unsigned)nf * nf));
+            const unsigned V = (unsigned)(x >> 1) + (unsigned)nc * ((y >> 1) + (unsigned)nc * (z >> 1));
+            copy8(cat + (size_t)v * Ct + 8 * j, coarse + (size_t)V * Cu + 8 * j);
         } else {
-            cat[e] = skip[v * Cs + (c - Cu)];
+            copy8(cat + (size_t)v * Ct + 8 * j, skip + (size_t)v * Cs + 8 * (j - U8));
         }
     }
 }
@@ -253,25 +298,28 @@ static __global__ void k_up_cat(int nf, int Cu, int Cs, const bf16* __restrict__
 // children of dcat[v][c] (c < Cu) (the adjoint of the upsampling), and
 // dskip[v][c] = dcat[v][Cu + c].
 static __global__ void k_up_cat_back(int nf, int Cu, int Cs, const bf16* __restrict__ dcat, bf16* __restrict__ dcoarse,
-                              bf16* __restrict__ dskip) {
+                                     bf16* __restrict__ dskip) {
     const int nc = nf / 2;
-    const size_t Nc = (size_t)nc * nc * nc, Nf = (size_t)nf * nf * nf;
-    const int Ct = Cu + Cs;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nc * Cu; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t V = e / Cu;
-        const int c = (int)(e % Cu);
-        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((size_t)nc * nc));
-        float s = 0.f;
+    const unsigned Nc = (unsigned)nc * nc * nc, Nf = (unsigned)nf * nf * nf;
+    const int Ct = Cu + Cs, U8 = Cu / 8, S8 = Cs / 8;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < Nc * U8; e += gridDim.x * blockDim.x) {
+        const unsigned V = e / U8;
+        const int c = (int)(e - V * U8) * 8;
+        const int X = (int)(V % nc), Y = (int)((V / nc) % nc), Z = (int)(V / ((unsigned)nc * nc));
+        float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < 8; ++q) {
-            const size_t f = (size_t)(2 * X + (q & 1)) + (size_t)nf * ((2 * Y + ((q >> 1) & 1)) + (size_t)nf * (2 * Z + (q >> 2)));
-            s += __bfloat162float(dcat[f * Ct + c]);
+            const unsigned f = (unsigned)(2 * X + (q & 1)) + (unsigned)nf * ((2 * Y + ((q >> 1) & 1)) + (unsigned)nf * (2 * Z + (q >> 2)));
+            float w[8];
+            bf8_load(dcat + (size_t)f * Ct + c, w);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s[i] += w[i];
         }
-        dcoarse[e] = __float2bfloat16_rn(s);
+        bf8_store(dcoarse + (size_t)V * Cu + c, s);
     }
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < Nf * Cs; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = e / Cs;
-        const int c = (int)(e % Cs);
-        dskip[e] = dcat[v * Ct + Cu + c];
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < Nf * S8; e += gridDim.x * blockDim.x) {
+        const unsigned v = e / S8;
+        const int j = (int)(e - v * S8);
+        copy8(dskip + (size_t)v * Cs + 8 * j, dcat + (size_t)v * Ct + Cu + 8 * j);
     }
 }
 
@@ -292,11 +340,16 @@ static __global__ void k_head(size_t N, int C, const bf16* __restrict__ d, const
                        const float* __restrict__ b, float* __restrict__ y) {
     for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += (size_t)gridDim.x * blockDim.x) {
         float a0 = b[0], a1 = b[1], a2 = b[2];
-        for (int c = 0; c < C; ++c) {
-            const float dv = __bfloat162float(d[v * C + c]);
-            a0 += dv * H[c * 3 + 0];
-            a1 += dv * H[c * 3 + 1];
-            a2 += dv * H[c * 3 + 2];
+        for (int c0 = 0; c0 < C; c0 += 8) {
+            float dv[8];
+            bf8_load(d + v * C + c0, dv);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int c = c0 + i;
+                a0 += dv[i] * H[c * 3 + 0];
+                a1 += dv[i] * H[c * 3 + 1];
+                a2 += dv[i] * H[c * 3 + 2];
+            }
         }
         y[v] = a0;
         y[N + v] = a1;
