@@ -232,9 +232,10 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
 // ||f - K (hi + lo)||^2 with error-free element terms (see k_true_residual):
 // each of the 32 terms k_e (u_w - u_v) of a node is formed with TwoProduct
 // and summed with TwoSum.
-static __global__ void __launch_bounds__(256, 3)
+template <class Fin>
+__global__ void __launch_bounds__(256, 3)
 k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
-                   const float* __restrict__ f, RedBuf rb, FinTrue fin) {
+                   const float* __restrict__ f, RedBuf rb, Fin fin) {
     pdl_enter();
     const size_t N = (size_t)n * n * n;
     const int lane = threadIdx.x & 31;

@@ -876,7 +876,7 @@ if (zrm_ > 0)
     otm_status enqueue_check() {
         ++nl_;
         if (wr_)
-            launch_pdl(k_true_residual_wr, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const float*)kf,
+            launch_pdl(k_true_residual_wr<FinTrue>, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const float*)kf,
                        (const float*)x, (const float*)xl, (const float*)f, rbuf(), FinTrue{ps});
         else
             launch_pdl(k_true_residual<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, rbuf(), FinTrue{ps});
@@ -1265,8 +1265,13 @@ if (zrm_ > 0)
         RedBuf rb = rbuf();
         auto score = [&](const R* xh, const R* xlo, int slot) -> otm_status {
             ++nl_;
-            launch_pdl(k_true_residual<R, FinStore>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, xh, xlo, f, rb,
-                       FinStore{&ws->cand[slot][0]});
+            if (wr_)
+                launch_pdl(k_true_residual_wr<FinStore>, wr_grid((long long)n * n * (n / 128)), 256, stream, n,
+                           (const float*)kf, (const float*)xh, (const float*)xlo, (const float*)f, rb,
+                           FinStore{&ws->cand[slot][0]});
+            else
+                launch_pdl(k_true_residual<R, FinStore>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, xh, xlo, f, rb,
+                           FinStore{&ws->cand[slot][0]});
             OTM_LAUNCH();
             return OTM_OK;
         };

@@ -442,14 +442,15 @@ static __global__ void k_adam(size_t P, float* __restrict__ p, const float* __re
 // (tap t -> 26 - t).
 static __global__ void k_pack_w(int a, int ap, int b, const float* __restrict__ w, bf16* __restrict__ wc,
                          bf16* __restrict__ wt) {
-    const size_t M = (size_t)27 * ap * b;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < M; e += (size_t)gridDim.x * blockDim.x) {
-        const int t = (int)(e / ((size_t)ap * b));
-        const int ci = (int)((e / b) % ap), co = (int)(e % b);
-        const float val = ci < a ? w[((size_t)t * a + ci) * b + co] : 0.f;
+    const unsigned M = 27u * ap * b, apb = (unsigned)ap * b;
+    for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < M; e += gridDim.x * blockDim.x) {
+        const int t = (int)(e / apb);
+        const unsigned r = e - t * apb;
+        const int ci = (int)(r / b), co = (int)(r - ci * b);
+        const float val = ci < a ? w[((unsigned)t * a + ci) * b + co] : 0.f;
         const bf16 bv = __float2bfloat16_rn(val);
         wc[e] = bv;
-        if (wt) wt[((size_t)(26 - t) * b + co) * ap + ci] = bv;
+        if (wt) wt[((unsigned)(26 - t) * b + co) * ap + ci] = bv;
     }
 }
 
