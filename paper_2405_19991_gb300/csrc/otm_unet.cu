@@ -356,19 +356,34 @@ struct otm_unet {
         return OTM_OK;
     }
 
+    // keep_input: also store the padded input (the first layer's weight
+    // gradient needs it); a prediction alone does not.
     template <class T>
-    otm_status forward(const T* x, cudaStream_t st) {
-        otm::nn::k_input16<T><<<elt_grid(Nl[0]), 256, 0, st>>>(Nl[0], x, x0);
-        g_launches += 1;
-        U_LAUNCH();
+    otm_status forward(const T* x, cudaStream_t st, bool keep_input = true) {
+        const bool direct = cv[0].b <= 64;   // first convolution on the CUDA cores (k_conv3_in1)
+        if (keep_input || !direct) {
+            otm::nn::k_input16<T><<<elt_grid(Nl[0]), 256, 0, st>>>(Nl[0], x, x0);
+            g_launches += 1;
+            U_LAUNCH();
+        }
         for (int k = 0; k < 4; ++k) {
             if (k > 0) {
                 const size_t M = Nl[k] * c[k - 1];
                 otm::nn::k_pool<<<elt_grid(M), 256, 0, st>>>(side[k], c[k - 1], h2[k - 1], pin[k]);
                 g_launches += 1;
                 U_LAUNCH();
+                U_TRY(block_fwd(k, st));
+            } else if (!direct) {
+                U_TRY(block_fwd(0, st));
+            } else {
+                // block 0: the first convolution straight from the density
+                const Conv &q1 = cv[0], &q2 = cv[1];
+                otm::nn::k_conv3_in1<T><<<elt_grid(Nl[0]), 256, 0, st>>>(side[0], x, q1.Wc, q1.ap, q1.b, p + q1.ob,
+                                                                          h1[0]);
+                g_launches += 1;
+                U_LAUNCH();
+                U_TRY(conv3(side[0], q2.ap, q2.b, h1[0], q2.Wc, p + q2.ob, true, h2[0], st));
             }
-            U_TRY(block_fwd(k, st));
         }
         // D2 <- (E3, E2), D1 <- (D2, E1), D0 <- (D1, E0)
         const bf16* coarse[3] = {h2[3], h2[4], h2[5]};
@@ -384,7 +399,7 @@ struct otm_unet {
         otm::nn::k_head<<<elt_grid(Nl[0]), 256, 0, st>>>(Nl[0], c[0], h2[6], p + oHW, p + oHb, y);
         g_launches += 1;
         U_LAUNCH();
-        have_forward = true;
+        have_forward = keep_input;
         return OTM_OK;
     }
 
@@ -463,8 +478,8 @@ struct otm_unet {
 namespace otm {
 
 otm_status unet_predict(otm_unet* u, const void* x, bool x_double, float* y, cudaStream_t st) {
-    if (x_double) U_TRY(u->forward((const double*)x, st));
-    else U_TRY(u->forward((const float*)x, st));
+    if (x_double) U_TRY(u->forward((const double*)x, st, false));
+    else U_TRY(u->forward((const float*)x, st, false));
     U_CU(cudaMemcpyAsync(y, u->y, 3 * u->Nl[0] * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return OTM_OK;
 }

@@ -323,6 +323,48 @@ static __global__ void k_up_cat_back(int nf, int Cu, int Cs, const bf16* __restr
     }
 }
 
+// The network's first convolution, whose input is the single density
+// channel: y[v][co] = relu(b[co] + sum_t W[t][0][co] bf16(rho[v + off(t)]))
+// with the packed weights [27][16][cout] (only input channel 0 is real), in
+// FP32 on the CUDA cores -- the tensor-core path would multiply 15 zero
+// channels.  cout <= 64, a multiple of 8.
+template <class T>
+__global__ void __launch_bounds__(256)
+k_conv3_in1(int n, const T* __restrict__ rho, const bf16* __restrict__ W, int ap, int cout,
+            const float* __restrict__ bias, bf16* __restrict__ y) {
+    __shared__ float w[27][64];
+    __shared__ float bs[64];
+    for (int i = threadIdx.x; i < 27 * cout; i += blockDim.x) {
+        const int t = i / cout, co = i - t * cout;
+        w[t][co] = __bfloat162float(W[((size_t)t * ap) * cout + co]);
+    }
+    for (int i = threadIdx.x; i < cout; i += blockDim.x) bs[i] = bias ? bias[i] : 0.f;
+    __syncthreads();
+    const unsigned N = (unsigned)n * n * n;
+    for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        const int x = (int)(v % n), yy = (int)((v / n) % n), z = (int)(v / ((unsigned)n * n));
+        float r[27];
+#pragma unroll
+        for (int t = 0; t < 27; ++t) {
+            const unsigned o = (unsigned)wrapd(x, tap_dx(t), n) +
+                               (unsigned)n * ((unsigned)wrapd(yy, tap_dy(t), n) + (unsigned)n * wrapd(z, tap_dz(t), n));
+            r[t] = __bfloat162float(__float2bfloat16_rn((float)rho[o]));
+        }
+        for (int c0 = 0; c0 < cout; c0 += 8) {
+            float a[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 27; ++t)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a[i] += w[t][c0 + i] * r[t];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = fmaxf(a[i] + bs[c0 + i], 0.f);
+            bf8_store(y + (size_t)v * cout + c0, a);
+        }
+    }
+}
+
 // Input layer: x[v][0] = rho[v], channels 1..15 zero (Cin padded to 16).
 template <class T>
 __global__ void k_input16(size_t N, const T* __restrict__ rho, bf16* __restrict__ x) {
