@@ -209,6 +209,9 @@ class Solver : public SolverBase {
         if (gx_pass) cudaGraphExecDestroy(gx_pass);
         if (gx_tail) cudaGraphExecDestroy(gx_tail);
         if (cap2) cudaStreamDestroy(cap2);
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
         void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
@@ -368,6 +371,9 @@ class Solver : public SolverBase {
         }
         for (auto& e : ev) OTM_CU(cudaEventCreate(&e));
         OTM_CU(cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking));
+        OTM_CU(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        OTM_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        OTM_CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
         {
             const char* ng = getenv("OTM_NO_GRAPH");
             use_graphs = !(ng && ng[0] == '1');
@@ -611,6 +617,11 @@ class Solver : public SolverBase {
     }
 
     otm_status build_hierarchy() {
+        OTM_TRY(fine_loads());
+        return coarse_hierarchy();
+    }
+    // macro loads (zero-mean) and the V-cycle's copy of k: fine-grid work
+    otm_status fine_loads() {
         ++nl_;
         launch_pdl(k_macro_load<R, R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, f);
         ++nl_;
@@ -623,6 +634,10 @@ class Solver : public SolverBase {
             launch_pdl(k_convert<R, S>, grid(N), 256, stream, N, kf, k_vc, 0);
             OTM_LAUNCH();
         }
+        return OTM_OK;
+    }
+    // Galerkin stencils of every level and the coarsest inverse (from k only)
+    otm_status coarse_hierarchy() {
         if (nlev == 1) {
             ++nl_;
             launch_pdl(k_stencil_from_k<R, C, S>, OTM_ROWS_CFG(rl(n, n * n, 128)), stream, n, kf, Al[0]);
@@ -825,6 +840,8 @@ class Solver : public SolverBase {
     int last_iters[3] = {0, 0, 0};
     bool use_graphs = true;
     cudaStream_t cap2 = nullptr;
+    cudaStream_t side = nullptr;              // side branch of the captured setup
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gx_first = nullptr, gx_pass = nullptr, gx_tail = nullptr;
     cudaGraphExec_t gx_setup = nullptr, gx_solve0 = nullptr;   // learned warm start: setup, then solve
     long long nlg_first = 0, nlg_pass = 0, nlg_body = 0, nlg_tail = 0, nlg_setup = 0, nlg_solve0 = 0;
@@ -951,8 +968,45 @@ if (zrm_ > 0)
             err = std::string("cudaStreamBeginCaptureToGraph: ") + cudaGetErrorString(e);
             return OTM_ECUDA;
         }
-        if (with_setup) st = enqueue_setup();
+        // With the setup, the coarse hierarchy (which needs only k) runs on a
+        // side branch of the graph, beside the macro loads and the pass's
+        // initial residual; the branches join before the PCG loop, whose
+        // first V-cycle is the first reader of the coarse levels.
+        bool forked = false;
+        if (with_setup) {
+            st = filter_simp();
+            if (st == OTM_OK && nlev > 1) {
+                e = cudaEventRecord(ev_fork, main);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+                if (e == cudaSuccess) {
+                    forked = true;
+                    stream = side;
+                    st = coarse_hierarchy();
+                    stream = main;
+                    if (st == OTM_OK) e = cudaEventRecord(ev_join, side);
+                }
+                if (st == OTM_OK && e == cudaSuccess) st = fine_loads();
+            } else if (st == OTM_OK) {
+                st = build_hierarchy();
+            }
+            if (st == OTM_OK && e == cudaSuccess) {
+                ++nl_;
+                launch_pdl(k_pcg_reset, 1, 1, stream, ps);
+                OTM_LAUNCH();
+            }
+            if (e != cudaSuccess && st == OTM_OK) {
+                err = std::string("graph capture of the setup branches: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
         if (st == OTM_OK) st = enqueue_pass_head(use_true);
+        if (st == OTM_OK && forked) {
+            e = cudaStreamWaitEvent(main, ev_join, 0);
+            if (e != cudaSuccess) {
+                err = std::string("graph capture of the setup join: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
         if (st == OTM_OK) {
             ++nl_;
             launch_pdl(k_set_cond, 1, 1, stream, ps, h, prm.cg_maxit);
