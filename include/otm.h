@@ -370,7 +370,8 @@ OTM_API otm_status otm_op_kappa_sens_noalloc(int dtype, int n, double penal, dou
                                              double kappa_out[6], void* s_f, void* stream);
 
 /* OC update (Sec. 3.3) of rho with gradient s under volume bound vstar:
- * writes rho_new, and *lambda_out (host, may be NULL). */
+ * writes rho_new (which may be the same array as rho), and *lambda_out
+ * (host, may be NULL). */
 OTM_API otm_status otm_op_oc_update(int dtype, int n, double vstar, double move,
                                     double damp, double rho_min, const void* rho,
                                     const void* s, void* rho_new, double* lambda_out,

@@ -57,11 +57,12 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
     Acc<C> a_rho, a_rhop;
     OTM_FOR_ROWS(row_, n * n) {
     const int y = row_ % n, z = row_ / n;
-    size_t zo[2 * RR + 1], yo[2 * RR + 1];
+    // 32-bit offsets: n^3 < 2^32 for every supported n
+    unsigned zo[2 * RR + 1], yo[2 * RR + 1];
 #pragma unroll
     for (int d = -RR; d <= RR; ++d) {
-        zo[d + RR] = (size_t)wrapd(z, sgn * d, n) * n * n;
-        yo[d + RR] = (size_t)wrapd(y, sgn * d, n) * n;
+        zo[d + RR] = (unsigned)wrapd(z, sgn * d, n) * (unsigned)n * (unsigned)n;
+        yo[d + RR] = (unsigned)wrapd(y, sgn * d, n) * (unsigned)n;
     }
     OTM_FOR_X(x, n) {
         const size_t v = (size_t)row_ * n + x;
@@ -77,7 +78,7 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
                 for (int dx = -RR; dx <= RR; ++dx) {
                     const int d2 = dx * dx + dy * dy + dz * dz;
                     if (d2 > 12) continue;
-                    acc += w[d2] * (C)in[(size_t)xo[dx + RR] + yo[dy + RR] + zo[dz + RR]];
+                    acc += w[d2] * (C)in[(unsigned)xo[dx + RR] + yo[dy + RR] + zo[dz + RR]];
                 }
         const C rf = acc * inv;
         out[v] = rf;
@@ -429,8 +430,7 @@ k_oc_search(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op
 
 template <class R>
 __global__ void __launch_bounds__(256)
-k_oc_apply(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op,
-           const DesignScalars* __restrict__ ds, R* __restrict__ rho_new) {
+k_oc_apply(size_t N, R* rho, const R* __restrict__ s, OcP op, const DesignScalars* __restrict__ ds) {
     pdl_enter();
     using C = typename St<R>::C;
     const int mode = ds->oc_mode;
@@ -446,7 +446,7 @@ k_oc_apply(size_t N, const R* __restrict__ rho, const R* __restrict__ s, OcP op,
             v = c * mu;
             v = v < lo ? lo : (v > hi ? hi : v);
         }
-        rho_new[e] = v;
+        rho[e] = v;   // in place: element e reads only its own old value
     }
 }
 

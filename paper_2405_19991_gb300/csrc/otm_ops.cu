@@ -232,7 +232,9 @@ otm_status oc_t(int n, double vstar, double move, double damp, double rho_min, c
         otm::k_oc_search<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, linear, rb,
                                                           otm::FinOcSearch{sc.ds, dN, linear, linear, 1.0 / damp});
     }
-    otm::k_oc_apply<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, (R*)rho_new);
+    // the update runs in place: start rho_new from rho (the same array is fine)
+    if (rho_new != rho) cudaMemcpyAsync(rho_new, rho, N * sizeof(R), cudaMemcpyDeviceToDevice, oc.st);
+    otm::k_oc_apply<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (R*)rho_new, (const R*)s, op, sc.ds);
     double lam = 0.0;
     cudaMemcpyAsync(&lam, &sc.ds->lambda, sizeof(double), cudaMemcpyDeviceToHost, oc.st);
     otm_status st = finish(oc.st, "otm_op_oc_update");

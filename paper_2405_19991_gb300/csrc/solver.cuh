@@ -157,7 +157,7 @@ class Solver : public SolverBase {
     long long nl_ = 0;   // kernel launches issued (for the step report)
 
     // fine fields
-    R *rho = nullptr, *rho_f = nullptr, *kf = nullptr, *s_f = nullptr, *s = nullptr, *rho_tmp = nullptr;
+    R *rho = nullptr, *rho_f = nullptr, *kf = nullptr, *s_f = nullptr, *s = nullptr;
     R *f = nullptr, *x = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     S *z = nullptr, *res0 = nullptr, *k_vc = nullptr;
     // coarse levels 1..nlev-1 (level 0 uses z / r / res0 / k_vc)
@@ -214,7 +214,7 @@ class Solver : public SolverBase {
         if (ev_join) cudaEventDestroy(ev_join);
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
-        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_tmp, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
+        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
                         partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
@@ -395,7 +395,6 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(kf, N));
         OTM_TRY(alloc(s_f, N));
         OTM_TRY(alloc(s, N));
-        OTM_TRY(alloc(rho_tmp, N));
         OTM_TRY(alloc(rho_save, N));
         OTM_TRY(alloc(f, 3 * N));
         OTM_TRY(alloc(x, 3 * N));
@@ -1432,9 +1431,7 @@ if (zrm_ > 0)
             OTM_LAUNCH();
         }
         ++nl_;
-        launch_pdl(k_oc_apply<R>, grid(N), 256, stream, N, rho, s, op, ds, rho_tmp);
-        ++nl_;
-        launch_pdl(k_convert<R, R>, grid(N), 256, stream, N, rho_tmp, rho, 0);
+        launch_pdl(k_oc_apply<R>, grid(N), 256, stream, N, rho, s, op, ds);
         OTM_LAUNCH();
         return OTM_OK;
     }
