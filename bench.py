@@ -178,6 +178,10 @@ def cpu_sample(wl, budget_s=25.0, chunk=10, steps=None, warmup=0, log=None):
     elif len(half) >= 2 and half[-1][1] < half[0][1]:
         rate = (math.log(half[-1][1]) - math.log(half[0][1])) / (half[-1][0] - half[0][0])
         n_needed = done + math.log(1e-6 / hist[-1][1]) / rate
+    elif 0.0 < hist[-1][1] < 1.0:
+        # a single chunk: the decay from the zero start (relative residual 1)
+        rate = math.log(hist[-1][1]) / hist[-1][0]
+        n_needed = done + math.log(1e-6 / hist[-1][1]) / rate
     else:
         n_needed = float("inf")
     t_oc = t_setup + 3.0 * n_needed * t_iter + t_tail
