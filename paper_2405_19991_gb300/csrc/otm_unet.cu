@@ -43,6 +43,17 @@ otm_status ufail(otm_status st, const std::string& m) {
         if (s_ != OTM_OK) return s_;                                                                 \
     } while (0)
 
+int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
 int elt_grid(size_t work) {
     static int sms = 0;
     if (!sms) {
@@ -85,8 +96,12 @@ otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const 
                  cudaStream_t st) {
     const size_t N = (size_t)n * n * n;
     if (otm::nn::conv3_tile_ok(n) && cout % 16 == 0 && cin % 16 == 0) {
-        const int tb = cout % 32 == 0 ? 32 : 16;
-        const dim3 grid((unsigned)((n / otm::nn::kBX) * (n / otm::nn::kBY) * (n / otm::nn::kBZ)), (unsigned)(cout / tb));
+        // 32 output channels per CTA, unless that leaves a small grid with
+        // fewer CTAs than SMs (the 16^3 level): then 16, for twice the CTAs
+        const long long bricks = (long long)(n / otm::nn::kBX) * (n / otm::nn::kBY) * (n / otm::nn::kBZ);
+        int tb = cout % 32 == 0 ? 32 : 16;
+        if (tb == 32 && bricks * (cout / 32) < sm_count()) tb = 16;
+        const dim3 grid((unsigned)bricks, (unsigned)(cout / tb));
         const size_t smem = otm::nn::conv3_tile_smem(tb);
         cudaError_t e = cudaSuccess;
 #define TILE_CASE(BN, RL)                                                                                  \
