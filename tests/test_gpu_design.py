@@ -271,6 +271,17 @@ def test_autotuned_configuration_is_valid(n, precision):
         assert us[chosen] == min(u for u in us if u > 0), cfg
         if n % 64 == 0:
             assert cfg["stencil_form"] == 0 and cfg["stencil_chunks"] >= 1, cfg
+            # the z-reuse stencil's chunk count is the wave cost model's choice:
+            # ceil(CTAs / resident slots) waves of (n / m + 1.5) planes, minimised
+            # over chunks of at least 4 planes (3 resident CTAs per SM)
+            import math
+            import torch
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            per_m, slots = 3 * (n // 64) * (n // 8), 3 * sms
+            cost = {m: math.ceil(per_m * m / slots) * (n / m + 1.5) for m in range(1, n // 4 + 1)
+                    if per_m * m <= 8 * sms}
+            best = min(cost.values())
+            assert cost[cfg["stencil_chunks"]] <= best * (1 + 1e-12), (cfg, best)
         info, st = otm.otm_step(ctx)
         assert st == otm.OTM_OK and max(info.resid) <= 1e-6 * 1.0001
     finally:
