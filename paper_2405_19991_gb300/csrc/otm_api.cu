@@ -1,5 +1,6 @@
 // C ABI of libotm.so (declared in include/otm.h): argument checking,
 // context lifecycle and dispatch to the per-precision solvers.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
@@ -262,12 +263,19 @@ otm_status otm_design_batch(int count, const otm_params* params, const float* co
     }
     int dev = 0;
     cudaGetDevice(&dev);
+    // largest designs first (longest-processing-time order), so the last
+    // designs to finish are small ones instead of a large one running alone;
+    // each design's result does not depend on when it runs
+    std::vector<int> order(count);
+    for (int d = 0; d < count; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return params[a].n > params[b].n; });
     std::atomic<int> next{0};
     auto work = [&]() {
         cudaSetDevice(dev);
         for (;;) {
-            const int d = next.fetch_add(1);
-            if (d >= count) break;
+            const int j = next.fetch_add(1);
+            if (j >= count) break;
+            const int d = order[j];
             if (stat[d] != OTM_OK) continue;
             otm_ctx* ctx = ctxs[d];
             otm_status st = OTM_OK;
