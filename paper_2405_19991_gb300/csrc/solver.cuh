@@ -171,6 +171,8 @@ class Solver : public SolverBase {
     // reductions and scalars
     double* partials = nullptr;
     unsigned int* counter = nullptr;
+    double* partials2 = nullptr;       // reductions of the graphs' second branch
+    unsigned int* counter2 = nullptr;
     PcgScalars* ps = nullptr;
     DesignScalars* ds = nullptr;
     PcgScalars* ps_h = nullptr;
@@ -212,10 +214,12 @@ class Solver : public SolverBase {
         if (side) cudaStreamDestroy(side);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_fork2) cudaEventDestroy(ev_fork2);
+        if (ev_join2) cudaEventDestroy(ev_join2);
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
         void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
-                        partials, counter, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
+                        partials, counter, partials2, counter2, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
         if (k_vc && (void*)k_vc != (void*)kf) cudaFree(k_vc);
@@ -238,6 +242,7 @@ class Solver : public SolverBase {
     }
 
     RedBuf rbuf() const { return RedBuf{partials, counter, max_blocks}; }
+    RedBuf rbuf2() const { return RedBuf{partials2, counter2, max_blocks}; }
     RowLaunch rl(int nx, int nrows, int thr = 256) const { return row_launch(nx, nrows, max_blocks, thr); }
     int tz_ = 0;   // z-planes per CTA of the tiled fine stencil (0: gather kernel)
     // First level of the cluster-run tail of the V-cycle: the first level >= 1
@@ -374,6 +379,8 @@ class Solver : public SolverBase {
         OTM_CU(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
         OTM_CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
         OTM_CU(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        OTM_CU(cudaEventCreateWithFlags(&ev_fork2, cudaEventDisableTiming));
+        OTM_CU(cudaEventCreateWithFlags(&ev_join2, cudaEventDisableTiming));
         {
             const char* ng = getenv("OTM_NO_GRAPH");
             use_graphs = !(ng && ng[0] == '1');
@@ -384,6 +391,8 @@ class Solver : public SolverBase {
                 cluster_maxn = atoi(cm);
                 maxn_fixed_ = true;
             }
+            const char* stv = getenv("OTM_SPEC_TENSOR");
+            spec_tensor_ = !(stv && stv[0] == '0');
             const char* at = getenv("OTM_AUTOTUNE");
             autotune_on_ = !(at && at[0] == '0');
             const char* tm = getenv("OTM_TAIL_MAXN");
@@ -491,6 +500,8 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(lam_d, kMaxLevels));
         OTM_TRY(alloc(partials, (size_t)max_blocks * kRedMaxVals));
         OTM_TRY(alloc(counter, 4));
+        OTM_TRY(alloc(partials2, (size_t)max_blocks * kRedMaxVals));
+        OTM_TRY(alloc(counter2, 4));
         OTM_TRY(alloc(ps, 1));
         OTM_TRY(alloc(ps_c, 1));
         OTM_TRY(alloc(ds, 1));
@@ -840,7 +851,7 @@ class Solver : public SolverBase {
     bool use_graphs = true;
     cudaStream_t cap2 = nullptr;
     cudaStream_t side = nullptr;              // side branch of the captured setup
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_fork2 = nullptr, ev_join2 = nullptr;
     cudaGraphExec_t gx_first = nullptr, gx_pass = nullptr, gx_tail = nullptr;
     cudaGraphExec_t gx_setup = nullptr, gx_solve0 = nullptr;   // learned warm start: setup, then solve
     long long nlg_first = 0, nlg_pass = 0, nlg_body = 0, nlg_tail = 0, nlg_setup = 0, nlg_solve0 = 0;
@@ -908,8 +919,8 @@ if (zrm_ > 0)
         return OTM_OK;
     }
     // design tail: tensor, sensitivity, filter transpose, Alg. 1, OC update
-    otm_status enqueue_tail() {
-        OTM_TRY(tensor_and_sens(true));
+    otm_status enqueue_tail(bool with_tensor = true) {
+        if (with_tensor) OTM_TRY(tensor_and_sens(true));
         ++nl_;
         launch_pdl(k_governor, 1, 1, stream, ds, 1.0 / (double)N, 0, 0.0);
         OTM_LAUNCH();
@@ -1042,7 +1053,36 @@ if (zrm_ > 0)
                 st = OTM_ECUDA;
             }
         }
+        // The design tail's tensor, sensitivity and filter transpose read only
+        // k, rho_f and this pass's iterate, so they run on a side branch beside
+        // the error-free convergence check (with their own reduction buffer).
+        // If the check asks for another pass, that pass's graph recomputes
+        // them from its own iterate, so the values the tail uses always belong
+        // to the last pass.
+        bool forked2 = false;
+        if (st == OTM_OK && spec_tensor_) {
+            e = cudaEventRecord(ev_fork2, main);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork2, 0);
+            if (e == cudaSuccess) {
+                forked2 = true;
+                stream = side;
+                st = tensor_and_sens(true, true);
+                stream = main;
+                if (st == OTM_OK) e = cudaEventRecord(ev_join2, side);
+            }
+            if (e != cudaSuccess && st == OTM_OK) {
+                err = std::string("graph capture of the tensor branch: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
         if (st == OTM_OK) st = enqueue_check();
+        if (st == OTM_OK && forked2) {
+            e = cudaStreamWaitEvent(main, ev_join2, 0);
+            if (e != cudaSuccess) {
+                err = std::string("graph capture of the tensor join: ") + cudaGetErrorString(e);
+                st = OTM_ECUDA;
+            }
+        }
         cudaGraph_t done = nullptr;
         e = cudaStreamEndCapture(main, &done);
         stream = main;
@@ -1065,13 +1105,17 @@ if (zrm_ > 0)
         return st;
     }
 
-    otm_status capture_tail() { return capture_seq(false, &gx_tail, &nlg_tail); }
+    // The pass graphs compute the tensor, the sensitivity and its filter
+    // transpose beside the convergence check (see capture_pass), so the
+    // tail graph starts at Alg. 1.
+    otm_status capture_tail() { return capture_seq(false, &gx_tail, &nlg_tail, !spec_tensor_); }
+    bool spec_tensor_ = true;   // OTM_SPEC_TENSOR=0: tensor and sensitivity in the tail graph instead
 
     // Capture the design tail (setup = false) or the solve setup (true).
-    otm_status capture_seq(bool setup, cudaGraphExec_t* out, long long* count) {
+    otm_status capture_seq(bool setup, cudaGraphExec_t* out, long long* count, bool tail_tensor = true) {
         const long long n0 = nl_;
         OTM_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeRelaxed));
-        otm_status st = setup ? enqueue_setup() : enqueue_tail();
+        otm_status st = setup ? enqueue_setup() : enqueue_tail(tail_tensor);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamEndCapture(stream, &g);
         if (st != OTM_OK) {
@@ -1403,9 +1447,10 @@ if (zrm_ > 0)
     }
 
     // kappa (and the objective) from x; optionally the sensitivity chain.
-    otm_status tensor_and_sens(bool with_sens) {
+    otm_status tensor_and_sens(bool with_sens, bool second_buffer = false) {
         ++nl_;
-        launch_pdl(k_kappa<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, rbuf(), FinKappa{ds, 1.0 / (double)N, 1});
+        launch_pdl(k_kappa<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, second_buffer ? rbuf2() : rbuf(),
+                   FinKappa{ds, 1.0 / (double)N, 1});
         OTM_LAUNCH();
         if (with_sens) {
             ++nl_;
