@@ -493,9 +493,6 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
 // and, when xpar >= 0, x%2 == xpar.  ZERO: the relaxed field starts at zero;
 // the pass also zeroes the other nodes of each 2x2 (y, z) cell, so no
 // separate clear is needed (only valid for group 0, xpar < 0).
-#ifndef OTM_GS_PRELOAD
-#define OTM_GS_PRELOAD 1
-#endif
 template <bool ZERO, class KT, class FT, class TT>
 __global__ void __launch_bounds__(256)
 k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __restrict__ f,
@@ -515,7 +512,6 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
         load_k8<KT, C>(k, g, kk);
         const C inv4k = C(1) / (C(4) * ksum8(kk));
         const size_t v = (size_t)(g.xc + g.yc + g.zc);
-#if OTM_GS_PRELOAD
         // all three load cases' neighbour values in flight before any sum
         // (the stores below could alias them as far as the compiler knows)
         C w[3][20];
@@ -523,17 +519,12 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
 #pragma unroll
             for (int i = 0; i < 3; ++i) nb_load<TT, C>(T + (size_t)i * N, g, w[i]);
         }
-#endif
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             TT* Ti = T + (size_t)i * N;
             const C fv = St<FT>::ld(f + (size_t)i * N, v);
             C nb = 0;
-#if OTM_GS_PRELOAD
             if (!ZERO) nb = nb_from<C>(w[i], kk);
-#else
-            if (!ZERO) nb = nb_sum<TT, C>(Ti, g, kk);
-#endif
             St<TT>::st(Ti, v, (C(12) * fv + nb) * inv4k);
             if (ZERO) {
                 const size_t y1 = (size_t)(y + 1) * n, z1 = (size_t)(z + 1) * n * n;
