@@ -8,18 +8,45 @@ namespace otm {
 
 // Filter weights by squared offset length: d_e(x_i, r) = max(0, r - |o|) for
 // |o| < r (Sec. 2.3, unit voxel volumes), offsets |o_d| <= R.
+// The parameter blocks carry FP32 copies of their values (filled on the
+// host by with_f32, the same roundings a kernel would make), so the FP32
+// kernels never convert from FP64 per thread: FP64 conversions and
+// arithmetic run at a small fraction of the FP32 rate on this part.
 struct FilterW {
     int R;
     int pad;
     double w[13];        // by dx^2 + dy^2 + dz^2 (R <= 2 -> at most 12)
     double inv_wsum;
+    float wf[13];
+    float inv_wsum_f;
 };
 
 struct SimpP {
     double penal, k_solid, k_void;
     int cubic;           // penal == 3
     int pad;
+    double sens_scale;   // (k_solid - k_void) / N of the sensitivity kernel
+    float k_void_f, dk_f, sens_scale_f;
 };
+
+// value of the compute type C: the FP32 copy for float, else the FP64 value
+template <class C>
+__host__ __device__ __forceinline__ C par(double d, float f) {
+    if (sizeof(C) == 4) return (C)f;
+    return (C)d;
+}
+inline FilterW with_f32(FilterW fw) {
+    for (int i = 0; i < 13; ++i) fw.wf[i] = (float)fw.w[i];
+    fw.inv_wsum_f = (float)fw.inv_wsum;
+    return fw;
+}
+inline SimpP with_f32(SimpP sp, size_t N) {
+    sp.sens_scale = (sp.k_solid - sp.k_void) / (double)N;
+    sp.k_void_f = (float)sp.k_void;
+    sp.dk_f = (float)(sp.k_solid - sp.k_void);
+    sp.sens_scale_f = (float)sp.sens_scale;
+    return sp;
+}
 
 template <class C>
 __device__ __forceinline__ C simp_pow(C r, const SimpP& sp) {
@@ -52,8 +79,8 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
     using C = typename St<R>::C;
     C w[13];
 #pragma unroll
-    for (int i = 0; i < 13; ++i) w[i] = (C)fw.w[i];
-    const C inv = (C)fw.inv_wsum;
+    for (int i = 0; i < 13; ++i) w[i] = par<C>(fw.w[i], fw.wf[i]);
+    const C inv = par<C>(fw.inv_wsum, fw.inv_wsum_f);
     Acc<C> a_rho, a_rhop;
     OTM_FOR_ROWS(row_, n * n) {
     const int y = row_ % n, z = row_ / n;
@@ -84,7 +111,7 @@ k_filter(int n, FilterW fw, int sgn, const R* __restrict__ in, R* __restrict__ o
         out[v] = rf;
         if (SIMP) {
             const C rp = simp_pow(rf, sp);
-            kout[v] = (C)sp.k_void + rp * (C)(sp.k_solid - sp.k_void);
+            kout[v] = par<C>(sp.k_void, sp.k_void_f) + rp * par<C>(sp.k_solid - sp.k_void, sp.dk_f);
             a_rho.add(in[v]);
             a_rhop.add(rp);
         }
@@ -214,7 +241,7 @@ k_sens(int n, const R* __restrict__ rho_f, const R* __restrict__ chi, const Desi
     C w[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) w[c] = (C)ds->w[c];
-    const C scale = (C)((sp.k_solid - sp.k_void) / (double)N);
+    const C scale = par<C>(sp.sens_scale, sp.sens_scale_f);
     OTM_FOR_ROWS(row_, n * n) {
     const int y = row_ % n, z = row_ / n;
     OTM_FOR_X(x, n) {
@@ -261,13 +288,20 @@ struct OcP {
     double move, damp, rho_min;
     int half;     // damp == 0.5
     int pad;
+    float move_f, rho_min_f;
 };
+inline OcP with_f32(OcP op) {
+    op.move_f = (float)op.move;
+    op.rho_min_f = (float)op.rho_min;
+    return op;
+}
 
 template <class C>
 __device__ __forceinline__ void oc_elem(C rho, C s, const OcP& op, C& lo, C& hi, C& c) {
-    lo = rho - (C)op.move;
-    if (lo < (C)op.rho_min) lo = (C)op.rho_min;
-    hi = rho + (C)op.move;
+    const C mv = par<C>(op.move, op.move_f), rmin = par<C>(op.rho_min, op.rho_min_f);
+    lo = rho - mv;
+    if (lo < rmin) lo = rmin;
+    hi = rho + mv;
     if (hi > C(1)) hi = C(1);
     const C B = s < C(0) ? -s : C(0);
     C bp;

@@ -69,14 +69,14 @@ otm_status scratch_address(int dev, unsigned char** out) {
     return OTM_OK;
 }
 
-otm::SimpP simp_p(double penal, double ks, double kv) {
+otm::SimpP simp_p(double penal, double ks, double kv, size_t N) {
     otm::SimpP sp;
     memset(&sp, 0, sizeof(sp));
     sp.penal = penal;
     sp.k_solid = ks;
     sp.k_void = kv;
     sp.cubic = penal == 3.0;
-    return sp;
+    return otm::with_f32(sp, N);
 }
 
 template <class R>
@@ -110,7 +110,7 @@ otm_status run(int n, double penal, double ks, double kv, const void* k, const v
     if (s_f) {
         e = cudaMemcpyAsync(&ds->w[0], w, 6 * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return fail(OTM_ECUDA, std::string("otm_op_kappa_sens_noalloc: ") + cudaGetErrorString(e));
-        otm::k_sens<R><<<OTM_ROWS_CFG(L), 0, st>>>(n, (const R*)rho_f, (const R*)chi, ds, simp_p(penal, ks, kv),
+        otm::k_sens<R><<<OTM_ROWS_CFG(L), 0, st>>>(n, (const R*)rho_f, (const R*)chi, ds, simp_p(penal, ks, kv, (size_t)n * n * n),
                                                     (R*)s_f);
     }
     double kap[6];

@@ -100,17 +100,17 @@ otm::FilterW filter_w(double rmin) {
                 if (d2 <= 12) wsum += fw.w[d2];
             }
     fw.inv_wsum = 1.0 / wsum;
-    return fw;
+    return otm::with_f32(fw);
 }
 
-otm::SimpP simp_p(double penal, double ks, double kv) {
+otm::SimpP simp_p(double penal, double ks, double kv, size_t N) {
     otm::SimpP sp;
     memset(&sp, 0, sizeof(sp));
     sp.penal = penal;
     sp.k_solid = ks;
     sp.k_void = kv;
     sp.cubic = penal == 3.0;
-    return sp;
+    return otm::with_f32(sp, N);
 }
 
 template <class R>
@@ -121,7 +121,7 @@ otm_status filter_simp_t(int n, double rmin, double penal, double ks, double kv,
     if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_filter_simp: scratch");
     otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
     otm::launch_filter<R, true>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), 1, (const R*)rho, (R*)rho_f, (R*)k,
-                                simp_p(penal, ks, kv), rb, otm::FinFilter{sc.ds});
+                                simp_p(penal, ks, kv, (size_t)n * n * n), rb, otm::FinFilter{sc.ds});
     return finish(oc.st, "otm_op_filter_simp");
 }
 
@@ -130,7 +130,7 @@ otm_status filter_t_t(int n, double rmin, const void* s_f, void* s, void* stream
     OpCtx oc(stream);
     otm::RedBuf rb{nullptr, nullptr, 0};
     otm::launch_filter<R, false>(oc.rows(n, n * n), oc.st, n, filter_w(rmin), -1, (const R*)s_f, (R*)s, (R*)nullptr,
-                                 simp_p(3, 1, 1e-3), rb, otm::FinFilter{nullptr});
+                                 simp_p(3, 1, 1e-3, (size_t)n * n * n), rb, otm::FinFilter{nullptr});
     return finish(oc.st, "otm_op_filter_transpose");
 }
 
@@ -198,7 +198,7 @@ otm_status kappa_sens_t(int n, double penal, double ks, double kv, const void* k
     if (s_f) {
         cudaMemcpyAsync(&sc.ds->w[0], w, 6 * sizeof(double), cudaMemcpyHostToDevice, oc.st);
         otm::k_sens<R><<<OTM_ROWS_CFG(oc.rows(n, n * n)), 0, oc.st>>>(n, (const R*)rho_f, (const R*)chi, sc.ds,
-                                                     simp_p(penal, ks, kv), (R*)s_f);
+                                                     simp_p(penal, ks, kv, (size_t)n * n * n), (R*)s_f);
     }
     double kap[6];
     cudaMemcpyAsync(kap, &sc.ds->kappa[0], 6 * sizeof(double), cudaMemcpyDeviceToHost, oc.st);
@@ -223,6 +223,7 @@ otm_status oc_t(int n, double vstar, double move, double damp, double rho_min, c
     op.damp = damp;
     op.rho_min = rho_min;
     op.half = damp == 0.5;
+    op = otm::with_f32(op);
     otm::k_governor<<<1, 1, 0, oc.st>>>(sc.ds, 1.0 / dN, 1, vstar);
     otm::k_oc_prep<R><<<oc.grid(N), 256, 0, oc.st>>>(N, (const R*)rho, (const R*)s, op, sc.ds, rb,
                                                     otm::FinOcPrep{sc.ds, dN});

@@ -508,15 +508,17 @@ class Solver : public SolverBase {
         OTM_CU(cudaMallocHost((void**)&ps_h, sizeof(PcgScalars)));
         OTM_CU(cudaMallocHost((void**)&ds_h, sizeof(DesignScalars)));
 
-        fw = make_filter(pin.rmin);
+        fw = with_f32(make_filter(pin.rmin));
         sp.penal = pin.penal;
         sp.k_solid = pin.k_solid;
         sp.k_void = pin.k_void;
         sp.cubic = pin.penal == 3.0;
+        sp = with_f32(sp, N);
         op.move = pin.move;
         op.damp = pin.damp;
         op.rho_min = pin.rho_min;
         op.half = pin.damp == 0.5;
+        op = with_f32(op);
 
         memset(ds_h, 0, sizeof(DesignScalars));
         gov_init.df = 1.0;
