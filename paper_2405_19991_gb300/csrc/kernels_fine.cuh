@@ -208,7 +208,7 @@ __device__ __forceinline__ void nd_sum_exact(const C* __restrict__ hi, const C* 
     const C hv = hi[v], lv = lo ? lo[v] : C(0);
     C s = 0, c = 0;
     auto term = [&](C kv, C d) {
-        const C p = kv * d;
+        const C p = mul_rn(kv, d);
         const C pe = fma(kv, d, -p);
         C t, e;
         two_sum(s, p, t, e);
@@ -476,8 +476,9 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
             // r = f + nd / 12, nd = s + c; one rounding of the final sum
             const C fv = f[o + v];
             C t, e;
-            two_sum(fv, s * C(1.0 / 12.0), t, e);
-            const C rv = t + (e + c * C(1.0 / 12.0) + fma(s, C(1.0 / 12.0), -(s * C(1.0 / 12.0))));
+            const C s12 = mul_rn(s, C(1.0 / 12.0));
+            two_sum(fv, s12, t, e);
+            const C rv = t + (e + c * C(1.0 / 12.0) + fma(s, C(1.0 / 12.0), -s12));
             acc[i].add_prod(rv, rv);
             acc[3 + i].add_prod(fv, fv);
         }
@@ -746,7 +747,7 @@ k_update_xr(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r, 
             const size_t o = (size_t)i * N + v;
             const C pv = p[o];
             if (xl) {
-                const C ap = a * pv;
+                const C ap = mul_rn(a, pv);
                 const C ep = fma(a, pv, -ap);
                 C sh, se;
                 two_sum((C)x[o], ap, sh, se);
@@ -795,7 +796,7 @@ k_update_xr4(size_t N, R* __restrict__ x, R* __restrict__ xl, R* __restrict__ r,
                 Q4<C> lv = ld4(xl, o);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const C ap = a * pv.v[t];
+                    const C ap = mul_rn(a, pv.v[t]);
                     const C ep = fma(a, pv.v[t], -ap);
                     C sh, se;
                     two_sum(xv.v[t], ap, sh, se);

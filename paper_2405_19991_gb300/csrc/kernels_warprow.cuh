@@ -18,6 +18,11 @@ namespace otm {
 
 inline bool warprow_ok(int n) { return n >= 128 && n % 128 == 0; }
 
+// CTAs per SM the two residual kernels are compiled for (3: 80 registers).
+#ifndef OTM_WR_MINB
+#define OTM_WR_MINB 3
+#endif
+
 // Values of one row at x0+4l-1 .. x0+4l+4 (six floats).
 template <class T>
 __device__ __forceinline__ void row6(const T* __restrict__ F, size_t ro, int xb, int n, int lane, bool whole,
@@ -35,14 +40,15 @@ __device__ __forceinline__ void row6(const T* __restrict__ F, size_t ro, int xb,
     }
 }
 
-// Row offsets of the 3 x 3 (y, z) neighbourhood: ro[dz+1][dy+1].
-__device__ __forceinline__ void row_offsets(int n, int y, int z, size_t (&ro)[3][3]) {
-    const size_t nn = (size_t)n * n;
+// Row offsets of the 3 x 3 (y, z) neighbourhood: ro[dz+1][dy+1].  32-bit:
+// the solver's grids have n <= 512, so an offset within a field is < 2^28.
+__device__ __forceinline__ void row_offsets(int n, int y, int z, unsigned (&ro)[3][3]) {
+    const unsigned nn = (unsigned)n * n;
 #pragma unroll
     for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy)
-            ro[dz + 1][dy + 1] = (size_t)wrapd(y, dy, n) * n + (size_t)wrapd(z, dz, n) * nn;
+            ro[dz + 1][dy + 1] = (unsigned)wrapd(y, dy, n) * n + (unsigned)wrapd(z, dz, n) * nn;
 }
 
 template <class KT>
@@ -161,10 +167,36 @@ __device__ __forceinline__ void pair_row(const float* __restrict__ xh, const flo
         for (int t = 0; t < 6; ++t) vl[t] = 0.f;
 }
 
+// The error-free check processes the lane's four nodes as two pairs, nodes
+// (0, 2) and (1, 3), one packed FP32x2 instruction per pair.  Pair jp at x-offset dx reads the
+// row value of node jp + dx and of node jp + 2 + dx: P[1 + jp + dx] with
+// P[t] = (v[t], v[t + 2]).
+__device__ __forceinline__ void pair_cols(const float (&v)[6], float2 (&P)[4]) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) P[t] = make_float2(v[t], v[t + 2]);
+}
+
+// The pair differences of row (dy, dz) for both node pairs and the three
+// x-offsets: D[jp][dx + 1] = (u_w - u_v) of nodes jp and jp + 2, each
+// rounded once (df_diff on both lanes).
+__device__ __forceinline__ void row_diffs(const float (&vh)[6], const float (&vl)[6], const float2 (&ch)[2],
+                                          const float2 (&cl)[2], float2 (&D)[2][3]) {
+    float2 PH[4], PL[4];
+    pair_cols(vh, PH);
+    pair_cols(vl, PL);
+#pragma unroll
+    for (int jp = 0; jp < 2; ++jp)
+#pragma unroll
+        for (int t = 0; t < 3; ++t) D[jp][t] = df_diff2(PH[jp + t], PL[jp + t], ch[jp], cl[jp]);
+}
+
+// Lane j of the pair layout: node j is lane j >> 1 of pair j & 1.
+__device__ __forceinline__ float pair_lane(const float2& p, int j) { return (j >> 1) ? p.y : p.x; }
+
 // r = f - K (hi + lo) (residual of the FP32-pair iterate; lo may be null),
 // reducing ||r||^2 and ||f||^2 into FinInit.
 template <class Fin>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, OTM_WR_MINB)
 k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
                  const float* __restrict__ f, float* __restrict__ r, RedBuf rb, Fin fin) {
     pdl_enter();
@@ -180,7 +212,7 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
         const int row = (int)(w / wpr);
         const int y = row % n, z = row / n;
         const int xb = seg * 128 + 4 * lane;
-        size_t ro[3][3];
+        unsigned ro[3][3];
         row_offsets(n, y, z, ro);
         float kr[2][2][6];
         load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
@@ -201,7 +233,9 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
                     float vh[6], vl[6];
                     pair_row(xh + fo, xl ? xl + fo : nullptr, ro[dz + 1][dy + 1], xb, n, lane, whole, vh, vl);
                     // the three x-neighbours of node j as pair differences,
-                    // placed where add_row reads them for node j
+                    // placed where add_row reads them for node j (scalar: the
+                    // packed form of these differences measured 123 against
+                    // 115 us here, its pair moves costing more than it saves)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         float d[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -231,9 +265,9 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
 
 // ||f - K (hi + lo)||^2 with error-free element terms (see k_true_residual):
 // each of the 32 terms k_e (u_w - u_v) of a node is formed with TwoProduct
-// and summed with TwoSum.
+// and summed with TwoSum, two nodes per packed instruction.
 template <class Fin>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, OTM_WR_MINB)
 k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
                    const float* __restrict__ f, RedBuf rb, Fin fin) {
     pdl_enter();
@@ -249,7 +283,7 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
         const int row = (int)(w / wpr);
         const int y = row % n, z = row / n;
         const int xb = seg * 128 + 4 * lane;
-        size_t ro[3][3];
+        unsigned ro[3][3];
         row_offsets(n, y, z, ro);
         float kr[2][2][6];
         load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
@@ -260,7 +294,11 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
             const Q4<float> ch = ld4f(xh + fo, vb);
             Q4<float> cl{{0.f, 0.f, 0.f, 0.f}};
             if (xl) cl = ld4f(xl + fo, vb);
-            float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+            const float2 ch2[2] = {make_float2(ch.v[0], ch.v[2]), make_float2(ch.v[1], ch.v[3])};
+            const float2 cl2[2] = {make_float2(cl.v[0], cl.v[2]), make_float2(cl.v[1], cl.v[3])};
+            // running sums s + c of the pair (jp, jp + 2), both lanes at once
+            float2 S[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            float2 Cc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -268,39 +306,44 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
                     if (dy == 0 && dz == 0) continue;
                     float vh[6], vl[6];
                     pair_row(xh + fo, xl ? xl + fo : nullptr, ro[dz + 1][dy + 1], xb, n, lane, whole, vh, vl);
+                    float2 Dr[2][3];
+                    row_diffs(vh, vl, ch2, cl2, Dr);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        auto term = [&](float kv, float dv) {
-                            const float p = kv * dv;
-                            const float pe = fmaf(kv, dv, -p);
-                            float t, e;
-                            two_sum(s[j], p, t, e);
-                            s[j] = t;
-                            c[j] += e + pe;
+                    for (int jp = 0; jp < 2; ++jp) {
+                        // TwoProduct per lane, TwoSum of the pair's running sums
+                        auto term = [&](float k0, float k1, float2 d) {
+                            const float2 p = make_float2(__fmul_rn(k0, d.x), __fmul_rn(k1, d.y));
+                            const float2 pe = make_float2(fmaf(k0, d.x, -p.x), fmaf(k1, d.y, -p.y));
+                            float2 t, e;
+                            two_sum2(S[jp], p, t, e);
+                            S[jp] = t;
+                            Cc[jp] = __fadd2_rn(Cc[jp], __fadd2_rn(e, pe));
                         };
-                        auto D = [&](int dx) -> float { return df_diff(vh[1 + j + dx], vl[1 + j + dx], ch.v[j], cl.v[j]); };
-                        auto K = [&](int cc, int b, int a) -> float { return kr[cc][b][1 + j - a]; };
+                        auto D = [&](int dx) -> float2 { return Dr[jp][dx + 1]; };
+                        // conductivity k_{cc,b,a} of nodes jp and jp + 2
+                        auto K0 = [&](int cc, int b, int a) -> float { return kr[cc][b][1 + jp - a]; };
+                        auto K1 = [&](int cc, int b, int a) -> float { return kr[cc][b][3 + jp - a]; };
                         if (dy != 0 && dz != 0) {
                             const int b = (1 - dy) / 2, cc = (1 - dz) / 2;
-                            const float d0 = D(0);
-                            term(K(cc, b, 0), D(1));
-                            term(K(cc, b, 1), D(-1));
-                            term(K(cc, b, 0), d0);
-                            term(K(cc, b, 1), d0);
+                            const float2 d0 = D(0);
+                            term(K0(cc, b, 0), K1(cc, b, 0), D(1));
+                            term(K0(cc, b, 1), K1(cc, b, 1), D(-1));
+                            term(K0(cc, b, 0), K1(cc, b, 0), d0);
+                            term(K0(cc, b, 1), K1(cc, b, 1), d0);
                         } else if (dy != 0) {
                             const int b = (1 - dy) / 2;
-                            const float dp = D(1), dm = D(-1);
-                            term(K(0, b, 0), dp);
-                            term(K(1, b, 0), dp);
-                            term(K(0, b, 1), dm);
-                            term(K(1, b, 1), dm);
+                            const float2 dp = D(1), dm = D(-1);
+                            term(K0(0, b, 0), K1(0, b, 0), dp);
+                            term(K0(1, b, 0), K1(1, b, 0), dp);
+                            term(K0(0, b, 1), K1(0, b, 1), dm);
+                            term(K0(1, b, 1), K1(1, b, 1), dm);
                         } else {
                             const int cc = (1 - dz) / 2;
-                            const float dp = D(1), dm = D(-1);
-                            term(K(cc, 0, 0), dp);
-                            term(K(cc, 1, 0), dp);
-                            term(K(cc, 0, 1), dm);
-                            term(K(cc, 1, 1), dm);
+                            const float2 dp = D(1), dm = D(-1);
+                            term(K0(cc, 0, 0), K1(cc, 0, 0), dp);
+                            term(K0(cc, 1, 0), K1(cc, 1, 0), dp);
+                            term(K0(cc, 0, 1), K1(cc, 0, 1), dm);
+                            term(K0(cc, 1, 1), K1(cc, 1, 1), dm);
                         }
                     }
                 }
@@ -308,9 +351,11 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float fvj = fv.v[j];
+                const float sj = pair_lane(S[j & 1], j), cj = pair_lane(Cc[j & 1], j);
+                const float s12 = __fmul_rn(sj, 1.0f / 12.0f);
                 float t, e;
-                two_sum(fvj, s[j] * (1.0f / 12.0f), t, e);
-                const float rv = t + (e + c[j] * (1.0f / 12.0f) + fmaf(s[j], 1.0f / 12.0f, -(s[j] * (1.0f / 12.0f))));
+                two_sum(fvj, s12, t, e);
+                const float rv = t + (e + cj * (1.0f / 12.0f) + fmaf(sj, 1.0f / 12.0f, -s12));
                 acc[i].add_prod(rv, rv);
                 acc[3 + i].add_prod(fvj, fvj);
             }

@@ -45,15 +45,6 @@ inline int stencil_choice() {
     return c;
 }
 
-// a - b on both lanes (one packed FP32 subtract; bitwise a + (-b))
-__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
-    unsigned long long d;
-    asm("sub.rn.f32x2 %0, %1, %2;"
-        : "=l"(d)
-        : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
-    return *reinterpret_cast<const float2*>(&d);
-}
-
 #ifndef OTM_X2_MINB
 #define OTM_X2_MINB 2
 #endif

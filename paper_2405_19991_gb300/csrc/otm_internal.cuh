@@ -290,15 +290,15 @@ template <> struct Acc<double> {
 template <> struct Acc<float> {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float x) {
-        float t = s + x;
+        float t = __fadd_rn(s, x);
         float bp = t - s;
         c += (s - (t - bp)) + (x - bp);
         s = t;
     }
     __device__ __forceinline__ void add_prod(float a, float b) {
-        float p = a * b;
+        float p = __fmul_rn(a, b);
         float pe = fmaf(a, b, -p);
-        float t = s + p;
+        float t = __fadd_rn(s, p);
         float bp = t - s;
         c += ((s - (t - bp)) + (p - bp)) + pe;
         s = t;
@@ -306,12 +306,37 @@ template <> struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-// Error-free transformations (Knuth TwoSum, FMA TwoProduct).
+// Error-free transformations (Knuth TwoSum, FMA TwoProduct).  The build
+// lets the compiler fuse a multiply and a dependent add into one FMA, which
+// would silently break both transformations (the rounded product p is then
+// not the value the error term assumes).  Products that feed them are formed
+// with mul_rn and the leading sum with add_rn, neither of which is fused.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 template <class C>
 __device__ __forceinline__ void two_sum(C a, C b, C& s, C& e) {
-    s = a + b;
+    s = add_rn(a, b);
     const C bp = s - a;
     e = (a - (s - bp)) + (b - bp);
+}
+
+// a - b on both lanes (one packed FP32 subtract; bitwise a + (-b))
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
+    return *reinterpret_cast<const float2*>(&d);
+}
+
+// TwoSum on both lanes of a pair: each lane runs the scalar sequence, so the
+// result is bitwise that of two two_sum calls.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+    s = __fadd2_rn(a, b);
+    const float2 bp = f2_sub(s, a);
+    e = __fadd2_rn(f2_sub(a, f2_sub(s, bp)), f2_sub(b, bp));
 }
 
 // A value kept as an unevaluated sum hi + lo (double-float when C = float).
@@ -320,6 +345,15 @@ __device__ __forceinline__ C df_diff(C hw, C lw, C hv, C lv) {   // (hw + lw) - 
     C s, e;
     two_sum(hw, -hv, s, e);
     return s + ((lw - lv) + e);
+}
+// df_diff on both lanes.  two_sum(hw, -hv) is written with subtractions:
+// hw + (-hv) = hw - hv and (-hv) - bp = -(hv + bp) exactly, so each lane is
+// bitwise the scalar df_diff.
+__device__ __forceinline__ float2 df_diff2(float2 hw, float2 lw, float2 hv, float2 lv) {
+    const float2 s = f2_sub(hw, hv);
+    const float2 bp = f2_sub(s, hw);
+    const float2 e = f2_sub(f2_sub(hw, f2_sub(s, bp)), __fadd2_rn(hv, bp));
+    return __fadd2_rn(s, __fadd2_rn(f2_sub(lw, lv), e));
 }
 
 // ---------------------------------------------------------------------------
@@ -406,7 +440,7 @@ __device__ bool grid_reduce(const double (&v)[NV], const RedBuf& rb, double* out
 // TwoSum error term does not depend on the operand order), so butterfly
 // lanes agree and the result is the same for the same grid.
 __device__ __forceinline__ void ff_add(float& s, float& c, float s2, float c2) {
-    const float t = s + s2;
+    const float t = __fadd_rn(s, s2);
     const float bp = t - s;
     const float e = (s - (t - bp)) + (s2 - bp);
     c = (c + c2) + e;
