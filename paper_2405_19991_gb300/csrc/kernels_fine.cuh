@@ -491,11 +491,11 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
 }
 
 // Fine Gauss-Seidel launch settings: the L2 prefetch of the next row
-// (OTM_GS_PF, default on) and a cap on the grid (OTM_GS_GRID blocks; 0 = the
-// row-mapped default).
-inline int gs_prefetch_setting() {
+// (OTM_GS_PF=0|1 overrides the caller's default) and a cap on the grid
+// (OTM_GS_GRID blocks; 0 = the caller's choice).
+inline int gs_prefetch_setting(bool dflt) {
     const char* e = getenv("OTM_GS_PF");
-    return e ? (atoi(e) != 0) : 1;
+    return e ? (atoi(e) != 0) : (dflt ? 1 : 0);
 }
 inline int gs_grid_cap() {
     const char* e = getenv("OTM_GS_GRID");

@@ -373,6 +373,7 @@ class Solver : public SolverBase {
         // (256^3 FP32 design iteration: 16.19 ms against 16.62 ms with the
         // 8-per-SM grid's 2.67 waves and 16.29 ms with one wave; at 128^3 two
         // waves measured slower, 2.877 against 2.845 ms, so it keeps 8 per SM).
+        gs_pf_ = gs_prefetch_setting(pin.n >= 256);
         gs_cap_ = gs_grid_cap();
         if (gs_cap_ == 0 && pin.n >= 256) {
             const dim3 blk = rl(pin.n, (pin.n / 2) * (pin.n / 2)).block;
@@ -730,9 +731,10 @@ class Solver : public SolverBase {
         launch_pdl(k_gs_fine<false, S, R, S>, gs_grid(), rl(n, (n / 2) * (n / 2)).block, stream, n, gidx, -1, k_vc, r,
                    z, gs_pf_);
     }
-    // L2 prefetch of each block's next row (measured at 256^3: a group pass
-    // 220 -> 170 us; no change at 128^3, where the fields stay in L2)
-    int gs_pf_ = gs_prefetch_setting();
+    // L2 prefetch of each block's next row where the fields outgrow L2
+    // (measured at 256^3: a group pass 220 -> 170 us; at 128^3, where the
+    // fields stay in L2, the design iteration did not change)
+    int gs_pf_ = 0;
     int gs_cap_ = 0;   // grid cap of the fine Gauss-Seidel pass, 0: the row-mapped grid
     int gs_grid() const {
         const RowLaunch c = rl(n, (n / 2) * (n / 2));
