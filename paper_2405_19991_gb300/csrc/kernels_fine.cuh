@@ -490,13 +490,8 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
     }
 }
 
-// Fine Gauss-Seidel launch settings: the L2 prefetch of the next row
-// (OTM_GS_PF=0|1 overrides the caller's default) and a cap on the grid
-// (OTM_GS_GRID blocks; 0 = the caller's choice).
-inline int gs_prefetch_setting(bool dflt) {
-    const char* e = getenv("OTM_GS_PF");
-    return e ? (atoi(e) != 0) : (dflt ? 1 : 0);
-}
+// Grid of the fine Gauss-Seidel pass: OTM_GS_GRID blocks overrides the
+// caller's choice (0 = keep it).
 inline int gs_grid_cap() {
     const char* e = getenv("OTM_GS_GRID");
     return e ? std::max(atoi(e), 0) : 0;
@@ -505,13 +500,11 @@ inline int gs_grid_cap() {
 // One Gauss-Seidel pass over the nodes with y%2 == group&1, z%2 == group>>1
 // and, when xpar >= 0, x%2 == xpar.  ZERO: the relaxed field starts at zero;
 // the pass also zeroes the other nodes of each 2x2 (y, z) cell, so no
-// separate clear is needed (only valid for group 0, xpar < 0).  prefetch:
-// before each row, have L2 fetch the lines of the block's next row (group
-// passes only).
+// separate clear is needed (only valid for group 0, xpar < 0).
 template <bool ZERO, class KT, class FT, class TT>
 __global__ void __launch_bounds__(256)
 k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __restrict__ f,
-          TT* __restrict__ T, int prefetch) {
+          TT* __restrict__ T) {
     pdl_enter();
     using C = typename St<TT>::C;
     const size_t N = (size_t)n * n * n;
@@ -520,33 +513,8 @@ k_gs_fine(int n, int group, int xpar, const KT* __restrict__ k, const FT* __rest
     const int yo = group & 1, zo = group >> 1;
     OTM_FOR_ROWS(grow, h * h) {
     const int y = 2 * (grow % h) + yo, z = 2 * (grow / h) + zo;
-    const int gnext = grow + gridDim.x * blockDim.y;
     OTM_FOR_X(xi, nx) {
         const int x = xpar < 0 ? xi : 2 * xi + xpar;
-        if (prefetch && xpar < 0 && gnext < h * h) {
-            // Ask L2 for the lines this warp reads at the same x of its next
-            // row: one 32-node segment of each of the 24 neighbour rows of
-            // the three load cases, the 4 conductivity rows and the 3 load
-            // rows, one line per lane (no registers held, nothing waited on).
-            const int lane = threadIdx.x & 31;
-            const int x0 = x - lane;
-            const int yn = 2 * (gnext % h) + yo, zn = 2 * (gnext / h) + zo;
-            const size_t nn = (size_t)n * n;
-            const void* pa = nullptr;
-            if (lane < 24) {
-                const int r = lane & 7;
-                const int rr = r < 4 ? r : r + 1;              // skip the centre row
-                const int dy = rr % 3 - 1, dz = rr / 3 - 1;
-                if (!ZERO)   // the zeroing pass reads no neighbours
-                    pa = T + (size_t)(lane >> 3) * N + (size_t)wrapd(yn, dy, n) * n + (size_t)wrapd(zn, dz, n) * nn + x0;
-            } else if (lane < 28) {
-                const int b = (lane - 24) & 1, c = (lane - 24) >> 1;
-                pa = k + (size_t)wrapd(yn, -b, n) * n + (size_t)wrapd(zn, -c, n) * nn + x0;
-            } else if (lane < 31) {
-                pa = f + (size_t)(lane - 28) * N + (size_t)yn * n + (size_t)zn * nn + x0;
-            }
-            if (pa) asm volatile("prefetch.global.L2 [%0];" ::"l"(pa));
-        }
         const Nbr g = make_nbr(x, y, z, n);
         C kk[2][2][2];
         load_k8<KT, C>(k, g, kk);

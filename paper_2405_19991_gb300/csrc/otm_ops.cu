@@ -177,10 +177,10 @@ otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* 
     if (colour >= 8) {   // a group pass (both x parities), as the solver runs it
         const int group = colour - 8;
         otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n, (n / 2) * (n / 2))), 0, oc.st>>>(
-            n, group, -1, (const R*)k, (const R*)f, (R*)T, otm::gs_prefetch_setting(n >= 256));
+            n, group, -1, (const R*)k, (const R*)f, (R*)T);
     } else {
         otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n / 2, (n / 2) * (n / 2))), 0, oc.st>>>(
-            n, colour >> 1, colour & 1, (const R*)k, (const R*)f, (R*)T, 0);
+            n, colour >> 1, colour & 1, (const R*)k, (const R*)f, (R*)T);
     }
     return finish(oc.st, "otm_op_gs_colour");
 }

@@ -369,11 +369,10 @@ class Solver : public SolverBase {
         if (std::is_same<R, float>::value && stencil_choice() == 3) x2tz_ = x2_tz(pin.n, sm_count, max_blocks);
         wr_ = warprow_ok(pin.n) && std::is_same<R, float>::value;
         // Fine Gauss-Seidel grid: where the fields outgrow L2 (n >= 256) the
-        // prefetching pass runs best as two full waves of resident blocks
-        // (256^3 FP32 design iteration: 16.19 ms against 16.62 ms with the
-        // 8-per-SM grid's 2.67 waves and 16.29 ms with one wave; at 128^3 two
-        // waves measured slower, 2.877 against 2.845 ms, so it keeps 8 per SM).
-        gs_pf_ = gs_prefetch_setting(pin.n >= 256);
+        // pass runs best as two full waves of resident blocks (256^3 design
+        // iteration: 15.66 ms FP32 and 14.98 ms with the BF16 V-cycle, against
+        // 16.06 and 15.39 ms with the 8-per-SM grid's 2.67 waves; one wave
+        // 15.67 ms).  At 128^3 it keeps 8 blocks per SM.
         gs_cap_ = gs_grid_cap();
         if (gs_cap_ == 0 && pin.n >= 256) {
             const dim3 blk = rl(pin.n, (pin.n / 2) * (pin.n / 2)).block;
@@ -729,12 +728,8 @@ class Solver : public SolverBase {
     // One fine-grid Gauss-Seidel group pass.
     void fine_gs_pass(int gidx) {
         launch_pdl(k_gs_fine<false, S, R, S>, gs_grid(), rl(n, (n / 2) * (n / 2)).block, stream, n, gidx, -1, k_vc, r,
-                   z, gs_pf_);
+                   z);
     }
-    // L2 prefetch of each block's next row where the fields outgrow L2
-    // (measured at 256^3: a group pass 220 -> 170 us; at 128^3, where the
-    // fields stay in L2, the design iteration did not change)
-    int gs_pf_ = 0;
     int gs_cap_ = 0;   // grid cap of the fine Gauss-Seidel pass, 0: the row-mapped grid
     int gs_grid() const {
         const RowLaunch c = rl(n, (n / 2) * (n / 2));
@@ -751,8 +746,7 @@ class Solver : public SolverBase {
         }
         // level 0, pre-smooth: groups {0,1}, {2,3}, {4,5}, {6,7}
         ++nl_;
-        launch_pdl(k_gs_fine<true, S, R, S>, gs_grid(), rl(n, (n / 2) * (n / 2)).block, stream, n, 0, -1, k_vc, r, z,
-                   gs_pf_);
+        launch_pdl(k_gs_fine<true, S, R, S>, gs_grid(), rl(n, (n / 2) * (n / 2)).block, stream, n, 0, -1, k_vc, r, z);
         for (int gidx = 1; gidx < 4; ++gidx) {
             ++nl_;
             fine_gs_pass(gidx);
