@@ -168,9 +168,9 @@ __device__ __forceinline__ void pair_row(const float* __restrict__ xh, const flo
 }
 
 // The error-free check processes the lane's four nodes as two pairs, nodes
-// (0, 2) and (1, 3), one packed FP32x2 instruction per pair.  Pair jp at x-offset dx reads the
-// row value of node jp + dx and of node jp + 2 + dx: P[1 + jp + dx] with
-// P[t] = (v[t], v[t + 2]).
+// (0, 2) and (1, 3), one packed FP32x2 instruction per pair.  Pair jp at
+// x-offset dx reads the row values of nodes jp + dx and jp + 2 + dx:
+// P[1 + jp + dx] with P[t] = (v[t], v[t + 2]).
 __device__ __forceinline__ void pair_cols(const float (&v)[6], float2 (&P)[4]) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) P[t] = make_float2(v[t], v[t + 2]);
