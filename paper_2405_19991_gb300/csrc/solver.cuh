@@ -731,6 +731,18 @@ class Solver : public SolverBase {
                    z);
     }
     int gs_cap_ = 0;   // grid cap of the fine Gauss-Seidel pass, 0: the row-mapped grid
+    // Threads per block of a standalone coarse level's colour passes: 256,
+    // or 64 where 256-thread blocks would not cover every SM and a colour's
+    // row fills whole warps (the 64^3 level at n = 128 and 256: 512 blocks
+    // instead of 128).  OTM_CGS_THREADS overrides.
+    int cgs_thr(int m) const {
+        const char* e = getenv("OTM_CGS_THREADS");
+        if (e) {
+            const int t = atoi(e);
+            return t >= 32 && t <= 256 && t % 32 == 0 ? t : 256;
+        }
+        return (m / 2) % 32 == 0 && rl(m / 2, (m / 2) * (m / 2)).grid < sm_count ? 64 : 256;
+    }
     int gs_grid() const {
         const RowLaunch c = rl(n, (n / 2) * (n / 2));
         return gs_cap_ > 0 && gs_cap_ < c.grid ? gs_cap_ : c.grid;
@@ -770,10 +782,10 @@ class Solver : public SolverBase {
                 Tcur = T2l[l];
             } else {
                 ++nl_;
-                launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
+                launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
                 for (int c = 1; c < 8; ++c) {
                     ++nl_;
-                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
                 }
             }
             ++nl_;
@@ -835,7 +847,7 @@ class Solver : public SolverBase {
             } else {
                 for (int c = 7; c >= 0; --c) {
                     ++nl_;
-                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
                 }
             }
             OTM_LAUNCH();
