@@ -3,8 +3,7 @@ update with the adaptive volume bound.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Readings of points where the paper is silent or garbled (each is also listed
-in DESIGN.md):
+Readings of points where the paper is silent or garbled:
 
 * Filter weight (Sec. 2.3): d_e(x_i, r) = max(0, r - |x_i - x_e|) over voxel
   centroids at minimum-image periodic distance, neighbourhood |x_i - x_e| < r,
