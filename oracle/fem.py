@@ -193,13 +193,15 @@ def colour_nodes(n: int, colour: int) -> np.ndarray:
 
 
 def pcg(K: sp.csr_matrix, f: np.ndarray, tol: float = 1e-12, maxit: int | None = None,
-        x0: np.ndarray | None = None):
+        x0: np.ndarray | None = None, observe=None):
     """Jacobi-preconditioned CG for the singular periodic system K x = f.
 
     The constant vector spans the null space of K, so f and every
     preconditioned residual are projected to zero mean, and the returned x is
     zero-mean.  Stops when ||f - K x|| <= tol * ||f|| (an all-zero f returns
-    x = 0).  Returns (x, iterations, true relative residual)."""
+    x = 0).  Returns (x, iterations, true relative residual).  observe, if
+    given, is called as observe(iterations, ||r|| / ||f||) with the recurrence
+    residual the stopping test just computed (for timing; it changes nothing)."""
     N = f.shape[0]
     if maxit is None:
         maxit = 50 * N + 1000
@@ -215,7 +217,12 @@ def pcg(K: sp.csr_matrix, f: np.ndarray, tol: float = 1e-12, maxit: int | None =
     p = z.copy()
     rz = r @ z
     it = 0
-    while it < maxit and np.linalg.norm(r) > tol * nf:
+    while it < maxit:
+        rn = np.linalg.norm(r)
+        if observe is not None:
+            observe(it, rn / nf)
+        if not rn > tol * nf:
+            break
         q = K @ p
         alpha = rz / (p @ q)
         x += alpha * p
