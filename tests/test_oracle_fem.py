@@ -338,3 +338,22 @@ def test_gauss_seidel_at_matches_pass():
     nodes = fem.colour_nodes(n, 5)
     full = fem.gauss_seidel_pass(K, f[0], T[0], nodes)
     assert np.allclose(fem.gauss_seidel_at(n, k, f, T, nodes)[0], full[nodes], atol=1e-12)
+
+
+def test_pcg_observer_sees_every_iteration_and_changes_nothing():
+    """The observer hook the CPU baseline times the solve with: called once
+    per stopping test with iterations 0, 1, ..., the recurrence residual
+    starting at 1 from a zero start, and the solve bitwise the one without
+    it."""
+    n = 6
+    rng = np.random.default_rng(3)
+    k = 1e-3 + rng.random(n ** 3) ** 3
+    K = fem.assemble(n, k)
+    f = fem.macro_load(n, k)[0]
+    seen = []
+    x1, it1, r1 = fem.pcg(K, f, tol=1e-10, observe=lambda it, res: seen.append((it, res)))
+    x0, it0, r0 = fem.pcg(K, f, tol=1e-10)
+    assert it1 == it0 and r1 == r0 and np.array_equal(x1, x0)
+    assert [s[0] for s in seen] == list(range(it0 + 1))
+    assert abs(seen[0][1] - 1.0) < 1e-12
+    assert seen[-1][1] <= 1e-10 < seen[-2][1]
