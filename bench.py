@@ -564,10 +564,13 @@ def main():
         chunk = max(10, -(-200 // max(args.steps, 1)))
         r = cpu_sample(wl, chunk=chunk, steps=args.steps, warmup=args.warmup, log=log)
         cores = r["cores"]
+        budget = chunk * (args.warmup + args.steps)
+        ran = (f"{r['cg_done']} iterations (it reached 1e-6 within the {args.warmup}+{args.steps} steps of "
+               f"{chunk} allowed)" if r['cg_done'] < budget else
+               f"{r['cg_done']} iterations in {args.warmup}+{args.steps} steps of {chunk}")
         sample = (f"{wl.name}: filter+SIMP+assembly+loads ({r['t_setup']:.1f}s) and the tail "
                   f"({r['t_tail']:.1f}s) timed in full; one uninterrupted Jacobi-PCG solve of load case 1, "
-                  f"{r['cg_done']} iterations in {args.warmup}+{args.steps} steps of {chunk}, "
-                  f"{r['t_iter'] * 1e3:.0f} ms each after the warm-up, residual {r['res_reached']:.2e}; "
+                  f"{ran}, {r['t_iter'] * 1e3:.0f} ms each after the warm-up, residual {r['res_reached']:.2e}; "
                   f"{r['cg_needed']:.0f} iterations to 1e-6 (own count, or extrapolated); "
                   f"one OC iteration estimated at {r['t_oc']:.0f}s")
         out = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
