@@ -57,7 +57,9 @@ typedef enum otm_status {
 /* Arithmetic of the solve (params.precision). */
 enum {
     OTM_FP64 = 0,   /* every field and operation in FP64 */
-    OTM_FP32 = 1,   /* FP32 fields and arithmetic; FP64 inner products, tensor and volume sums */
+    OTM_FP32 = 1,   /* FP32 fields and arithmetic; inner products, tensor and volume sums accumulated
+                       with error-free transformations in FP32 pairs (about 48 significant bits) and
+                       handed on as doubles; the iterate kept as an FP32 pair */
     OTM_MIXED = 2   /* FP32 outer CG; V-cycle fields and operators stored in BF16, FP32 arithmetic */
 };
 
