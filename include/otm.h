@@ -365,7 +365,8 @@ OTM_API otm_status otm_op_kappa_sens(int dtype, int n, double penal, double k_so
  * that device current; make that first call before any stream capture.  All
  * calls share the scratch and it keeps the last call's contents (the call
  * clears what must start at zero); calls whose GPU work overlaps race on it
- * and must be serialised by the caller. */
+ * and must be serialised by the caller.  Like the other operator-level
+ * calls it waits for its stream before it returns. */
 OTM_API otm_status otm_op_kappa_sens_noalloc(int dtype, int n, double penal, double k_solid,
                                              double k_void, const void* k, const void* rho_f,
                                              const void* chi, const double w[6],
@@ -428,6 +429,18 @@ OTM_API otm_status otm_unet_forward(otm_unet* u, const float* x, float* y, void*
  * last otm_unet_forward: dy 3 n^3 (device), grads param_count FP32 (device,
  * may be NULL: the gradient then stays inside the network). */
 OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads, void* stream);
+/* Stored activation of the last otm_unet_forward, converted to FP32, for
+ * gradient checks that reuse the network's own activations and ReLU masks:
+ * block in [0, 7) (E0 E1 E2 E3 D2 D1 D0, the order of the architecture
+ * above), which = 0 the block's input (E0: the BF16 density in channel 0 of
+ * 16, the others zero; E1..E3: the pooled input; D2..D0: the concatenation
+ * (upsampled coarse, skip)), 1 the first convolution's output after ReLU,
+ * 2 the block's output.  out (device, FP32) receives [voxel][C] (voxels x
+ * fastest at the block's grid n / 2^level), *channels = C; count = the
+ * capacity of out.  OTM_ESTATE without a stored forward pass, OTM_EINVAL
+ * for bad indices or a too small out. */
+OTM_API otm_status otm_unet_get_activation(otm_unet* u, int block, int which, float* out, size_t count,
+                                           int* channels, void* stream);
 /* One Adam step on L = mean((net(x) - target / target_scale)^2) over the
  * 3 n^3 entries (target_scale > 0; the predictor's scale when the targets are
  * solutions): forward, loss, backward, update.  *loss (host, may be NULL) =
@@ -463,6 +476,15 @@ OTM_API otm_status otm_op_conv3(int n, int cin, int cout, const void* in, const 
  * (FP32, accumulated into; db may be NULL). */
 OTM_API otm_status otm_op_conv3_wgrad(int n, int cin, int cout, const void* in, const void* g,
                                       float* dw, float* db, void* stream);
+/* Its input gradient, by the network's own backward path: the FP32 weights
+ * w [27][cin][cout] are rounded to BF16 and stored tap-flipped and
+ * transposed ([26 - t][co][ci]), and the forward convolution runs on that
+ * copy: dx[v][ci] = sum_t sum_co w[t][ci][co] g[v - d_t][co], with g
+ * [n^3][cout] and dx [n^3][cin] BF16 (device).  Takes its 2 x 27 cin cout
+ * BF16 weight scratch from the stream-ordered allocator (OTM_ENOMEM when it
+ * cannot). */
+OTM_API otm_status otm_op_conv3_dgrad(int n, int cin, int cout, const void* g, const float* w,
+                                      void* dx, void* stream);
 
 #ifdef __cplusplus
 }

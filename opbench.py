@@ -1,8 +1,8 @@
 """Run one libotm operator (or design steps) on seeded inputs, for timing and
 for profiling a single kernel under ncu.
 
-  python -m paper_2405_19991_gb300.opbench --op apply_K --n 128 --reps 3
-  python -m paper_2405_19991_gb300.opbench --op step --n 128 --reps 2 --warmup 3
+  python opbench.py --op apply_K --n 128 --reps 3
+  python opbench.py --op step --n 128 --reps 2 --warmup 3
 
 Ops: apply_K, gs (one fine colour pass), filter, kappa_sens, oc, step,
 unet (network forward), unet_train (one Adam step), conv3 (one convolution,
@@ -17,7 +17,7 @@ import sys
 
 import numpy as np
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -34,6 +34,8 @@ def main():
     ap.add_argument("--smoother", type=int, default=0, help="--op step: coarse_smoother (0 GS, 1 Chebyshev)")
     ap.add_argument("--cin", type=int, default=16)
     ap.add_argument("--cout", type=int, default=16)
+    ap.add_argument("--async", dest="async_", action="store_true",
+                    help="--op apply_K: queue the stream-ordered entry point back to back (no host sync per call)")
     args = ap.parse_args()
 
     import torch
@@ -71,7 +73,9 @@ def main():
         otm.otm_set_density(ctx, r0.ctypes.data, 0)
 
     def run():
-        if args.op == "apply_K":
+        if args.op == "apply_K" and args.async_:
+            otm.otm_op_apply_K_async(args.dtype, n, k, u, out, st.cuda_stream)
+        elif args.op == "apply_K":
             otm.otm_op_apply_K(args.dtype, n, k, u, out, st.cuda_stream)
         elif args.op == "gs":
             otm.otm_op_gs_colour(args.dtype, n, k, u, out, args.colour, st.cuda_stream)

@@ -3,9 +3,9 @@
 
 The computation lives in libotm.so (C ABI in include/otm.h, CUDA kernels for
 sm_103a under csrc/).  ``paper_2405_19991_gb300.otm`` is its thin ctypes
-binding and ``paper_2405_19991_gb300.api`` a small convenience layer over it
-for torch/numpy callers.  There is no CPU fallback: importing the binding
-fails when the library is missing.
+binding (argument marshalling only) and ``paper_2405_19991_gb300.warmstart``
+the host-side driver of the learned warm start's training loop.  There is no
+CPU fallback: importing the binding fails when the library is missing.
 """
 import os as _os
 

@@ -141,32 +141,34 @@ __device__ __forceinline__ C nb_from(const C (&w)[20], const C (&kk)[2][2][2]) {
 // Difference form of the same sum: nd(u) = sum coef (u_w - u_v) = nb(u) - 4 sum(k) u_v,
 // so 12 [K u]_v = -nd(u).  Constant fields cancel exactly, which keeps the
 // rounding error of K u proportional to the local differences of u instead
-// of to |u|.
+// of to |u|.  The terms are summed plane by plane -- the eight neighbours in
+// the plane below (c = 1: body diagonals, x-z, y-z edge diagonals), the four
+// in-plane edge diagonals, then the eight in the plane above (c = 0) -- the
+// order in which the TMA-staged form (kernels_tma.cuh) meets them while it
+// marches in z; every stencil form sums in this order.
 template <class UT, class C>
 __device__ __forceinline__ C nd_sum(const UT* __restrict__ u, const Nbr& g, const C (&kk)[2][2][2], C uc) {
     C acc = 0;
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
+    auto plane = [&](int c) {
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int a = 0; a < 2; ++a)
                 acc += kk[c][b][a] * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.Z[c])) - uc);
 #pragma unroll
+        for (int a = 0; a < 2; ++a)
+            acc += (kk[c][0][a] + kk[c][1][a]) * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.yc + g.Z[c])) - uc);
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            acc += (kk[c][b][0] + kk[c][b][1]) * ((C)St<UT>::ld(u, (size_t)(g.xc + g.Y[b] + g.Z[c])) - uc);
+    };
+    plane(1);
+#pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
         for (int a = 0; a < 2; ++a)
             acc += (kk[0][b][a] + kk[1][b][a]) * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.Y[b] + g.zc)) - uc);
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-            acc += (kk[c][0][a] + kk[c][1][a]) * ((C)St<UT>::ld(u, (size_t)(g.X[a] + g.yc + g.Z[c])) - uc);
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-            acc += (kk[c][b][0] + kk[c][b][1]) * ((C)St<UT>::ld(u, (size_t)(g.xc + g.Y[b] + g.Z[c])) - uc);
+    plane(0);
     return acc;
 }
 

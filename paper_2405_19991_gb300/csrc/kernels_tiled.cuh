@@ -145,28 +145,27 @@ k_stencil_tiled(int n, int tz, const KT* __restrict__ k, const UT* __restrict__ 
             };
             const C uc = Uat(0, 0, 0);
             C acc_nd = 0;
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
+            // plane by plane, as nd_sum (kernels_fine.cuh)
+            auto plane = [&](int c) {
 #pragma unroll
                 for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
                     for (int a = 0; a < 2; ++a)
                         acc_nd += kk[c][bb][a] * (Uat(1 - 2 * a, 1 - 2 * bb, 1 - 2 * c) - uc);
 #pragma unroll
+                for (int a = 0; a < 2; ++a)
+                    acc_nd += (kk[c][0][a] + kk[c][1][a]) * (Uat(1 - 2 * a, 0, 1 - 2 * c) - uc);
+#pragma unroll
+                for (int bb = 0; bb < 2; ++bb)
+                    acc_nd += (kk[c][bb][0] + kk[c][bb][1]) * (Uat(0, 1 - 2 * bb, 1 - 2 * c) - uc);
+            };
+            plane(1);
+#pragma unroll
             for (int bb = 0; bb < 2; ++bb)
 #pragma unroll
                 for (int a = 0; a < 2; ++a)
                     acc_nd += (kk[0][bb][a] + kk[1][bb][a]) * (Uat(1 - 2 * a, 1 - 2 * bb, 0) - uc);
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int a = 0; a < 2; ++a)
-                    acc_nd += (kk[c][0][a] + kk[c][1][a]) * (Uat(1 - 2 * a, 0, 1 - 2 * c) - uc);
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int bb = 0; bb < 2; ++bb)
-                    acc_nd += (kk[c][bb][0] + kk[c][bb][1]) * (Uat(0, 1 - 2 * bb, 1 - 2 * c) - uc);
+            plane(0);
             const C Ku = acc_nd * C(-1.0 / 12.0);
             C o;
             if (MODE == 0) {

@@ -8,7 +8,7 @@
 
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
-#include "kernels_x2.cuh"
+#include "kernels_tma.cuh"
 #include "kernels_tiled.cuh"
 #include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
@@ -73,6 +73,23 @@ otm_status finish(cudaStream_t st, const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return op_fail(OTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return OTM_OK;
+}
+
+// Set by a kernel whose bounded wait ran out (the TMA-staged stencil).
+__device__ int g_op_err;
+
+otm_status finish_flagged(cudaStream_t st, const char* what) {
+    const otm_status s = finish(st, what);
+    if (s != OTM_OK) return s;
+    int e = 0;
+    if (cudaMemcpyFromSymbol(&e, g_op_err, sizeof(int)) != cudaSuccess)
+        return op_fail(OTM_ECUDA, std::string(what) + ": reading the wait flag");
+    if (e) {
+        const int zero = 0;
+        cudaMemcpyToSymbol(g_op_err, &zero, sizeof(int));
+        return op_fail(OTM_ETIMEOUT, std::string(what) + ": a bounded wait on a shared-memory stage ran out");
+    }
     return OTM_OK;
 }
 
@@ -148,18 +165,19 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int zrm = sizeof(R) == 4 && otm::stencil_choice() == 0 ? otm::zr_m_for<false, otm::FinNone>(n, sms, oc.max_blocks) : 0;
-    if (zrm > 0) {   // the kernel and launch shape the solver uses at this size
-        otm::k_stencil_zr<false, otm::FinNone><<<otm::zr_grid(n, zrm), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
-            n, zrm, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
-        return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
+    otm::TmaLaunch tl;
+    otm::TmaStencilMaps maps;
+    if (sizeof(R) == 4 && otm::stencil_choice() == 0 &&
+        otm::tma_launch_shape<0, false, float, float, float, otm::FinNone>(tl, n, sms, oc.max_blocks) &&
+        otm::tma_make_maps<float, float>(maps, n, k, u, nullptr)) {
+        // the kernel and launch shape the solver uses at this size
+        int* err = nullptr;
+        if (cudaGetSymbolAddress((void**)&err, g_op_err) != cudaSuccess) return op_fail(OTM_ECUDA, "otm_op_apply_K: flag");
+        otm::launch_pdl_smem(otm::tma_kernel<0, false, float, float, float, otm::FinNone>(n), tl.grid, tl.threads,
+                             tl.smem, oc.st, maps, n, tl.ty, tl.m, tl.stages, (float*)Ku, err, rb, otm::FinNone{});
+        return sync ? finish_flagged(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
     }
-    const int x2tz = sizeof(R) == 4 && otm::stencil_choice() == 3 ? otm::x2_tz(n, sms, oc.max_blocks) : 0;
-    if (x2tz > 0) {
-        otm::k_stencil_x2<false, otm::FinNone><<<otm::x2_grid(n, x2tz), dim3(otm::kX2T, otm::kX2Y), 0, oc.st>>>(
-            n, x2tz, (const float*)k, (const float*)u, (float*)Ku, rb, otm::FinNone{});
-        return sync ? finish(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
-    }
+    cudaGetLastError();
     const int tz = sizeof(R) == 4 && otm::stencil_choice() != 2 ? otm::tiled_tz(n, sms, oc.max_blocks) : 0;
     if (tz > 0)
         otm::k_stencil_tiled<0, false, R, R, R, R, otm::FinNone>

@@ -580,6 +580,24 @@ OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads,
     return OTM_OK;
 }
 
+OTM_API otm_status otm_unet_get_activation(otm_unet* u, int block, int which, float* out, size_t count,
+                                           int* channels, void* stream) {
+    if (!u || !out || !channels) return ufail(OTM_EINVAL, "otm_unet_get_activation: NULL argument");
+    if (block < 0 || block >= kBlocks || which < 0 || which > 2)
+        return ufail(OTM_EINVAL, "otm_unet_get_activation: block must be in [0, 7) and which in [0, 2]");
+    if (!u->have_forward) return ufail(OTM_ESTATE, "otm_unet_get_activation: no stored forward pass");
+    const size_t N = u->Nl[kLevel[block]];
+    const int C = which == 0 ? (block == 0 ? 16 : u->cv[2 * block].ap) : u->blk_b[block];
+    const bf16* src = which == 0 ? u->block_in(block) : (which == 1 ? u->h1[block] : u->h2[block]);
+    if (count < N * C) return ufail(OTM_EINVAL, "otm_unet_get_activation: out holds fewer than N * C values");
+    cudaStream_t st = pick(u, stream);
+    otm::nn::k_bf16_to_f32<<<elt_grid(N * C), 256, 0, st>>>(N * C, src, out);
+    U_LAUNCH();
+    U_CU(cudaStreamSynchronize(st));
+    *channels = C;
+    return OTM_OK;
+}
+
 OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float* target, double target_scale,
                                        double lr, double* loss, void* stream) {
     if (!u || !x || !target) return ufail(OTM_EINVAL, "otm_unet_train_step: NULL argument");
@@ -619,6 +637,33 @@ OTM_API otm_status otm_op_conv3(int n, int cin, int cout, const void* in, const 
     if (!in || !w || !out) return ufail(OTM_EINVAL, "otm_op_conv3: NULL pointer");
     cudaStream_t st = (cudaStream_t)stream;
     U_TRY(conv3(n, cin, cout, (const bf16*)in, (const bf16*)w, bias, relu != 0, (bf16*)out, st));
+    U_CU(cudaStreamSynchronize(st));
+    return OTM_OK;
+}
+
+OTM_API otm_status otm_op_conv3_dgrad(int n, int cin, int cout, const void* g, const float* w, void* dx,
+                                      void* stream) {
+    if (n < 1 || n > 512) return ufail(OTM_EINVAL, "otm_op_conv3_dgrad: n must be in [1, 512]");
+    if (cin < 16 || cin > 512 || cin % 16 || cout < 16 || cout > 512 || cout % 16)
+        return ufail(OTM_EINVAL, "otm_op_conv3_dgrad: cin and cout must be multiples of 16 in [16, 512]");
+    if (!g || !w || !dx) return ufail(OTM_EINVAL, "otm_op_conv3_dgrad: NULL pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the network's own input-gradient path: pack the FP32 weights into the
+    // BF16 copy and its tap-flipped, transposed copy (k_pack_w), then run the
+    // forward convolution on the transposed copy
+    const size_t M = (size_t)27 * cin * cout;
+    bf16 *wc = nullptr, *wt = nullptr;
+    U_CU(cudaMallocAsync((void**)&wc, M * sizeof(bf16), st));
+    cudaError_t e = cudaMallocAsync((void**)&wt, M * sizeof(bf16), st);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(wc, st);
+        return ufail(OTM_ENOMEM, "otm_op_conv3_dgrad: scratch");
+    }
+    otm::nn::k_pack_w<<<elt_grid(M), 256, 0, st>>>(cin, cin, cout, w, wc, wt);
+    otm_status s2 = conv3(n, cout, cin, (const bf16*)g, wt, nullptr, false, (bf16*)dx, st);
+    cudaFreeAsync(wc, st);
+    cudaFreeAsync(wt, st);
+    if (s2 != OTM_OK) return s2;
     U_CU(cudaStreamSynchronize(st));
     return OTM_OK;
 }

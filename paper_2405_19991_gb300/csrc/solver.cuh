@@ -18,7 +18,7 @@
 #include "kernels_tiled.cuh"
 #include "kernels_cluster.cuh"
 #include "kernels_warprow.cuh"
-#include "kernels_x2.cuh"
+#include "kernels_tma.cuh"
 #include "kernels_ws.cuh"
 #include "otm_internal.cuh"
 #include "unet_api.cuh"
@@ -296,8 +296,22 @@ class Solver : public SolverBase {
         return q * q * sizeof(C) <= 24 * 1024 ? q * q * sizeof(C) : 0;
     }
     int tiled_grid() const { return (n / kTX) * (n / kTY) * (n / tz_); }
-    int x2tz_ = 0;   // z-planes per CTA of the paired-node fine stencil (FP32 fields), 0: not used
-    int zrm_ = 0;    // z-chunks per column of its z-reuse form, 0: not used
+    // TMA-staged fine stencil (FP32 PCG fields, 32 | n or 64 | n for BF16
+    // storage): the PCG product q = K p with p . q, and the V-cycle's
+    // residual f - K T; grid 0 when the form is not used
+    TmaLaunch tma_pcg_, tma_vc_;
+    TmaStencilMaps maps_pcg_, maps_vc_;
+    void launch_tma_pcg(const RedBuf& rb) {
+        if constexpr (std::is_same<R, float>::value)
+            launch_pdl_smem(tma_kernel<0, true, float, float, float, FinAlpha>(n), tma_pcg_.grid, tma_pcg_.threads,
+                            tma_pcg_.smem, stream, maps_pcg_, n, tma_pcg_.ty, tma_pcg_.m, tma_pcg_.stages, (float*)q, &ps->dev_err, rb,
+                            FinAlpha{ps});
+    }
+    void launch_tma_vc() {
+        if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value)
+            launch_pdl_smem(tma_kernel<1, false, S, float, S, FinNone>(n), tma_vc_.grid, tma_vc_.threads, tma_vc_.smem,
+                            stream, maps_vc_, n, tma_vc_.ty, tma_vc_.m, tma_vc_.stages, res0, &ps->dev_err, rbuf(), FinNone{});
+    }
     size_t inv_smem_ = 0;    // dynamic shared memory of the coarsest inverse
     int inv_use_smem_ = 0;   // its working matrix in shared memory
     // warp-row kernels on the finest grid (FP32 / mixed paths, 128 | n)
@@ -314,8 +328,17 @@ class Solver : public SolverBase {
         return (int)b;
     }
 
+    // Host-side fault injection for the failure tests: OTM_FAIL_ALLOC_AT=k
+    // makes the k-th device allocation of a context (1-based) report an
+    // allocation failure without allocating; the context then unwinds as
+    // on a real cudaMalloc failure.
+    int alloc_seq_ = 0, fail_alloc_at_ = 0;
     template <class T>
     otm_status alloc(T*& ptr, size_t count) {
+        if (++alloc_seq_ == fail_alloc_at_) {
+            err = "cudaMalloc: injected allocation failure (OTM_FAIL_ALLOC_AT)";
+            return OTM_ENOMEM;
+        }
         OTM_CU(cudaMalloc((void**)&ptr, count * sizeof(T) + 16));
         OTM_CU(cudaMemsetAsync(ptr, 0, count * sizeof(T) + 16, stream));
         return OTM_OK;
@@ -351,6 +374,7 @@ class Solver : public SolverBase {
 
     otm_status init(const otm_params& pin) override {
         prm = pin;
+        if (const char* fa = getenv("OTM_FAIL_ALLOC_AT")) fail_alloc_at_ = atoi(fa);
         n = pin.n;
         N = (size_t)n * n * n;
         std::vector<int> sizes;
@@ -365,8 +389,6 @@ class Solver : public SolverBase {
         OTM_CU(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
         max_blocks = sm_count * 8;
         tz_ = stencil_choice() != 2 ? tiled_tz(pin.n, sm_count, max_blocks) : 0;
-        if (std::is_same<R, float>::value && stencil_choice() == 0) zrm_ = zr_m_for<true, FinAlpha>(pin.n, sm_count, max_blocks);
-        if (std::is_same<R, float>::value && stencil_choice() == 3) x2tz_ = x2_tz(pin.n, sm_count, max_blocks);
         wr_ = warprow_ok(pin.n) && std::is_same<R, float>::value;
         // Fine Gauss-Seidel grid: where the fields outgrow L2 (n >= 256) the
         // pass runs best as two full waves of resident blocks (256^3 design
@@ -430,6 +452,18 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(stage_f, 3 * N));
         if (std::is_same<R, S>::value) k_vc = (S*)kf;
         else OTM_TRY(alloc(k_vc, N));
+        if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
+            if (stencil_choice() == 0) {
+                // tensor maps of the fixed fine buffers, encoded once per context
+                if (tma_launch_shape<0, true, float, float, float, FinAlpha>(tma_pcg_, n, sm_count, max_blocks) &&
+                    !tma_make_maps<float, float>(maps_pcg_, n, kf, p, nullptr))
+                    tma_pcg_.grid = 0;
+                if (tma_launch_shape<1, false, S, float, S, FinNone>(tma_vc_, n, sm_count, max_blocks) &&
+                    !tma_make_maps<S, float>(maps_vc_, n, k_vc, z, r))
+                    tma_vc_.grid = 0;
+                cudaGetLastError();   // a refused shape leaves the older forms in place
+            }
+        }
         for (int l = 1; l < nlev; ++l) {
             // coarse levels are node-major: fields [N][4], stencil [N][CL<S>::AW]
             OTM_TRY(alloc(Tl[l], 4 * Nl[l]));
@@ -764,7 +798,9 @@ class Solver : public SolverBase {
             fine_gs_pass(gidx);
         }
         ++nl_;
-        if (tz_ > 0 && !std::is_same<S, double>::value)
+        if (tma_vc_.grid > 0)
+            launch_tma_vc();
+        else if (tz_ > 0 && !std::is_same<S, double>::value)
             launch_pdl(k_stencil_tiled<1, false, S, S, R, S, FinNone>, tiled_grid(), dim3(kTX, kTY), stream, n, tz_,
                        k_vc, z, r, res0, rbuf(), FinNone{});
         else
@@ -901,12 +937,8 @@ class Solver : public SolverBase {
         if (N % 4 == 0) launch_pdl(k_update_p4<R, S>, grid(N / 4), 256, stream, N, p, z, ps);
         else launch_pdl(k_update_p<R, S>, grid(N), 256, stream, N, p, z, ps);
         ++nl_;
-if (zrm_ > 0)
-            launch_pdl(k_stencil_zr<true, FinAlpha>, zr_grid(n, zrm_), dim3(kX2T, kX2Y), stream, n, zrm_,
-                       (const float*)kf, (const float*)p, (float*)q, rb, FinAlpha{ps});
-        else if (x2tz_ > 0)
-            launch_pdl(k_stencil_x2<true, FinAlpha>, x2_grid(n, x2tz_), dim3(kX2T, kX2Y), stream, n, x2tz_,
-                       (const float*)kf, (const float*)p, (float*)q, rb, FinAlpha{ps});
+if (tma_pcg_.grid > 0)
+            launch_tma_pcg(rb);
         else if (tz_ > 0 && std::is_same<R, float>::value)
             launch_pdl(k_stencil_tiled<0, true, R, R, R, R, FinAlpha>, tiled_grid(), dim3(kTX, kTY), stream, n, tz_,
                        kf, p, (const R*)nullptr, q, rb, FinAlpha{ps});
@@ -1123,6 +1155,7 @@ if (zrm_ > 0)
             err = std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e);
             st = OTM_ECUDA;
         }
+        const bool captured = st == OTM_OK;
         if (st == OTM_OK) {
             e = cudaGraphInstantiate(out, g, 0);
             if (e != cudaSuccess) {
@@ -1130,7 +1163,10 @@ if (zrm_ > 0)
                 st = OTM_ECUDA;
             }
         }
-        cudaGraphDestroy(g);
+        // A graph whose capture failed part way (a launch inside the PCG loop's
+        // conditional body refused) is left alone: destroying one crashed the
+        // driver (in cuGraphDestroy).  The graph leaks only on that error path.
+        if (captured) cudaGraphDestroy(g);
         *fixed = (nl_ - n0) - body;
         nlg_body = body;
         nl_ = n0;
@@ -1263,10 +1299,9 @@ if (zrm_ > 0)
         OTM_TRY(prepare());
         memset(out, 0, sizeof(*out));
         out->stencil_form = stencil_choice();
-        if (out->stencil_form == 0 && zrm_ == 0) out->stencil_form = tz_ > 0 ? 1 : 2;
-        if (out->stencil_form == 3 && x2tz_ == 0) out->stencil_form = tz_ > 0 ? 1 : 2;
+        if (out->stencil_form == 0 && tma_pcg_.grid == 0) out->stencil_form = tz_ > 0 ? 1 : 2;
         if (out->stencil_form == 1 && tz_ == 0) out->stencil_form = 2;
-        out->stencil_chunks = zrm_;
+        out->stencil_chunks = tma_pcg_.m;
         out->levels = nlev;
         out->coarsest_n = sz[nlev - 1];
         out->cluster_maxn = use_cluster && nlev > 1 ? cluster_maxn : 0;
@@ -1344,7 +1379,7 @@ if (zrm_ > 0)
             OTM_TRY(enqueue_setup());
             OTM_TRY(pass_direct(0));
         }
-        bool converged = false;
+        bool converged = false, finite = true;
         double prev_worst = 1e300;
         for (int restart = 0;; ++restart) {
             for (int i = 0; i < 3; ++i) iters[i] += ps_h->iters[i];
@@ -1352,10 +1387,18 @@ if (zrm_ > 0)
             bool all_ok = true;
             for (int i = 0; i < 3; ++i) {
                 const double ff = ps_h->true_ff[i];
+                // a non-finite load or residual (NaN or Inf in rho or in the
+                // iterate) never counts as converged
+                if (!std::isfinite(ff) || !std::isfinite(ps_h->true_rr[i])) {
+                    finite = false;
+                    all_ok = false;
+                    continue;
+                }
                 const double rel = ff > 0 ? std::sqrt(ps_h->true_rr[i] / ff) : 0.0;
                 worst = rel > worst ? rel : worst;
                 if (!(rel <= prm.cg_tol)) all_ok = false;
             }
+            if (!finite) break;
             if (all_ok) {
                 converged = true;
                 break;
@@ -1373,6 +1416,10 @@ if (zrm_ > 0)
                 info->cg_iters[i] = iters[i];
                 info->resid[i] = rel;
             }
+        }
+        if (!finite) {
+            err = "non-finite load or residual (NaN or Inf in the density or the solution)";
+            return OTM_ENOCONV;
         }
         if (!converged) {
             err = "PCG did not reach cg_tol (cg_maxit reached or the residual stagnated)";

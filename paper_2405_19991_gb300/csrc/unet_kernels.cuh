@@ -222,6 +222,12 @@ __device__ __forceinline__ void copy8(bf16* d, const bf16* s) {
 }
 
 // g = g * (y > 0): ReLU backward, y the block output (count a multiple of 8).
+// BF16 -> FP32 copy (exports of stored activations)
+static __global__ void k_bf16_to_f32(size_t count, const bf16* __restrict__ in, float* __restrict__ out) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __bfloat162float(in[i]);
+}
+
 static __global__ void k_relu_mask(size_t count, bf16* __restrict__ g, const bf16* __restrict__ y) {
     const unsigned n8 = (unsigned)(count / 8);
     for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n8; e += gridDim.x * blockDim.x) {

@@ -151,6 +151,8 @@ def _load():
         "otm_set_predictor": [vp, vp, d],
         "otm_op_conv3": [i, i, i, vp, vp, vp, i, vp, vp],
         "otm_op_conv3_wgrad": [i, i, i, vp, vp, vp, vp, vp],
+        "otm_op_conv3_dgrad": [i, i, i, vp, vp, vp, vp],
+        "otm_unet_get_activation": [vp, i, i, vp, sz, P(C.c_int), vp],
     }
     for name, args in sigs.items():
         fn = getattr(lib, name)
@@ -173,7 +175,7 @@ EXPORTED = [
     "otm_op_oc_update", "otm_op_kappa_sens_noalloc", "otm_unet_create", "otm_unet_destroy",
     "otm_unet_param_count", "otm_unet_get_params", "otm_unet_set_params", "otm_unet_forward",
     "otm_unet_backward", "otm_unet_train_step", "otm_unet_eval", "otm_set_predictor", "otm_op_conv3",
-    "otm_op_conv3_wgrad",
+    "otm_op_conv3_wgrad", "otm_op_conv3_dgrad", "otm_unet_get_activation",
 ]
 
 
@@ -410,3 +412,15 @@ def otm_op_conv3(n, cin, cout, x, w, bias, relu, out, stream=None):
 
 def otm_op_conv3_wgrad(n, cin, cout, x, g, dw, db, stream=None):
     return check(lib.otm_op_conv3_wgrad(n, cin, cout, _p(x), _p(g), _p(dw), _p(db), stream))
+
+
+def otm_op_conv3_dgrad(n, cin, cout, g, w, dx, stream=None):
+    return check(lib.otm_op_conv3_dgrad(n, cin, cout, _p(g), _p(w), _p(dx), stream))
+
+
+def otm_unet_get_activation(u, block, which, out, count, stream=None) -> int:
+    """Copies one stored activation into `out` (device FP32, [voxel][C]);
+    returns C."""
+    ch = C.c_int(0)
+    check(lib.otm_unet_get_activation(u, int(block), int(which), _p(out), int(count), C.byref(ch), stream))
+    return ch.value

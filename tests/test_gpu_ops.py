@@ -249,39 +249,42 @@ np.save(out, o.cpu().numpy())
 """
 
 
-@pytest.mark.parametrize("n", [64, 128, 192])
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 192, 256])
 def test_stencil_forms_are_bitwise_equal(n, tmp_path):
-    """The four fine-stencil forms (z-reuse, three-plane paired, tiled, gather)
-    perform the same operations per node in the same order: same bits."""
+    """The three fine-stencil forms (TMA-staged, tiled, gather) sum the same
+    terms per node in the same plane-by-plane order: same bits.  The sizes
+    cover 1 to 16 rows per CTA (n = 256 .. 32) and a row of 48 pairs (n = 96,
+    where the tiled form also applies)."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     got = {}
-    for form in ("zr", "pair", "tiled", "gather"):
+    for form in ("tma", "tiled", "gather"):
         path = str(tmp_path / f"{form}.npy")
         env = dict(os.environ, OTM_STENCIL=form)
         subprocess.run([sys.executable, "-c", _FORM_SCRIPT, root, str(n), path], env=env, check=True,
                        timeout=300)
         got[form] = np.load(path)
-    for form in ("pair", "tiled", "gather"):
-        assert np.array_equal(got["zr"].view(np.uint32), got[form].view(np.uint32)), form
+    for form in ("tiled", "gather"):
+        assert np.array_equal(got["tma"].view(np.uint32), got[form].view(np.uint32)), form
 
 
-@pytest.mark.parametrize("grid", [1, 7, 456, 1000])
-def test_stencil_zr_any_grid(grid, tmp_path):
-    """The z-reuse form's runs of (column, plane) units: any grid size (runs
-    crossing column boundaries, one CTA doing everything) gives the same bits."""
+@pytest.mark.parametrize("m", [1, 2, 7, 64])
+def test_stencil_tma_any_chunking(m, tmp_path):
+    """The TMA-staged form's z-chunks (m chunks per column, ragged when m does
+    not divide n; one chunk marches the whole column through the ring many
+    times): any chunk count gives the same bits."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     paths = []
-    for g in (None, grid):
-        path = str(tmp_path / f"g{g}.npy")
-        env = dict(os.environ, OTM_STENCIL="zr")
-        if g is not None:
-            env["OTM_ZR_GRID"] = str(g)
+    for mm in (None, m):
+        path = str(tmp_path / f"m{mm}.npy")
+        env = dict(os.environ, OTM_STENCIL="tma")
+        if mm is not None:
+            env["OTM_TMA_M"] = str(mm)
         subprocess.run([sys.executable, "-c", _FORM_SCRIPT, root, "128", path], env=env, check=True, timeout=300)
         paths.append(path)
     a, b = np.load(paths[0]), np.load(paths[1])

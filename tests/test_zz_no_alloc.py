@@ -27,6 +27,58 @@ def _inputs(n, seed, dtype):
     return dev(k, t), dev(rho_f, t), dev(chi.ravel(), t), w, t
 
 
+def _runtime():
+    """The CUDA runtime library this process already loaded (the one
+    libotm.so links), to read the stream-ordered allocator's counters."""
+    import ctypes
+    with open("/proc/self/maps") as fh:
+        paths = sorted({ln.split()[-1] for ln in fh if "libcudart.so" in ln})
+    assert paths, "no CUDA runtime mapped"
+    return ctypes.CDLL(paths[0])
+
+
+def _pool_high_water(rt, reset=False):
+    """High-water mark of the device's current memory pool (the pool the
+    allocating entry point's cudaMallocAsync draws from); reset=True first
+    lowers it to the pool's current use."""
+    import ctypes
+    import torch
+    pool = ctypes.c_void_p()
+    assert rt.cudaDeviceGetMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    v = ctypes.c_uint64(0)
+    if reset:
+        assert rt.cudaMemPoolSetAttribute(pool, 8, ctypes.byref(v)) == 0   # cudaMemPoolAttrUsedMemHigh
+    assert rt.cudaMemPoolGetAttribute(pool, 8, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_noalloc_makes_no_device_allocation():
+    """The property the entry point exists for.  After its first call on the
+    device (which looks up the scratch's address), further calls leave both
+    the stream-ordered pool's high-water mark and the device's free memory
+    where they were, while the allocating entry point, as a control, does
+    raise the pool's mark."""
+    import torch
+    from paper_2405_19991_gb300 import otm
+    n = 64
+    k_d, rf_d, chi_d, w, t = _inputs(n, 5, 1)
+    s = empty(n ** 3, t)
+    otm.otm_op_kappa_sens_noalloc(1, n, 3.0, 1.0, 1e-3, k_d, rf_d, chi_d, w, s)
+    torch.cuda.synchronize()
+    rt = _runtime()
+    base = _pool_high_water(rt, reset=True)
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        otm.otm_op_kappa_sens_noalloc(1, n, 3.0, 1.0, 1e-3, k_d, rf_d, chi_d, w, s)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert _pool_high_water(rt) == base
+    assert free1 == free0
+    otm.otm_op_kappa_sens(1, n, 3.0, 1.0, 1e-3, k_d, rf_d, chi_d, w, s)
+    torch.cuda.synchronize()
+    assert _pool_high_water(rt) > base
+
+
 @pytest.mark.parametrize("dtype", [1, 0])
 @pytest.mark.parametrize("n", [16, 128])
 def test_noalloc_matches_allocating_entry_point_twice(dtype, n):
