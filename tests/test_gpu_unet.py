@@ -15,7 +15,14 @@ Tolerances come from the arithmetic:
   root-mean-square (errors uniform in half an ulp), and with layer gains near
   1 (He initialisation) the perturbations add at most linearly:
   38 x 2^-8 / sqrt(3) = 0.086, so the norm-wise forward bound is 0.1.
-* the parameter gradients of this network are ill-conditioned: one relative
+* the parameter gradients, evaluated on the GPU's own stored activations
+  (same ReLU masks), differ from the oracle's backward only by the BF16
+  roundings of the activation gradients along the way (d of them before a
+  group, each <= 2^-8 relative) and FP32 sums: element-wise
+  |gpu - ref| <= ((d + 1) 2^-8 + N 2^-22) S with S the same backward over
+  absolute values, and norm-wise <= (d + 1) 2^-8 / sqrt(3);
+* evaluated end to end instead (each side its own forward), the parameter
+  gradients of this network are ill-conditioned: one relative
   perturbation of size u of the oracle's own weights and input changes whole
   gradient groups by 15-100 % (ReLU masks flip and sums cancel at the coarse
   levels, which hold 1 to 27 voxels).  The GPU gradient is therefore compared
@@ -132,6 +139,121 @@ def test_conv3_weight_gradient_matches_definition(n, cin, cout):
     tol_b = N * 2.0 ** -22 * S_b + 1e-30
     assert np.all(np.abs(host(dw) - dW_ref) <= tol_w)
     assert np.all(np.abs(host(db) - db_ref) <= tol_b)
+
+
+@pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32), (16, 48, 16),
+                                        (16, 16, 32), (8, 128, 64), (24, 32, 16)])
+def test_conv3_input_gradient_matches_definition(n, cin, cout):
+    """The network's input-gradient path -- the FP32 weights packed by
+    k_pack_w into the tap-flipped, transposed BF16 copy, then the forward
+    convolution kernel on it -- against the definition
+    dx[ci][v] = sum_t sum_co W[t][ci][co] g[co][v - d_t] (the adjoint of the
+    circular convolution), on the same BF16 g and BF16-rounded weights.
+    Bound as for the forward: K = 27 cout FP32 products and one BF16
+    rounding of the output."""
+    otm = _otm()
+    torch = _torch()
+    rng = np.random.default_rng(13 * n + cin + 7 * cout)
+    N = n ** 3
+    g_d, g = _bf16_dev(rng.standard_normal((N, cout)))
+    w = rng.standard_normal((27, cin, cout)) / np.sqrt(27 * cout)
+    w_d = dev(w, torch.float32)
+    wb = torch.as_tensor(w, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    dx = torch.empty((N, cin), dtype=torch.bfloat16, device="cuda")
+    otm.otm_op_conv3_dgrad(n, cin, cout, g_d, w_d, dx)
+    go = _to_oracle(g, n, cout)
+    x0 = np.zeros((cin, n, n, n))
+    ref, _, _ = U.conv3_backward(x0, wb, go)
+    S, _, _ = U.conv3_backward(x0, np.abs(wb), np.abs(go))
+    got = _to_oracle(dx.float().cpu().double().numpy(), n, cin)
+    K = 27 * cout
+    tol = 2.0 ** -8 * np.abs(ref) + K * 2.0 ** -22 * S + 1e-30
+    assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
+
+
+# BF16 roundings of activation gradients between dy and each parameter
+# group's gradient in the network's backward pass: the head's output
+# gradient (1); per block, the convolution producing the first layer's
+# gradient (+1) and the block's input gradient (+1); upsample-concatenation
+# backward sums 8 children of the coarse part (+1, the skip part is a copy);
+# pooling backward adds into the skip gradient (+1).
+_DEPTH = {"H": 0, "D0.W2": 1, "D0.W1": 2, "D1.W2": 4, "D1.W1": 5, "D2.W2": 7, "D2.W1": 8,
+          "E3.W2": 10, "E3.W1": 11, "E2.W2": 13, "E2.W1": 14, "E1.W2": 16, "E1.W1": 17,
+          "E0.W2": 19, "E0.W1": 20}
+_LEVEL = {"E0": 0, "E1": 1, "E2": 2, "E3": 3, "D2": 2, "D1": 1, "D0": 0}
+
+
+def _activations(u, n, widths):
+    """The network's stored BF16 activations of the last forward, as the
+    oracle's cache: per block (input, first convolution's output, block
+    output) in (C, z, y, x) layout, FP64."""
+    otm = _otm()
+    torch = _torch()
+    cache = {}
+    for k, name in enumerate(U.BLOCKS):
+        ns = n >> _LEVEL[name]
+        parts = []
+        for which in range(3):
+            buf = torch.empty(ns ** 3 * 512, dtype=torch.float32, device="cuda")
+            c = otm.otm_unet_get_activation(u, k, which, buf, buf.numel())
+            a = _to_oracle(host(buf[: ns ** 3 * c]), ns, c)
+            if name == "E0" and which == 0:
+                a = a[:1]   # the density sits in channel 0 of the 16-channel padded input
+            parts.append(a)
+        cache[name] = tuple(parts)
+    cache["H"] = cache["D0"][2]
+    return cache
+
+
+@pytest.mark.parametrize("n,widths", [(8, (16, 16, 16, 16)), (16, (16, 32, 64, 128)), (24, (16, 32, 32, 48))])
+def test_unet_gradient_on_the_networks_own_activations(n, widths):
+    """Each parameter group's gradient element by element against the
+    oracle's backward pass evaluated on the GPU's own stored BF16
+    activations (so the ReLU masks are the GPU's: no mask flips) and on the
+    BF16-rounded convolution weights the GPU computes with.  What remains is
+    the GPU's rounding: the BF16 activation gradients between dy and the
+    group (_DEPTH roundings, each at most 2^-8 relative) and the FP32 sums
+    (27 c products per convolution, N voxels per weight gradient), bounded
+    element-wise by the same sums over absolute values S:
+    |gpu - ref| <= ((d + 1) 2^-8 + N 2^-22) S."""
+    otm = _otm()
+    torch = _torch()
+    u, p = _net(n, widths, seed=3)
+    try:
+        x = W.random_density(n, 5).reshape(1, n, n, n)
+        x_d = dev(x.reshape(-1), torch.float32)
+        y_d = empty(3 * n ** 3, torch.float32)
+        otm.otm_unet_forward(u, x_d, y_d)
+        cache = _activations(u, n, widths)
+        rng = np.random.default_rng(17)
+        dy = rng.standard_normal((3, n, n, n))
+        dy_d = dev(dy.reshape(-1), torch.float32)
+        P = otm.otm_unet_param_count(u)
+        g_d = empty(P, torch.float32)
+        otm.otm_unet_backward(u, dy_d, g_d)
+        dyh = host(dy_d).reshape(3, n, n, n)
+        pb = {}
+        for k, v in p.items():
+            rounded = k.endswith(".W1") or k.endswith(".W2")
+            pb[k] = torch.as_tensor(v, dtype=torch.float32).to(torch.bfloat16).double().numpy() if rounded else v
+        g_ref, _ = U.backward(pb, cache, dyh, widths)
+        S, _ = U.backward({k: np.abs(v) for k, v in pb.items()}, cache, np.abs(dyh), widths)
+        g = _unflat(host(g_d), widths)
+        worst = {}
+        for key in g_ref:
+            name = key.split(".")[0]
+            d = _DEPTH["H"] if name == "H" else _DEPTH[name + ".W" + ("2" if key.endswith("2") else "1")]
+            N = (n >> _LEVEL.get(name, 0)) ** 3
+            tol = ((d + 1) * 2.0 ** -8 + N * 2.0 ** -22) * S[key] + 1e-30
+            err = np.abs(g[key] - g_ref[key])
+            assert np.all(err <= tol), (key, float(np.max(err / tol)))
+            # norm-wise: d + 1 roundings of RMS 2^-8 / sqrt(3) each, adding linearly
+            rel = _rel(g[key], g_ref[key])
+            assert rel <= (d + 1) * 2.0 ** -8 / np.sqrt(3.0) + 1e-6, (key, rel, d)
+            worst[key] = (round(rel, 5), round(float(np.max(err / tol)), 3))
+        print("relative error, worst error / bound per group:", worst)
+    finally:
+        otm.otm_unet_destroy(u)
 
 
 def _net(n, widths, seed):
