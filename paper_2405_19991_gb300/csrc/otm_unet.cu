@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "conv_tc05.cuh"
 #include "otm_internal.cuh"
 #include "unet_kernels.cuh"
 #include "unet_api.cuh"
@@ -91,10 +92,76 @@ cudaError_t tile_prepare() {
     return e;
 }
 
-// out = act(conv3(in) + bias)
+// Convolution form: 0 tcgen05 (where it applies), 1 the mma.sync kernels
+// (OTM_CONV=mma), for comparisons.
+int conv_choice() {
+    static int c = [] {
+        const char* e = getenv("OTM_CONV");
+        return e && e[0] == 'm' ? 1 : 0;
+    }();
+    return c;
+}
+
+// Set by a tcgen05 convolution whose bounded wait ran out.
+__device__ int g_conv_err;
+
+// After a synchronised operator call: OTM_ETIMEOUT (and the flag cleared)
+// when a tcgen05 convolution's bounded wait ran out.
+otm_status conv_flag(const char* what) {
+    int e = 0;
+    U_CU(cudaMemcpyFromSymbol(&e, g_conv_err, sizeof(int)));
+    if (!e) return OTM_OK;
+    const int zero = 0;
+    cudaMemcpyToSymbol(g_conv_err, &zero, sizeof(int));
+    return ufail(OTM_ETIMEOUT, std::string(what) + ": a bounded wait for the tensor-core MMAs ran out");
+}
+
+// Opt in to the tcgen05 kernel's dynamic shared memory, only ever raising it.
+template <bool RL>
+cudaError_t tc_prepare(size_t bytes) {
+    static std::mutex m;
+    static size_t granted[64] = {};
+    std::lock_guard<std::mutex> lock(m);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (bytes <= granted[dev]) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(otm::nn::k_conv3_tc<RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) granted[dev] = bytes;
+    return e;
+}
+
+// out = act(conv3(in) + bias).  wtc: the weights already in the tcgen05
+// kernel's packed layout (k_pack_w_tc), or NULL to pack them here into
+// stream-ordered scratch.
 otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const float* bias, bool relu, bf16* out,
-                 cudaStream_t st) {
+                 cudaStream_t st, const bf16* wtc = nullptr) {
     const size_t N = (size_t)n * n * n;
+    if (conv_choice() == 0 && otm::nn::conv3_tc_ok(n, cin, cout)) {
+        const size_t smem = otm::nn::conv3_tc_smem(cout);
+        const cudaError_t e = relu ? tc_prepare<true>(smem) : tc_prepare<false>(smem);
+        if (e != cudaSuccess) return ufail(OTM_ECUDA, std::string("conv3 (tcgen05) shared-memory opt-in: ") + cudaGetErrorString(e));
+        bf16* scratch = nullptr;
+        if (!wtc) {
+            const size_t M = (size_t)27 * cin * cout;
+            U_CU(cudaMallocAsync((void**)&scratch, M * sizeof(bf16), st));
+            otm::nn::k_pack_w_tc<<<elt_grid(M), 256, 0, st>>>(cin, cout, w, scratch);
+            g_launches += 1;
+            wtc = scratch;
+        }
+        int* err = nullptr;
+        U_CU(cudaGetSymbolAddress((void**)&err, g_conv_err));
+        const unsigned grid = (unsigned)((n / otm::nn::kTcX) * (n / otm::nn::kTcY) * n);
+        if (relu)
+            otm::nn::k_conv3_tc<true><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
+        else
+            otm::nn::k_conv3_tc<false><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
+        g_launches += 1;
+        if (scratch) cudaFreeAsync(scratch, st);
+        U_LAUNCH();
+        return OTM_OK;
+    }
     if (otm::nn::conv3_tile_ok(n) && cout % 16 == 0 && cin % 16 == 0) {
         // 32 output channels per CTA, unless that leaves a small grid with
         // fewer CTAs than SMs (the 16^3 level): then 16, for twice the CTAs
@@ -221,6 +288,7 @@ struct otm_unet {
         int a = 0, ap = 0, b = 0;
         size_t oW = 0, ob = 0;
         bf16 *Wc = nullptr, *Wt = nullptr;
+        bf16 *Wc_tc = nullptr, *Wt_tc = nullptr;   // the same in the tcgen05 kernel's packed layout
     };
     Conv cv[2 * kBlocks];
     int blk_a[kBlocks] = {}, blk_b[kBlocks] = {};
@@ -304,6 +372,8 @@ struct otm_unet {
         for (auto& q : cv) {
             U_TRY(alloc(q.Wc, (size_t)27 * q.ap * q.b));
             U_TRY(alloc(q.Wt, (size_t)27 * q.ap * q.b));
+            U_TRY(alloc(q.Wc_tc, (size_t)27 * q.ap * q.b));
+            U_TRY(alloc(q.Wt_tc, (size_t)27 * q.ap * q.b));
         }
         U_TRY(alloc(x0, Nl[0] * 16));
         for (int k = 0; k < kBlocks; ++k) {
@@ -357,6 +427,10 @@ struct otm_unet {
         for (auto& q : cv) {
             const size_t M = (size_t)27 * q.ap * q.b;
             otm::nn::k_pack_w<<<elt_grid(M), 256, 0, st>>>(q.a, q.ap, q.b, p + q.oW, q.Wc, q.Wt);
+            if (q.ap % 16 == 0 && q.b % 16 == 0) {
+                otm::nn::k_pack_w_tc<<<elt_grid(M), 256, 0, st>>>(q.ap, q.b, q.Wc, q.Wc_tc);
+                otm::nn::k_pack_w_tc<<<elt_grid(M), 256, 0, st>>>(q.b, q.ap, q.Wt, q.Wt_tc);
+            }
         }
         g_launches += 1;
         U_LAUNCH();
@@ -366,8 +440,8 @@ struct otm_unet {
     otm_status block_fwd(int k, cudaStream_t st) {
         const int ns = side[kLevel[k]];
         const Conv &q1 = cv[2 * k], &q2 = cv[2 * k + 1];
-        U_TRY(conv3(ns, q1.ap, q1.b, block_in(k), q1.Wc, p + q1.ob, true, h1[k], st));
-        U_TRY(conv3(ns, q2.ap, q2.b, h1[k], q2.Wc, p + q2.ob, true, h2[k], st));
+        U_TRY(conv3(ns, q1.ap, q1.b, block_in(k), q1.Wc, p + q1.ob, true, h1[k], st, q1.Wc_tc));
+        U_TRY(conv3(ns, q2.ap, q2.b, h1[k], q2.Wc, p + q2.ob, true, h2[k], st, q2.Wc_tc));
         return OTM_OK;
     }
 
@@ -397,7 +471,7 @@ struct otm_unet {
                                                                           h1[0]);
                 g_launches += 1;
                 U_LAUNCH();
-                U_TRY(conv3(side[0], q2.ap, q2.b, h1[0], q2.Wc, p + q2.ob, true, h2[0], st));
+                U_TRY(conv3(side[0], q2.ap, q2.b, h1[0], q2.Wc, p + q2.ob, true, h2[0], st, q2.Wc_tc));
             }
         }
         // D2 <- (E3, E2), D1 <- (D2, E1), D0 <- (D1, E0)
@@ -428,12 +502,12 @@ struct otm_unet {
         g_launches += 1;
         U_LAUNCH();
         U_TRY(conv3_wgrad(ns, q2.ap, q2.a, q2.b, h1[k], G2, g + q2.oW, g + q2.ob, st));
-        U_TRY(conv3(ns, q2.b, q2.ap, G2, q2.Wt, nullptr, false, G1, st));
+        U_TRY(conv3(ns, q2.b, q2.ap, G2, q2.Wt, nullptr, false, G1, st, q2.Wt_tc));
         otm::nn::k_relu_mask<<<elt_grid(N * q1.b), 256, 0, st>>>(N * q1.b, G1, h1[k]);
         g_launches += 1;
         U_LAUNCH();
         U_TRY(conv3_wgrad(ns, q1.ap, q1.a, q1.b, block_in(k), G1, g + q1.oW, g + q1.ob, st));
-        if (dx) U_TRY(conv3(ns, q1.b, q1.ap, G1, q1.Wt, nullptr, false, dx, st));
+        if (dx) U_TRY(conv3(ns, q1.b, q1.ap, G1, q1.Wt, nullptr, false, dx, st, q1.Wt_tc));
         return OTM_OK;
     }
 
@@ -638,7 +712,7 @@ OTM_API otm_status otm_op_conv3(int n, int cin, int cout, const void* in, const 
     cudaStream_t st = (cudaStream_t)stream;
     U_TRY(conv3(n, cin, cout, (const bf16*)in, (const bf16*)w, bias, relu != 0, (bf16*)out, st));
     U_CU(cudaStreamSynchronize(st));
-    return OTM_OK;
+    return conv_flag("otm_op_conv3");
 }
 
 OTM_API otm_status otm_op_conv3_dgrad(int n, int cin, int cout, const void* g, const float* w, void* dx,
@@ -665,7 +739,7 @@ OTM_API otm_status otm_op_conv3_dgrad(int n, int cin, int cout, const void* g, c
     cudaFreeAsync(wt, st);
     if (s2 != OTM_OK) return s2;
     U_CU(cudaStreamSynchronize(st));
-    return OTM_OK;
+    return conv_flag("otm_op_conv3_dgrad");
 }
 
 OTM_API otm_status otm_op_conv3_wgrad(int n, int cin, int cout, const void* in, const void* g, float* dw, float* db,

@@ -95,7 +95,11 @@ def _unflat(vec, widths):
 
 @pytest.mark.parametrize("n,cin,cout,relu", [(4, 16, 16, 1), (6, 16, 32, 0), (8, 48, 16, 1),
                                              (5, 32, 64, 1), (8, 128, 64, 0), (3, 64, 128, 1),
-                                             (16, 16, 16, 1), (16, 48, 16, 0), (24, 32, 32, 1), (32, 16, 32, 0)])
+                                             (16, 16, 16, 1), (16, 48, 16, 0), (24, 32, 32, 1), (32, 16, 32, 0),
+                                             # tcgen05 tiles (16 | n): every halo wrap, 1-12 input
+                                             # chunks, N = 16 .. 192
+                                             (16, 32, 64, 1), (32, 48, 16, 1), (16, 192, 64, 0),
+                                             (32, 64, 128, 1), (16, 16, 192, 0), (48, 96, 32, 1)])
 def test_conv3_matches_definition(n, cin, cout, relu):
     otm = _otm()
     torch = _torch()
@@ -142,7 +146,7 @@ def test_conv3_weight_gradient_matches_definition(n, cin, cout):
 
 
 @pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32), (16, 48, 16),
-                                        (16, 16, 32), (8, 128, 64), (24, 32, 16)])
+                                        (16, 16, 32), (8, 128, 64), (24, 32, 16), (32, 96, 32), (16, 64, 128)])
 def test_conv3_input_gradient_matches_definition(n, cin, cout):
     """The network's input-gradient path -- the FP32 weights packed by
     k_pack_w into the tap-flipped, transposed BF16 copy, then the forward
