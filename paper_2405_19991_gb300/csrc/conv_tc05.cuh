@@ -169,5 +169,165 @@ k_conv3_tc(int n, int cin, int cout, const __nv_bfloat16* __restrict__ in, const
     if (warp == 0) tc_dealloc(tmem, ncols);
 }
 
+
+// ---------------------------------------------------------------------------
+// Pipelined form for layers whose weights fit in shared memory: a CTA owns
+// the 8 x 16 tile column at (x0, y0) over a range of z-planes and keeps the
+// weights of all input chunks resident.  Halo planes (10 x 18 voxels, all
+// channels, layout [chunk][half][180 voxels][16 B]) sit in a ring of five
+// slots: output plane z reads halo planes z - 1, z, z + 1, and while its MMAs
+// run, plane z + 2 is being copied in (cp.async).  A slot is refilled once
+// the MMAs of every output plane that read it have completed (five slots: the
+// refill of plane z + 2 replaces plane z - 3, last read by output plane
+// z - 2, whose completion the epilogue of plane z - 2 has already waited
+// for).  The accumulators are double-buffered in tensor memory, so the
+// epilogue of plane z - 1 (tcgen05.ld, bias, ReLU, BF16 store) overlaps the
+// MMAs of plane z.
+constexpr int kTcRing = 5;
+constexpr int kTcPlaneVox = kTcHX * kTcHY;   // 180
+__host__ __device__ inline size_t conv3_tcz_smem(int cin, int cout) {
+    const int nch = cin / 16;
+    return (size_t)nch * conv3_tc_wbytes(cout) + (size_t)kTcRing * nch * 2 * kTcPlaneVox * 16 + 128;
+}
+inline bool conv3_tcz_ok(int n, int cin, int cout) {
+    return conv3_tc_ok(n, cin, cout) && 2 * cout <= 256 && conv3_tcz_smem(cin, cout) <= 200 * 1024;
+}
+
+template <bool RELU>
+static __global__ void __launch_bounds__(128)
+k_conv3_tcz(int n, int cin, int cout, int m, const __nv_bfloat16* __restrict__ in,
+            const __nv_bfloat16* __restrict__ wtc, const float* __restrict__ bias, __nv_bfloat16* __restrict__ out,
+            int* err) {
+    extern __shared__ unsigned char tcz_smem_raw[];
+    __shared__ __align__(8) uint64_t mma_done[2];
+    __shared__ uint32_t tmem_slot;
+    unsigned char* sm = tcz_smem_raw + ((128u - (smem_u32(tcz_smem_raw) & 127u)) & 127u);
+    const int nch = cin / 16;
+    const int wbytes = conv3_tc_wbytes(cout);
+    unsigned char* wts = sm;                                   // [nch][27][2][cout][16 B]
+    unsigned char* ring = sm + (size_t)nch * wbytes;           // [R][nch][2][180][16 B]
+    const int plane_bytes = nch * 2 * kTcPlaneVox * 16;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ntx = n / kTcX, nty = n / kTcY;
+    const int col = blockIdx.x % (ntx * nty), zc = blockIdx.x / (ntx * nty);
+    const int x0 = (col % ntx) * kTcX, y0 = (col / ntx) * kTcY;
+    const int z0 = zc * n / m, z1 = (zc + 1) * n / m, P = z1 - z0;
+    const uint32_t ncols = conv3_tc_cols(2 * cout);
+
+    if (warp == 0) tc_alloc(&tmem_slot, ncols);
+    if (tid == 0) {
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
+        fence_mbar_init();
+    }
+    // halo plane q (global plane z0 - 1 + q) into its ring slot
+    auto load_plane = [&](int q) {
+        int gz = z0 - 1 + q;
+        gz += gz < 0 ? n : (gz >= n ? -n : 0);
+        unsigned char* dst = ring + (size_t)(q % kTcRing) * plane_bytes;
+        for (int e = tid; e < nch * 2 * kTcPlaneVox; e += 128) {
+            const int ck = e / (2 * kTcPlaneVox), rem = e - ck * 2 * kTcPlaneVox;
+            const int half = rem / kTcPlaneVox, h = rem - half * kTcPlaneVox;
+            int gx = x0 + h % kTcHX - 1, gy = y0 + h / kTcHX - 1;
+            gx += gx < 0 ? n : (gx >= n ? -n : 0);
+            gy += gy < 0 ? n : (gy >= n ? -n : 0);
+            const size_t v = (size_t)gx + (size_t)n * ((size_t)gy + (size_t)n * gz);
+            cp_async16(dst + (size_t)e * 16, in + v * cin + ck * 16 + half * 8);
+        }
+    };
+    // prologue: the weights and halo planes q = 0, 1, 2 (output plane 0)
+    for (int e = tid; e < nch * wbytes / 16; e += 128)
+        cp_async16(wts + (size_t)e * 16, reinterpret_cast<const unsigned char*>(wtc) + (size_t)e * 16);
+    load_plane(0);
+    load_plane(1);
+    load_plane(2);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc = tc_idesc_bf16(128, cout);
+    const uint32_t ring_s = smem_u32(ring), wts_s = smem_u32(wts);
+    const int r = warp * 32 + lane;   // this thread's accumulator row = voxel of the tile
+    const size_t vrow = (size_t)(x0 + (r & 7)) + (size_t)n * (size_t)(y0 + (r >> 3));
+    bool ok = true;
+    int issued = 0;   // planes whose MMAs were issued
+
+    auto epilogue = [&](int i) -> bool {
+        // wait for plane i's MMAs (bounded), then read its accumulator buffer
+        if (!mbar_wait_bounded(&mma_done[i & 1], (uint32_t)((i >> 1) & 1))) return false;
+        tc_fence_after();
+        __nv_bfloat16* o = out + (vrow + (size_t)n * n * (size_t)(z0 + i)) * cout;
+        for (int c0 = 0; c0 < cout; c0 += 16) {
+            float acc[16];
+            tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((i & 1) * cout + c0), acc);
+            uint32_t pk[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                float a0 = acc[2 * k] + (bias ? bias[c0 + 2 * k] : 0.f);
+                float a1 = acc[2 * k + 1] + (bias ? bias[c0 + 2 * k + 1] : 0.f);
+                if (RELU) {
+                    a0 = fmaxf(a0, 0.f);
+                    a1 = fmaxf(a1, 0.f);
+                }
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(a0, a1);
+                pk[k] = *reinterpret_cast<const uint32_t*>(&h2);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(o + c0);
+            dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        tc_fence_before();
+        return true;
+    };
+
+    for (int i = 0; i < P; ++i) {
+        // a. prefetch halo plane q = i + 3 (needed by output plane i + 1);
+        //    its slot last served output plane i - 2, complete since the
+        //    epilogue of plane i - 2 (previous trip)
+        if (i + 3 <= P + 1) load_plane(i + 3);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // b. halo planes i .. i + 2 landed (all groups but the newest)
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        fence_proxy_async_smem();
+        __syncthreads();
+        // c. MMAs of output plane i into accumulator buffer i & 1
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t dcol = tmem + (uint32_t)((i & 1) * cout);
+            for (int ck = 0; ck < nch; ++ck)
+                for (int t = 0; t < 27; ++t) {
+                    const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;   // offsets + 1
+                    const uint32_t a_addr = ring_s + (uint32_t)(((i + dz) % kTcRing) * plane_bytes) +
+                                            (uint32_t)((ck * 2 * kTcPlaneVox + dx + kTcHX * dy) * 16);
+                    const uint64_t adesc = tc_smem_desc(a_addr, kTcPlaneVox * 16, kTcHX * 16);
+                    const uint64_t bdesc =
+                        tc_smem_desc(wts_s + (uint32_t)((ck * 27 + t) * 2 * cout * 16), cout * 16, 128);
+                    tc_mma_bf16(dcol, adesc, bdesc, idesc, (ck > 0 || t > 0) ? 1u : 0u);
+                }
+            tc_commit(&mma_done[i & 1]);
+        }
+        issued = i + 1;
+        // d. epilogue of plane i - 1 while plane i's MMAs run
+        if (i >= 1) ok = epilogue(i - 1);
+        if (__syncthreads_or(!ok)) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok && P >= 1) ok = epilogue(P - 1);
+    if (!ok) {
+        if (tid == 0 && err) *err = 1;
+        // the MMAs still in flight finish before their operands and tensor
+        // memory go away (bounded waits on the last two planes issued)
+        for (int i = issued - 2 < 0 ? 0 : issued - 2; i < issued; ++i)
+            (void)mbar_wait_bounded(&mma_done[i & 1], (uint32_t)((i >> 1) & 1));
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, ncols);
+}
+
 }  // namespace nn
 }  // namespace otm

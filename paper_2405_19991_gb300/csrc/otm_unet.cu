@@ -92,12 +92,16 @@ cudaError_t tile_prepare() {
     return e;
 }
 
-// Convolution form: 0 tcgen05 (where it applies), 1 the mma.sync kernels
-// (OTM_CONV=mma), for comparisons.
+// Convolution form: 0 tcgen05 one-tile (where it applies), 2 the tcgen05
+// z-march form where it applies (OTM_CONV=z; bitwise the same, measured
+// slower: its MMA issue waits behind each plane's epilogue and loads), 1 the
+// mma.sync kernels (OTM_CONV=mma), for comparisons.
 int conv_choice() {
     static int c = [] {
         const char* e = getenv("OTM_CONV");
-        return e && e[0] == 'm' ? 1 : 0;
+        if (e && e[0] == 'm') return 1;
+        if (e && e[0] == 'z') return 2;
+        return 0;
     }();
     return c;
 }
@@ -116,8 +120,9 @@ otm_status conv_flag(const char* what) {
     return ufail(OTM_ETIMEOUT, std::string(what) + ": a bounded wait for the tensor-core MMAs ran out");
 }
 
-// Opt in to the tcgen05 kernel's dynamic shared memory, only ever raising it.
-template <bool RL>
+// Opt in to a tcgen05 kernel's dynamic shared memory, only ever raising it
+// (Z: the pipelined z-march form).
+template <bool RL, bool Z>
 cudaError_t tc_prepare(size_t bytes) {
     static std::mutex m;
     static size_t granted[64] = {};
@@ -127,9 +132,28 @@ cudaError_t tc_prepare(size_t bytes) {
     if (dev < 0 || dev >= 64) dev = 0;
     if (bytes <= granted[dev]) return cudaSuccess;
     const cudaError_t e =
-        cudaFuncSetAttribute(otm::nn::k_conv3_tc<RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        Z ? cudaFuncSetAttribute(otm::nn::k_conv3_tcz<RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+          : cudaFuncSetAttribute(otm::nn::k_conv3_tc<RL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) granted[dev] = bytes;
     return e;
+}
+
+// z-chunks of the pipelined form: one wave of resident CTAs over the tile
+// columns (OTM_CONV_M overrides, for sweeps).
+template <bool RL>
+int tcz_chunks(int n, int cin, int cout) {
+    const char* e = getenv("OTM_CONV_M");
+    if (e && atoi(e) >= 1 && atoi(e) <= n) return atoi(e);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, otm::nn::k_conv3_tcz<RL>, 128,
+                                                      otm::nn::conv3_tcz_smem(cin, cout)) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const long long cols = (long long)(n / otm::nn::kTcX) * (n / otm::nn::kTcY);
+    long long mm = ((long long)per_sm * sm_count() + cols - 1) / cols;
+    if (mm < 1) mm = 1;
+    if (mm > n / 2) mm = n / 2;
+    return (int)mm;
 }
 
 // out = act(conv3(in) + bias).  wtc: the weights already in the tcgen05
@@ -138,9 +162,11 @@ cudaError_t tc_prepare(size_t bytes) {
 otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const float* bias, bool relu, bf16* out,
                  cudaStream_t st, const bf16* wtc = nullptr) {
     const size_t N = (size_t)n * n * n;
-    if (conv_choice() == 0 && otm::nn::conv3_tc_ok(n, cin, cout)) {
-        const size_t smem = otm::nn::conv3_tc_smem(cout);
-        const cudaError_t e = relu ? tc_prepare<true>(smem) : tc_prepare<false>(smem);
+    if (conv_choice() != 1 && otm::nn::conv3_tc_ok(n, cin, cout)) {
+        const bool zform = conv_choice() == 2 && otm::nn::conv3_tcz_ok(n, cin, cout);
+        const size_t smem = zform ? otm::nn::conv3_tcz_smem(cin, cout) : otm::nn::conv3_tc_smem(cout);
+        const cudaError_t e = zform ? (relu ? tc_prepare<true, true>(smem) : tc_prepare<false, true>(smem))
+                                    : (relu ? tc_prepare<true, false>(smem) : tc_prepare<false, false>(smem));
         if (e != cudaSuccess) return ufail(OTM_ECUDA, std::string("conv3 (tcgen05) shared-memory opt-in: ") + cudaGetErrorString(e));
         bf16* scratch = nullptr;
         if (!wtc) {
@@ -152,11 +178,20 @@ otm_status conv3(int n, int cin, int cout, const bf16* in, const bf16* w, const 
         }
         int* err = nullptr;
         U_CU(cudaGetSymbolAddress((void**)&err, g_conv_err));
-        const unsigned grid = (unsigned)((n / otm::nn::kTcX) * (n / otm::nn::kTcY) * n);
-        if (relu)
-            otm::nn::k_conv3_tc<true><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
-        else
-            otm::nn::k_conv3_tc<false><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
+        if (zform) {
+            const int m = relu ? tcz_chunks<true>(n, cin, cout) : tcz_chunks<false>(n, cin, cout);
+            const unsigned grid = (unsigned)((n / otm::nn::kTcX) * (n / otm::nn::kTcY) * m);
+            if (relu)
+                otm::nn::k_conv3_tcz<true><<<grid, 128, smem, st>>>(n, cin, cout, m, in, wtc, bias, out, err);
+            else
+                otm::nn::k_conv3_tcz<false><<<grid, 128, smem, st>>>(n, cin, cout, m, in, wtc, bias, out, err);
+        } else {
+            const unsigned grid = (unsigned)((n / otm::nn::kTcX) * (n / otm::nn::kTcY) * n);
+            if (relu)
+                otm::nn::k_conv3_tc<true><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
+            else
+                otm::nn::k_conv3_tc<false><<<grid, 128, smem, st>>>(n, cin, cout, in, wtc, bias, out, err);
+        }
         g_launches += 1;
         if (scratch) cudaFreeAsync(scratch, st);
         U_LAUNCH();

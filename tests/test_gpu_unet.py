@@ -123,6 +123,45 @@ def test_conv3_matches_definition(n, cin, cout, relu):
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) / tol)
 
 
+_CONV_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+n, cin, cout, path = int(sys.argv[2]), int(sys.argv[3]), int(sys.argv[4]), sys.argv[5]
+rng = np.random.default_rng(n + cin + cout)
+x = torch.as_tensor(rng.standard_normal((n ** 3, cin)), dtype=torch.float32).to(torch.bfloat16).cuda()
+w = torch.as_tensor(rng.standard_normal((27, cin, cout)) / np.sqrt(27 * cin), dtype=torch.float32)
+w = w.to(torch.bfloat16).cuda()
+b = torch.as_tensor(rng.standard_normal(cout) * 0.1, dtype=torch.float32).cuda()
+y = torch.empty((n ** 3, cout), dtype=torch.bfloat16, device="cuda")
+otm.otm_op_conv3(n, cin, cout, x, w, b, 1, y)
+np.save(path, y.view(torch.int16).cpu().numpy())
+"""
+
+
+@pytest.mark.parametrize("n,cin,cout", [(16, 16, 16), (32, 48, 16), (16, 32, 64)])
+def test_conv3_tcgen05_forms_are_bitwise_equal(n, cin, cout, tmp_path):
+    """The pipelined z-march form and the one-tile form issue the same MMAs
+    per voxel in the same order (input chunks outer, taps inner): same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    got = []
+    for zform in (False, True):
+        path = str(tmp_path / f"z{int(zform)}.npy")
+        env = dict(os.environ)
+        env.pop("OTM_CONV", None)
+        if zform:
+            env["OTM_CONV"] = "z"
+        subprocess.run([sys.executable, "-c", _CONV_SCRIPT, root, str(n), str(cin), str(cout), path], env=env,
+                       check=True, timeout=300)
+        got.append(np.load(path))
+    assert np.array_equal(got[0], got[1])
+
+
 @pytest.mark.parametrize("n,cin,cout", [(4, 16, 16), (6, 32, 16), (8, 16, 64), (5, 48, 32), (16, 48, 16),
                                         (16, 16, 32), (32, 32, 32), (24, 16, 16)])
 def test_conv3_weight_gradient_matches_definition(n, cin, cout):
