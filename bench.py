@@ -53,7 +53,10 @@ def parse():
     ap.add_argument("--workload", default="ortho128", choices=["ortho128", "aniso128mixed", "aniso256mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the cold / mixed / learned+mixed forms")
-    ap.add_argument("--train-steps", type=int, default=240, help="Adam steps of the warm-start network")
+    ap.add_argument("--train-steps", type=int, default=2000, help="Adam steps of the warm-start network")
+    ap.add_argument("--ws-histories", type=int, default=10,
+                    help="design histories per recipe (orthotropic, anisotropic, random SPD) for the network's pairs")
+    ap.add_argument("--ws-iters", type=int, default=34, help="design iterations (pairs) per history")
     ap.add_argument("--cpu-budget", type=float, default=25.0, help="seconds of oracle CG in the CPU sample")
     return ap.parse_args()
 
@@ -212,11 +215,14 @@ def aggregate_rate(units_per_rank, world, seconds_max):
 
 
 # ------------------------------------------------------------------ forms
-def timed_steps(otm, ctx, stream, steps, warmup):
-    """Device time of `steps` OC iterations after `warmup` untimed ones."""
+def timed_steps(otm, ctx, stream, steps, warmup, warm_infos=None):
+    """Device time of `steps` OC iterations after `warmup` untimed ones (whose
+    reports go to warm_infos when given)."""
     import torch
     for _ in range(warmup):
-        otm.otm_step(ctx)
+        info, _ = otm.otm_step(ctx)
+        if warm_infos is not None:
+            warm_infos.append(info.as_dict())
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -308,11 +314,13 @@ def unet_rate(otm, unet, n, widths, buf, stream, reps=10):
             "note": "whole forward incl. pooling, concatenation and head kernels; BF16 mma.sync"}
 
 
-def run_forms(args, wl, dev, stream, rank, plain_value):
+def run_forms(args, wl, dev, stream, rank, plain_value, plain_ms, plain_iters):
     """Cold start, BF16 V-cycle, and learned warm start + BF16 V-cycle on the
-    benchmark workload; the warm-start network (widths 16/32/64/128) is
-    trained on (filtered density, solution) pairs from the design histories
-    of three other seeds before its form is timed."""
+    benchmark workload.  The warm-start network (widths 16/32/64/128) is
+    trained before its form is timed, on (filtered density, solution) pairs
+    from the design histories of other seeds and targets; the form reports
+    every candidate start's true residual, the network's cold starts on
+    held-out designs, and the measured cost model of a prediction."""
     import torch
     from paper_2405_19991_gb300 import otm, warmstart
 
@@ -331,7 +339,8 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
             otm.otm_set_density(ctx, rho0.ctypes.data, 0)
             if unet is not None:
                 otm.otm_set_predictor(ctx, unet, scale)
-            ms, infos = timed_steps(otm, ctx, stream, args.steps, args.warmup)
+            warm = []
+            ms, infos = timed_steps(otm, ctx, stream, args.steps, args.warmup, warm)
         finally:
             otm.otm_destroy(ctx)
         v = args.steps / (ms * 1e-3)
@@ -349,39 +358,126 @@ def run_forms(args, wl, dev, stream, rank, plain_value):
             rec["start_choices"] = {names[k]: v for k, v in sorted(counts.items())}
             rec["iterations_predictor_skipped"] = int(sum(1 for i in infos if i["ws_skipped"]))
             rec["predictions_that_paid"] = int(sum(1 for i in infos if i["ws_paid"]))
+            # per prediction and load case: the network's start and the previous
+            # solution plus the prediction's change, against the previous solution
+            ran = [i for i in warm + infos if i["ws_resid"][2][0] >= 0]   # warm-up and timed
+            rec["predictions"] = len(ran)
+            rec["_net_over_prev"] = [i["ws_resid"][2][c] / i["ws_resid"][1][c] for i in ran for c in range(3)
+                                     if i["ws_resid"][1][c] > 0]
+            delta = [i["ws_resid"][3][c] / i["ws_resid"][1][c] for i in ran for c in range(3)
+                     if i["ws_resid"][1][c] > 0 and i["ws_resid"][3][c] >= 0]
+            rec["candidate_residuals"] = {
+                "previous_solution_median": float(np.median([i["ws_resid"][1][c] for i in ran for c in range(3)]))
+                if ran else None,
+                "net_over_previous_median": float(np.median(rec["_net_over_prev"])) if rec["_net_over_prev"] else None,
+                "previous_plus_change_over_previous_median": float(np.median(delta)) if delta else None}
         out[name] = rec
 
     form("plain_fp32_cold_start", 1, otm.OTM_WS_NONE)
     out["batch_64_designs"] = run_batch(otm, args)
     form("mixed_bf16_vcycle_previous_start", 2, otm.OTM_WS_PREV)
-    # train the warm-start network on other seeds' histories
+
+    # ---- the warm-start network, trained on pairs from the design loop's own
+    # histories: three recipes at the benchmark size (the orthotropic and
+    # anisotropic targets, and random SPD targets with random volume
+    # fractions as in the batched workload), ws_histories seeds each
     t0 = time.perf_counter()
-    hist_iters, seeds = 20, (10, 11, 12)
-    buf = warmstart.PairBuffer(wl.n, hist_iters * len(seeds))
-    for sd in seeds:
-        warmstart.collect(params(1, otm.OTM_WS_PREV), W.initial_density(wl.n, wl.volfrac, sd), hist_iters, buf)
+    rng = np.random.default_rng(4242)
+    recipes = []
+    for h in range(args.ws_histories):
+        recipes.append((W.TARGET_ORTHOTROPIC, 0.3, 10 + h))
+        recipes.append((W.TARGET_ANISOTROPIC, 0.35, 100 + h))
+        recipes.append((tuple(float(t) for t in W.random_spd_target(rng)), float(rng.uniform(0.2, 0.45)), 200 + h))
+    buf = warmstart.PairBuffer(wl.n, len(recipes) * args.ws_iters)
+
+    def params_for(target, vf, prec=1, ws=otm.OTM_WS_PREV):
+        p = params(prec, ws)
+        for c in range(6):
+            p.kappa_target[c] = float(target[c])
+        p.volfrac = vf
+        return p
+
+    for target, vf, sd in recipes:
+        warmstart.collect(params_for(target, vf), W.initial_density(wl.n, vf, sd), args.ws_iters, buf)
+    torch.cuda.synchronize()
     t_collect = time.perf_counter() - t0
-    scale = warmstart.target_scale(buf)
+    scale = warmstart.target_scale(buf, sample=32)
     unet = otm.otm_unet_create(wl.n, (16, 32, 64, 128), 0, stream.cuda_stream)
     try:
         t0 = time.perf_counter()
-        losses = warmstart.train(unet, buf, args.train_steps, 1e-3, scale, seed=1, stream=stream.cuda_stream)
+        # Adam at 1e-3, the last quarter at 3e-4
+        s1 = (3 * args.train_steps) // 4
+        losses = warmstart.train(unet, buf, s1, 1e-3, scale, seed=1, stream=stream.cuda_stream)
+        losses += warmstart.train(unet, buf, args.train_steps - s1, 3e-4, scale, seed=2, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
-        held = warmstart.PairBuffer(wl.n, 4)
-        warmstart.collect(params(1, otm.OTM_WS_PREV), rho0, 4, held)
+        held = warmstart.PairBuffer(wl.n, 24)
+        for sd in (90, 91, 92):
+            warmstart.collect(params(1, otm.OTM_WS_PREV), W.initial_density(wl.n, wl.volfrac, sd), 8, held)
         held_loss = warmstart.evaluate(unet, held, scale, stream.cuda_stream)
         form("learned_start_mixed_bf16_vcycle", 2, otm.OTM_WS_LEARNED, unet, scale)
-        out["learned_start_mixed_bf16_vcycle"]["unet_forward"] = unet_rate(otm, unet, wl.n, (16, 32, 64, 128),
-                                                                           held, stream)
-        out["learned_start_mixed_bf16_vcycle"]["training"] = {
-            "pairs": buf.count, "histories": list(seeds), "iters_per_history": hist_iters,
-            "collect_s": t_collect, "adam_steps": args.train_steps, "lr": 1e-3, "train_s": t_train,
-            "ms_per_adam_step": t_train / max(args.train_steps, 1) * 1e3,
-            "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
-            "held_out_loss": held_loss, "params": otm.otm_unet_param_count(unet), "target": "chi / rms(chi)", "scale": scale}
+        lf = out["learned_start_mixed_bf16_vcycle"]
+        lf["unet_forward"] = unet_rate(otm, unet, wl.n, (16, 32, 64, 128), held, stream)
+        lf["training"] = {
+            "pairs": buf.count, "histories": len(recipes), "iters_per_history": args.ws_iters,
+            "recipes": "orthotropic vf 0.3, anisotropic vf 0.35, random SPD targets vf U[0.2, 0.45]",
+            "collect_s": t_collect, "adam_steps": args.train_steps, "lr": "1e-3, last quarter 3e-4",
+            "train_s": t_train, "ms_per_adam_step": t_train / max(args.train_steps, 1) * 1e3,
+            "loss_first100": float(np.mean(losses[:100])), "loss_last100": float(np.mean(losses[-100:])),
+            "held_out_loss": held_loss, "held_out": "seeds 90-92 of the benchmark recipe, 8 iterations each",
+            "params": otm.otm_unet_param_count(unet), "target": "chi / rms(chi)", "scale": scale}
+        # cold starts of held-out designs: the first design iteration from the
+        # zero start against the network's start (mixed V-cycle both; each
+        # context first steps another design so its graphs exist)
+        cold = {"zero": [], "learned": []}
+        for kind, ws in (("zero", otm.OTM_WS_NONE), ("learned", otm.OTM_WS_LEARNED)):
+            ctx = otm.otm_create_ex(params(2, ws))
+            try:
+                if ws == otm.OTM_WS_LEARNED:
+                    otm.otm_set_predictor(ctx, unet, scale)
+                r_w = W.initial_density(wl.n, wl.volfrac, 80).astype(np.float32)
+                otm.otm_set_density(ctx, r_w.ctypes.data, 0)
+                otm.otm_step(ctx)
+                for sd in range(93, 99):
+                    r0 = W.initial_density(wl.n, wl.volfrac, sd).astype(np.float32)
+                    otm.otm_set_density(ctx, r0.ctypes.data, 0)
+                    info, _ = otm.otm_step(ctx)
+                    d = info.as_dict()
+                    cold[kind].append({"cg_iters": max(d["cg_iters"]), "ms": d["stage_ms"][7],
+                                       "predict_ms": d["stage_ms"][1], "paid": d["ws_paid"],
+                                       "net_resid": max(d["ws_resid"][2]) if ws == otm.OTM_WS_LEARNED else None})
+            finally:
+                otm.otm_destroy(ctx)
+        lf["cold_start_held_out"] = {
+            "designs": "seeds 93-98 of the benchmark recipe, first design iteration (mixed V-cycle)",
+            "zero_start": {"mean_cg_iters": float(np.mean([c["cg_iters"] for c in cold["zero"]])),
+                           "mean_ms": float(np.mean([c["ms"] for c in cold["zero"]]))},
+            "learned_start": {"mean_cg_iters": float(np.mean([c["cg_iters"] for c in cold["learned"]])),
+                              "mean_ms": float(np.mean([c["ms"] for c in cold["learned"]])),
+                              "mean_predict_ms": float(np.mean([c["predict_ms"] for c in cold["learned"]])),
+                              "predictions_that_paid": int(sum(c["paid"] for c in cold["learned"])),
+                              "max_net_relative_residual": float(max(c["net_resid"] for c in cold["learned"]))}}
     finally:
         otm.otm_unet_destroy(unet)
+
+    # ---- cost model of the learned start (measured): a PCG iteration's
+    # marginal time, the V-cycle PCG's contraction per iteration, and what a
+    # prediction would have to reach to save iterations
+    lf = out["learned_start_mixed_bf16_vcycle"]
+    cold_f, warm_f = out["plain_fp32_cold_start"], {"ms_per_step": plain_ms, "mean_cg_iters": plain_iters}
+    t_it = (cold_f["ms_per_step"] - warm_f["ms_per_step"]) / max(cold_f["mean_cg_iters"] - warm_f["mean_cg_iters"], 1e-9)
+    rho_cg = (1e-6) ** (1.0 / max(cold_f["mean_cg_iters"], 1.0))
+    ratios = [r for r in lf.pop("_net_over_prev", []) if r > 0]
+    t_pred = lf["unet_forward"]["ms"]
+    lf["cost_model"] = {
+        "pcg_iteration_ms": t_it, "pcg_contraction_per_iteration": rho_cg,
+        "prediction_ms": t_pred,
+        "iterations_a_prediction_must_save": t_pred / t_it if t_it > 0 else None,
+        "residual_ratio_needed_vs_best_other_start": rho_cg ** max(1.0, np.ceil(t_pred / t_it)) if t_it > 0 else None,
+        "measured_net_over_previous_residual_median": float(np.median(ratios)) if ratios else None,
+        "measured_net_over_previous_residual_min": float(np.min(ratios)) if ratios else None,
+        "reading": "a start saves k PCG iterations only if its true residual is about rho_cg^k times the best other "
+                   "start's; it pays only if k * pcg_iteration_ms exceeds the prediction's time"}
     return out
 
 
@@ -538,7 +634,7 @@ def run_ours(args, rank, world):
     }
     otm.otm_destroy(ctx)
     if not args.no_forms and wl.n % 8 == 0:
-        forms = run_forms(args, wl, dev, stream, rank, value)
+        forms = run_forms(args, wl, dev, stream, rank, value, ms_max / args.steps, float(np.mean(cg)))
         forms = {"plain_fp32_previous_start": {"value": value, "unit": UNIT, "ms_per_step": ms_max / args.steps,
                                                "mean_cg_iters": float(np.mean(cg)), "vs_plain_fp32": 1.0},
                  **forms}

@@ -145,6 +145,10 @@ typedef struct otm_step_info {
                              2i: 0 zero, 1 previous solution, 2 predictor, 3 previous + predictor
                              change; bit 6 set: the predictor was skipped this iteration (back-off);
                              bit 7 set: the prediction paid (see otm_set_predictor) */
+    double ws_resid[4][3];  /* when the predictor ran: relative true residual ||f_i - K x0||/||f_i||
+                               of each candidate start x0 (index as in ws_choice: zero, previous
+                               solution, predictor, previous + predictor change) per load case;
+                               -1 for a candidate not scored, and every entry -1 otherwise */
 } otm_step_info;
 
 /* State of Alg. 1's adaptive volume bound. */

@@ -1577,6 +1577,8 @@ if (tma_pcg_.grid > 0)
         }
         otm_step_info loc;
         memset(&loc, 0, sizeof(loc));
+        for (auto& row : loc.ws_resid)
+            for (double& v : row) v = -1.0;
         const long long nl0 = nl_;
         otm_status sst = setup_and_solve(false, &loc);
         otm_status st = (sst == OTM_OK || sst == OTM_ENOCONV) ? tensor_and_sens(false) : sst;
@@ -1593,9 +1595,23 @@ if (tma_pcg_.grid > 0)
         return sst;
     }
 
+    // relative true residual of each scored candidate start (otm_step_info.ws_resid)
+    void fill_ws_resid(otm_step_info& loc) const {
+        for (int i = 0; i < 3; ++i) {
+            const double ff = ws_h->cand[kWsNet][3 + i];
+            auto rel = [&](int c) { return ff > 0 ? std::sqrt(ws_h->cand[c][i] / ff) : 0.0; };
+            loc.ws_resid[kWsZero][i] = ff > 0 ? 1.0 : 0.0;
+            loc.ws_resid[kWsPrev][i] = ws_had_prev ? rel(kWsPrev) : -1.0;
+            loc.ws_resid[kWsNet][i] = rel(kWsNet);
+            loc.ws_resid[kWsDelta][i] = ws_had_delta ? rel(kWsDelta) : -1.0;
+        }
+    }
+
     otm_status step(otm_step_info* info) override {
         otm_step_info loc;
         memset(&loc, 0, sizeof(loc));
+        for (auto& row : loc.ws_resid)
+            for (double& v : row) v = -1.0;
         const long long nl0 = nl_;
         OTM_CU(cudaEventRecord(ev[0], stream));
         const bool warm = have_prev && prm.warm_start != OTM_WS_NONE;
@@ -1604,6 +1620,7 @@ if (tma_pcg_.grid > 0)
         otm_status sst = setup_and_solve(warm, &loc, learned);
         if (learned && (sst == OTM_OK || sst == OTM_ENOCONV)) {
             if (ws_after_prediction()) loc.ws_choice |= 1 << 7;
+            fill_ws_resid(loc);
         }
         else if (attached) {
             --ws_wait;

@@ -81,6 +81,7 @@ class otm_step_info(C.Structure):
         ("stage_ms", C.c_float * 8),
         ("kernel_launches", C.c_int),
         ("ws_choice", C.c_int),
+        ("ws_resid", (C.c_double * 3) * 4),
     ]
 
     def as_dict(self):
@@ -90,7 +91,8 @@ class otm_step_info(C.Structure):
                     resid=list(self.resid), stage_ms=list(self.stage_ms),
                     kernel_launches=self.kernel_launches,
                     ws_choice=[(self.ws_choice >> (2 * i)) & 3 for i in range(3)],
-                    ws_skipped=bool(self.ws_choice & 64), ws_paid=bool(self.ws_choice & 128))
+                    ws_skipped=bool(self.ws_choice & 64), ws_paid=bool(self.ws_choice & 128),
+                    ws_resid=[[self.ws_resid[c][i] for i in range(3)] for c in range(4)])
 
 
 class otm_governor_state(C.Structure):
