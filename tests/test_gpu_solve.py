@@ -106,6 +106,31 @@ def test_128_solid_uniform_and_laminate(precision):
         otm.otm_destroy(ctx)
 
 
+def test_128_anisotropic_workload_kappa_against_oracle():
+    """The 128^3 anisotropic workload (volume fraction 0.35, r = 2, p = 3,
+    k_void = 1e-3, its seeded initial density) end to end: filter, SIMP,
+    loads, MG-PCG to 1e-6 and the tensor, FP32 and BF16-V-cycle paths, against
+    the oracle's own FP64 pipeline on the same density (Jacobi-PCG to 1e-8, a
+    tensor error far below the tolerances): FP32 <= 1e-6, mixed <= 1e-4
+    relative (Frobenius)."""
+    wl = W.ANISO_128
+    n = wl.n
+    rho = wl.rho0(np.float32)
+    rf = design.density_filter(n, rho.astype(np.float64), wl.rmin)
+    ref = fem.homogenize(n, design.simp(rf, wl.penal, wl.k_solid, wl.k_void), tol=1e-8)["kappa"]
+    for precision, tol in ((1, 1e-6), (2, 1e-4)):
+        ctx, otm = _ctx(n, precision, wl.cg_tol, rmin=wl.rmin, target=wl.kappa_target)
+        try:
+            kap, info, st = _homogenize_host(ctx, otm, rho)
+            assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+            assert max(info.resid) <= wl.cg_tol * 1.0001
+            err = rel_fro(kap, ref)
+            print(f"precision {precision}: kappa relative error {err:.2e}")
+            assert err <= tol, (precision, err, kap, ref)
+        finally:
+            otm.otm_destroy(ctx)
+
+
 def test_128_sampled_residual_tensor_and_sensitivity():
     """The benchmark configuration (128^3, r = 2, FP32, cg_tol 1e-6): the
     oracle recomputes, from the GPU's own k and corrector fields, the
