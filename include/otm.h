@@ -201,9 +201,10 @@ OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
 /* The launch configuration a context runs with (Alg. 3's V-cycle and the
  * Sec. 2.4 stencil).  Reading it builds the step's CUDA graphs first (as
  * otm_step would), so an automatic choice has been made.
- *   stencil_form    fine stencil: 0 z-reuse paired, 1 tiled, 2 gather,
- *                   3 paired three-plane ring (OTM_STENCIL)
- *   stencil_chunks  z-chunks per column of the z-reuse form (0: not used)
+ *   stencil_form    fine stencil: 0 TMA-staged z-march, 1 shared-memory
+ *                   tiled, 2 gather (OTM_STENCIL)
+ *   stencil_chunks  z-chunks per row block of the TMA-staged form (0: not
+ *                   used)
  *   levels, coarsest_n   the hierarchy: level count and the coarsest side
  *   cluster_maxn    levels with at most this many nodes per side run in one
  *                   thread-block cluster launch (0: no cluster)
@@ -217,6 +218,10 @@ OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
  *   tune_us         measured time of one V-cycle per candidate, in the order
  *                   (maxn 8, 8 CTAs), (8, 16), (16, 8), (16, 16); 0 when not
  *                   measured
+ *   gs_form         fine Gauss-Seidel group pass: 0 TMA-staged z-march,
+ *                   1 gather (OTM_GS); every form gives the same bits
+ *   gs_chunks       runs of output planes per row block of the TMA-staged
+ *                   group pass (0: not used)
  * Errors: OTM_EINVAL for NULL arguments; CUDA errors as OTM_ECUDA. */
 typedef struct {
     int stencil_form;
@@ -228,6 +233,8 @@ typedef struct {
     int tail_maxn;
     int autotuned;
     double tune_us[4];
+    int gs_form;
+    int gs_chunks;
 } otm_config;
 OTM_API otm_status otm_get_config(otm_ctx* ctx, otm_config* out);
 

@@ -9,6 +9,7 @@
 #include "kernels_design.cuh"
 #include "kernels_fine.cuh"
 #include "kernels_tma.cuh"
+#include "kernels_gs_tma.cuh"
 #include "kernels_tiled.cuh"
 #include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
@@ -194,6 +195,24 @@ otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* 
     OpCtx oc(stream);
     if (colour >= 8) {   // a group pass (both x parities), as the solver runs it
         const int group = colour - 8;
+        if (sizeof(R) == 4 && otm::gs_choice() == 0) {
+            // the TMA-staged form and launch shape the solver uses at this size
+            int sms = 0, dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            otm::TmaLaunch tl;
+            otm::TmaGsMaps maps;
+            if (otm::gs_tma_launch_shape<float, float>(tl, n, sms) &&
+                otm::gs_tma_make_maps<float, float>(maps, n, k, T, f)) {
+                int* err = nullptr;
+                if (cudaGetSymbolAddress((void**)&err, g_op_err) != cudaSuccess)
+                    return op_fail(OTM_ECUDA, "otm_op_gs_colour: flag");
+                otm::launch_pdl_smem(otm::gs_tma_kernel<float, float>(n), tl.grid, tl.threads, tl.smem, oc.st, maps, n,
+                                     tl.ty, tl.m, tl.stages, group, (float*)T, err);
+                return finish_flagged(oc.st, "otm_op_gs_colour");
+            }
+            cudaGetLastError();
+        }
         otm::k_gs_fine<false, R, R, R><<<OTM_ROWS_CFG(oc.rows(n, (n / 2) * (n / 2))), 0, oc.st>>>(
             n, group, -1, (const R*)k, (const R*)f, (R*)T);
     } else {

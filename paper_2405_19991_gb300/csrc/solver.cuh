@@ -19,6 +19,7 @@
 #include "kernels_cluster.cuh"
 #include "kernels_warprow.cuh"
 #include "kernels_tma.cuh"
+#include "kernels_gs_tma.cuh"
 #include "kernels_ws.cuh"
 #include "otm_internal.cuh"
 #include "unet_api.cuh"
@@ -463,6 +464,12 @@ class Solver : public SolverBase {
                     tma_vc_.grid = 0;
                 cudaGetLastError();   // a refused shape leaves the older forms in place
             }
+            if (gs_choice() == 0) {
+                if (gs_tma_launch_shape<S, float>(tma_gs_, n, sm_count) &&
+                    !gs_tma_make_maps<S, float>(maps_gs_, n, k_vc, z, r))
+                    tma_gs_.grid = 0;
+                cudaGetLastError();
+            }
         }
         for (int l = 1; l < nlev; ++l) {
             // coarse levels are node-major: fields [N][4], stencil [N][CL<S>::AW]
@@ -760,7 +767,18 @@ class Solver : public SolverBase {
     }
 
     // One fine-grid Gauss-Seidel group pass.
+    // TMA-staged fine group pass (FP32 or BF16 storage, f in FP32); grid 0
+    // when the gather form runs
+    TmaLaunch tma_gs_;
+    TmaGsMaps maps_gs_;
     void fine_gs_pass(int gidx) {
+        if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
+            if (tma_gs_.grid > 0) {
+                launch_pdl_smem(gs_tma_kernel<S, float>(n), tma_gs_.grid, tma_gs_.threads, tma_gs_.smem, stream,
+                                maps_gs_, n, tma_gs_.ty, tma_gs_.m, tma_gs_.stages, gidx, z, &ps->dev_err);
+                return;
+            }
+        }
         launch_pdl(k_gs_fine<false, S, R, S>, gs_grid(), rl(n, (n / 2) * (n / 2)).block, stream, n, gidx, -1, k_vc, r,
                    z);
     }
@@ -1309,6 +1327,8 @@ if (tma_pcg_.grid > 0)
         out->tail_maxn = tail_maxn;
         out->autotuned = autotuned_;
         for (int c = 0; c < 4; ++c) out->tune_us[c] = tune_us_[c];
+        out->gs_form = tma_gs_.grid > 0 ? 0 : 1;
+        out->gs_chunks = tma_gs_.grid > 0 ? tma_gs_.m : 0;
         return OTM_OK;
     }
 

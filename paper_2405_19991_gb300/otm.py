@@ -61,6 +61,8 @@ class otm_config(C.Structure):
         ("tail_maxn", C.c_int),
         ("autotuned", C.c_int),
         ("tune_us", C.c_double * 4),
+        ("gs_form", C.c_int),
+        ("gs_chunks", C.c_int),
     ]
 
     def as_dict(self):

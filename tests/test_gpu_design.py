@@ -319,3 +319,57 @@ def test_coarse_launch_configurations_are_bitwise_equal(precision, monkeypatch):
         assert np.array_equal(outs[0][0], o[0])
         assert np.array_equal(outs[0][1].view(np.uint32), o[1].view(np.uint32))
         assert outs[0][2] == o[2]
+
+
+_GS_TRAJ = r"""
+import sys, json
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+import workloads as W
+n, prec, out = int(sys.argv[2]), int(sys.argv[3]), sys.argv[4]
+p = otm.otm_params_default(n=n, precision=prec, cg_tol=1e-6, rmin=2.0, kappa_target=W.TARGET_ORTHOTROPIC,
+                           cg_maxit=3000)
+ctx = otm.otm_create_ex(p)
+rho0 = W.initial_density(n, 0.3, 6).astype(np.float32)
+otm.otm_set_density(ctx, rho0.ctypes.data, 0)
+cfg = otm.otm_get_config(ctx)
+infos, st = otm.otm_run(ctx, 3)
+chi = np.empty(3 * n ** 3, np.float32)
+otm.otm_get_field(ctx, otm.OTM_FIELD_CHI, chi.ctypes.data, 3 * n ** 3, 0)
+rho = np.empty(n ** 3, np.float32)
+otm.otm_get_density(ctx, rho.ctypes.data, 0)
+np.savez(out, chi=chi, rho=rho, g=np.array([i.g for i in infos]),
+         iters=np.array([list(i.cg_iters) for i in infos]))
+print("CFG", json.dumps({"gs_form": cfg["gs_form"], "gs_chunks": cfg["gs_chunks"], "st": st}))
+otm.otm_destroy(ctx)
+"""
+
+
+@pytest.mark.parametrize("n,precision", [(64, 1), (64, 2), (128, 2)])
+def test_gs_forms_give_the_same_trajectory(n, precision, tmp_path):
+    """The fine Gauss-Seidel group pass in its TMA-staged form and in the
+    gather form, inside the solver (FP32 storage, and BF16 storage with an
+    FP32 right-hand side on the mixed path): three design iterations give the
+    same density, the same chi to the bit and the same PCG iteration counts."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for form in ("tma", "gather"):
+        path = str(tmp_path / f"{form}.npz")
+        r = subprocess.run([sys.executable, "-c", _GS_TRAJ, root, str(n), str(precision), path],
+                           env=dict(os.environ, OTM_GS=form), capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        cfg = json.loads(r.stdout.split("CFG")[1].strip().splitlines()[0])
+        assert cfg["st"] == 0, cfg
+        assert cfg["gs_form"] == (0 if form == "tma" else 1), cfg
+        assert (cfg["gs_chunks"] >= 1) == (form == "tma"), cfg
+        res[form] = np.load(path)
+    a, b = res["tma"], res["gather"]
+    assert np.array_equal(a["iters"], b["iters"])
+    assert np.array_equal(a["g"], b["g"])
+    assert np.array_equal(a["rho"].view(np.uint32), b["rho"].view(np.uint32))
+    assert np.array_equal(a["chi"].view(np.uint32), b["chi"].view(np.uint32))

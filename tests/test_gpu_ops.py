@@ -293,6 +293,58 @@ def test_stencil_forms_are_bitwise_equal(n, tmp_path):
         assert np.array_equal(got["tma"].view(np.uint32), got[form].view(np.uint32)), form
 
 
+_GS_FORM_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+import workloads as W
+n, out = int(sys.argv[2]), sys.argv[3]
+rho = W.random_density(n, 31)
+k = torch.as_tensor(1e-3 + rho ** 3 * (1 - 1e-3), dtype=torch.float32, device="cuda").contiguous()
+f = torch.as_tensor(W.random_field(n, 32).ravel(), dtype=torch.float32, device="cuda").contiguous()
+T = torch.as_tensor(W.random_field(n, 33).ravel(), dtype=torch.float32, device="cuda").contiguous()
+outs = []
+for g in (0, 1, 2, 3, 2, 0):
+    otm.otm_op_gs_colour(1, n, k, f, T, 8 + g)
+    outs.append(T.cpu().numpy())
+np.save(out, np.stack(outs))
+"""
+
+
+def _gs_form_run(n, path, **env_extra):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, **env_extra)
+    subprocess.run([sys.executable, "-c", _GS_FORM_SCRIPT, root, str(n), path], env=env, check=True, timeout=300)
+    return np.load(path)
+
+
+@pytest.mark.parametrize("n", [32, 64, 96, 128, 256])
+def test_gs_forms_are_bitwise_equal(n, tmp_path):
+    """The TMA-staged group pass takes each node's sum in the gather kernel's
+    order with the same update expression: after each of six passes over
+    all four groups (both y and z parities, so every periodic wrap of the
+    staged rows and planes), the same bits.  n = 96 runs the form compiled
+    for a run-time n."""
+    a = _gs_form_run(n, str(tmp_path / "tma.npy"), OTM_GS="tma")
+    b = _gs_form_run(n, str(tmp_path / "gather.npy"), OTM_GS="gather")
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+@pytest.mark.parametrize("m,stages", [(1, 4), (3, 6), (7, 8), (64, 5)])
+def test_gs_tma_any_runs_and_ring_depth(m, stages, tmp_path):
+    """Runs of output planes (one run marching a whole column through the
+    ring many times, ragged runs, one plane per run) and ring depths 4..8:
+    the same bits as the gather form."""
+    a = _gs_form_run(128, str(tmp_path / "a.npy"), OTM_GS="tma", OTM_GS_M=str(m), OTM_GS_STAGES=str(stages))
+    b = _gs_form_run(128, str(tmp_path / "b.npy"), OTM_GS="gather")
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
 @pytest.mark.parametrize("m", [1, 2, 7, 64])
 def test_stencil_tma_any_chunking(m, tmp_path):
     """The TMA-staged form's z-chunks (m chunks per column, ragged when m does
