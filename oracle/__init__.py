@@ -19,10 +19,13 @@ and cites the section or equation it restates:
                OC update (Sec. 3.3 OCOptimizer) and the adaptive volume bound
                (Alg. 1), assembled into one design iteration (Alg. 2 and the
                optimisation loop of Sec. 3.4).
+* ``mma``    -- the Method of Moving Asymptotes with one constraint
+               (Svanberg's standard form, dual route), for model 2
+               (Eq. model2, MMAOptimizer of Sec. 3.3).
 * ``unet``   -- plain-loop periodic 3-D conv U-Net forward/backward used to
                check the learned warm-start kernels' gradients.
 
-Parity status of each function is listed in its docstring; all of ``fem`` and
-``design`` are pinned by tests in ``tests/test_oracle_*.py`` against closed
+Parity status of each function is listed in its docstring; all of ``fem``,
+``design`` and ``mma`` are pinned by tests in ``tests/test_oracle_*.py`` against closed
 forms, bounds, invariants, finite differences and brute force.
 """

@@ -251,6 +251,11 @@ class DesignParams:
     objective: str = "mse"
     symmetry: bool = False
     warm_start: bool = True
+    optimizer: str = "oc"       # "oc": Eq. model3 / model1 by OC; "mma": Eq. model2 by MMA (oracle.mma)
+    mma_eps: float = 1e-4       # eps of Eq. model2's constraint g <= eps
+    mma_move: float = 0.5
+    mma_c: float = 1000.0
+    mma_d: float = 1.0
 
 
 class Design:
@@ -265,6 +270,10 @@ class Design:
         if not params.governor:
             self.gov.vstar = params.fixed_volume
         self.iteration = 0
+        self.mma = None
+        if params.optimizer == "mma":
+            from .mma import MmaState
+            self.mma = MmaState(self.rho)
 
     def step(self):
         p = self.p
@@ -279,7 +288,9 @@ class Design:
         _, s = sensitivity(n, rho_f, h["E"], dg, p.penal, p.k_solid, p.k_void, p.rmin)
         low_bound = float((rho_f ** p.penal).mean())
         vol = float(self.rho.mean())
-        if p.governor:
+        if p.optimizer == "mma":
+            vstar = 0.0
+        elif p.governor:
             vstar = self.gov.update(g, low_bound, vol)
         else:
             vstar = p.fixed_volume
@@ -287,7 +298,13 @@ class Design:
         if p.symmetry:
             rho = central_symmetrize(n, rho)
             s = central_symmetrize(n, s)
-        rho_new, lam = oc_update(rho, s, vstar, p.move, p.damp, p.rho_min)
+        if p.optimizer == "mma":
+            # Eq. model2: f0 = V = mean(rho~), df0/drho = W^T (1/N); f1 = g - eps
+            N = rho.size
+            df0 = density_filter_transpose(n, np.full(N, 1.0 / N), p.rmin)
+            rho_new, lam = self.mma.step(rho, df0, g - p.mma_eps, s, move=p.mma_move, c=p.mma_c, d=p.mma_d)
+        else:
+            rho_new, lam = oc_update(rho, s, vstar, p.move, p.damp, p.rho_min)
         self.rho = rho_new
         self.iteration += 1
         return dict(g=g, kappa=kappa, vstar=vstar, lam=lam, mean_rho=vol,
