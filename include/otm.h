@@ -78,6 +78,13 @@ enum {
     OTM_OBJ_L1 = 2        /* Eq. l1: sum of |kappa - kappa*|, d|a|/da = 0 at 0 */
 };
 
+/* Design update (params.optimizer). */
+enum {
+    OTM_OPT_OC = 0,   /* optimality criteria on Eq. model3 (governor on) or Eq. model1 (governor off) */
+    OTM_OPT_MMA = 1   /* Method of Moving Asymptotes on Eq. model2: minimise V(rho) subject to
+                         g <= mma_eps, 0 <= rho <= 1 (MMAOptimizer, Sec. 3.3) */
+};
+
 /* Fields readable with otm_get_field. */
 enum {
     OTM_FIELD_RHO = 0,        /* design density rho, n^3 */
@@ -124,7 +131,12 @@ typedef struct otm_params {
     uint64_t seed;           /* seed of the learned predictor's initial weights */
     void* stream;            /* cudaStream_t to order work on; NULL = context-owned stream */
     int device;              /* CUDA device ordinal; -1 = current device */
-    int reserved1;
+    int optimizer;           /* OTM_OPT_OC | OTM_OPT_MMA; with MMA the governor, vstar and the OC
+                                parameters (move, damp, rho_min) are not used */
+    double mma_eps;          /* eps of Eq. model2's constraint g <= eps (default 1e-4) */
+    double mma_move;         /* MMA move limit, a fraction of the box [0, 1] (default 0.5) */
+    double mma_c, mma_d;     /* weights of the constraint's slack y in MMA's standard form,
+                                c y + d y^2 / 2 (defaults 1000 and 1) */
 } otm_params;
 
 /* Per design-iteration report. */
@@ -133,8 +145,10 @@ typedef struct otm_step_info {
     double kappa[6];      /* kappa^H at that density */
     double mean_rho;      /* V(rho) = mean rho (Sec. 2.3) */
     double mean_rhop;     /* mean filtered rho^p, Alg. 1 lowBound */
-    double vstar;         /* volume bound used by the OC update */
-    double lambda;        /* OC Lagrange multiplier; 0 = constraint inactive, inf = all at lower bound */
+    double vstar;         /* volume bound used by the OC update (0 with OTM_OPT_MMA) */
+    double lambda;        /* OC Lagrange multiplier; 0 = constraint inactive, inf = all at lower bound.
+                             OTM_OPT_MMA: the multiplier of g <= eps (0 = inactive, above mma_c = the
+                             constraint could not be met within the move limits) */
     int cg_iters[3];      /* PCG iterations per load case */
     int iteration;        /* design iteration index (0-based) of this report */
     double resid[3];      /* true relative residual per load case at exit */
@@ -168,7 +182,8 @@ typedef struct otm_ctx otm_ctx;
 /* Fill p with the defaults: n = 128, kappa* = [0.1,0.1,0.1,0,0,0],
  * volfrac 0.3, p = 3, r = 1.5, k = 1 / 1e-3, move 0.05, damp 0.5,
  * rho_min 1e-3, cg_tol 1e-6, cg_maxit 500, OTM_FP32, OTM_WS_PREV, MSE,
- * governor on (bound 1e-4, 1e-3, 1e-2), no symmetry, stream NULL, device -1. */
+ * governor on (bound 1e-4, 1e-3, 1e-2), no symmetry, stream NULL, device -1,
+ * OTM_OPT_OC (MMA: eps 1e-4, move 0.5, c 1000, d 1). */
 OTM_API otm_status otm_params_default(otm_params* p);
 
 /* OTM_OK if the 6-vector is a symmetric positive definite tensor (every
@@ -391,6 +406,27 @@ OTM_API otm_status otm_op_oc_update(int dtype, int n, double vstar, double move,
                                     const void* s, void* rho_new, double* lambda_out,
                                     void* stream);
 
+
+/* One iteration of the Method of Moving Asymptotes for model 2 (Eq. model2:
+ * minimise V(rho) = mean(rho) subject to g - eps <= 0, 0 <= rho <= 1; the
+ * MMAOptimizer of Sec. 3.3), on device arrays of n^3 values in dtype:
+ *   x       in: the design rho^k; out: rho^(k+1)
+ *   dg      dg/drho at rho^k (the constraint's gradient); dV/drho = 1/n^3
+ *   xold1, xold2   rho^(k-1), rho^(k-2); out: shifted (xold2 <- xold1 <- x)
+ *   low, upp       asymptotes of iteration k-1; out: those of iteration k
+ * iter = k (0-based; iterations 0 and 1 place the asymptotes at x -/+ 0.5,
+ * later ones adapt them), g = g(kappa^H(rho^k)), eps the bound of the
+ * constraint, move the move limit (fraction of the box, Svanberg's 0.5),
+ * c and d the weights of the constraint's slack (c y + d y^2 / 2; 1000, 1).
+ * xold1, xold2, low and upp are only read from iteration 2 on, but must be
+ * finite.  *lambda_out (host, may be NULL) receives the multiplier: 0 when
+ * the constraint is inactive, above c when it cannot be met within the move
+ * limits.  Errors: OTM_EINVAL for NULL arrays, a bad dtype or n, iter < 0,
+ * move outside (0, 1], c < 0, d <= 0 or a non-finite g or eps. */
+OTM_API otm_status otm_op_mma_update(int dtype, int n, int iter, double g, double eps, double move,
+                                     double c, double d, void* x, const void* dg, void* xold1,
+                                     void* xold2, void* low, void* upp, double* lambda_out,
+                                     void* stream);
 
 /* ------------------------------------------------- learned warm start (U-Net)
  *

@@ -72,6 +72,11 @@ std::string check_params(const otm_params* p) {
         return "governor thresholds must be positive";
     if (p->symmetry != 0 && p->symmetry != 1) return "symmetry must be 0 or 1";
     if (p->coarse_smoother != 0 && p->coarse_smoother != 1) return "coarse_smoother must be 0 or 1";
+    if (p->optimizer != OTM_OPT_OC && p->optimizer != OTM_OPT_MMA) return "unknown optimizer";
+    if (p->optimizer == OTM_OPT_MMA &&
+        !(std::isfinite(p->mma_eps) && p->mma_move > 0.0 && p->mma_move <= 1.0 && p->mma_c >= 0.0 &&
+          std::isfinite(p->mma_c) && p->mma_d > 0.0 && std::isfinite(p->mma_d)))
+        return "MMA parameters: need finite mma_eps, mma_move in (0, 1], mma_c >= 0, mma_d > 0";
     return "";
 }
 
@@ -118,6 +123,11 @@ otm_status otm_params_default(otm_params* p) {
     p->seed = 0;
     p->stream = nullptr;
     p->device = -1;
+    p->optimizer = OTM_OPT_OC;
+    p->mma_eps = 1e-4;
+    p->mma_move = 0.5;
+    p->mma_c = 1000.0;
+    p->mma_d = 1.0;
     return OTM_OK;
 }
 

@@ -646,6 +646,15 @@ struct DesignScalars {
     int oc_mode;                   // 0 interior, 1 inactive, 2 infeasible
     int oc_pass;
     double mu_min_seen, mu_max_seen;
+    // MMA (model 2) dual search
+    double mma_r1;                 // r1 of the constraint's approximation
+    double mma_lo, mma_hi;         // bracket of lambda
+    double mma_phi_lo, mma_phi_hi; // phi at the bracket ends
+    double mma_lam;                // lambda*
+    int mma_mode;                  // 0 search, 1 constraint inactive (lambda = 0)
+    int mma_pass;
+    int mma_k;                     // MMA iterations done (asymptote rule)
+    int mma_pad;
 };
 
 }  // namespace otm

@@ -10,6 +10,7 @@
 #include "kernels_fine.cuh"
 #include "kernels_tma.cuh"
 #include "kernels_gs_tma.cuh"
+#include "kernels_mma.cuh"
 #include "kernels_tiled.cuh"
 #include "kernels_warprow.cuh"
 #include "otm_internal.cuh"
@@ -289,6 +290,25 @@ bool bad_n(int n) { return n < 4 || n > 512; }
         if (cond) return op_fail(OTM_EINVAL, msg); \
     } while (0)
 
+template <class R>
+otm_status mma_t(int n, int iter, double g, double eps, double move, double c, double d, void* x, const void* dg,
+                 void* x1, void* x2, void* L, void* U, double* lambda_out, void* stream) {
+    OpCtx oc(stream);
+    Scratch sc;
+    if (sc.alloc(oc.st, oc.max_blocks) != cudaSuccess) return op_fail(OTM_ENOMEM, "otm_op_mma_update: scratch");
+    const size_t N = (size_t)n * n * n;
+    otm::RedBuf rb{sc.partials, sc.counter, oc.max_blocks};
+    cudaMemcpyAsync(&sc.ds->g, &g, sizeof(double), cudaMemcpyHostToDevice, oc.st);
+    cudaMemcpyAsync(&sc.ds->mma_k, &iter, sizeof(int), cudaMemcpyHostToDevice, oc.st);
+    otm::MmaP mp{0.0, 1.0, move, c, d, 1.0 / (double)N, eps};
+    otm::mma_enqueue<R>(N, (R*)x, (R*)x1, (R*)x2, (R*)L, (R*)U, (const R*)dg, mp, sc.ds, rb, oc.grid(N), oc.st);
+    double lam = 0.0;
+    cudaMemcpyAsync(&lam, &sc.ds->lambda, sizeof(double), cudaMemcpyDeviceToHost, oc.st);
+    otm_status st = finish(oc.st, "otm_op_mma_update");
+    if (st == OTM_OK && lambda_out) *lambda_out = lam;
+    return st;
+}
+
 extern "C" {
 
 otm_status otm_op_filter_simp(int dtype, int n, double rmin, double penal, double k_solid, double k_void,
@@ -339,6 +359,18 @@ otm_status otm_op_kappa_sens(int dtype, int n, double penal, double k_solid, dou
     if (dtype == OTM_FP64)
         return kappa_sens_t<double>(n, penal, k_solid, k_void, k, rho_f, chi, w, kappa_out, s_f, stream);
     return kappa_sens_t<float>(n, penal, k_solid, k_void, k, rho_f, chi, w, kappa_out, s_f, stream);
+}
+
+otm_status otm_op_mma_update(int dtype, int n, int iter, double g, double eps, double move, double c, double d,
+                             void* x, const void* dg, void* xold1, void* xold2, void* low, void* upp,
+                             double* lambda_out, void* stream) {
+    OP_CHECK(bad_dtype(dtype) || bad_n(n) || !x || !dg || !xold1 || !xold2 || !low || !upp,
+             "otm_op_mma_update: bad argument");
+    OP_CHECK(iter < 0 || !(move > 0 && move <= 1 && c >= 0 && d > 0 && std::isfinite(g) && std::isfinite(eps)),
+             "otm_op_mma_update: bad MMA parameters");
+    if (dtype == OTM_FP64)
+        return mma_t<double>(n, iter, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, lambda_out, stream);
+    return mma_t<float>(n, iter, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, lambda_out, stream);
 }
 
 otm_status otm_op_oc_update(int dtype, int n, double vstar, double move, double damp, double rho_min,

@@ -20,6 +20,7 @@
 #include "kernels_warprow.cuh"
 #include "kernels_tma.cuh"
 #include "kernels_gs_tma.cuh"
+#include "kernels_mma.cuh"
 #include "kernels_ws.cuh"
 #include "otm_internal.cuh"
 #include "unet_api.cuh"
@@ -159,6 +160,10 @@ class Solver : public SolverBase {
 
     // fine fields
     R *rho = nullptr, *rho_f = nullptr, *kf = nullptr, *s_f = nullptr, *s = nullptr;
+    // MMA (optimizer = OTM_OPT_MMA): the two previous iterates and the asymptotes
+    R *mx1 = nullptr, *mx2 = nullptr, *mL = nullptr, *mU = nullptr;
+    MmaP mp_{};
+    bool use_mma() const { return prm.optimizer == OTM_OPT_MMA; }
     R *f = nullptr, *x = nullptr, *xl = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     S *z = nullptr, *res0 = nullptr, *k_vc = nullptr;
     // coarse levels 1..nlev-1 (level 0 uses z / r / res0 / k_vc)
@@ -219,7 +224,7 @@ class Solver : public SolverBase {
         if (ev_join2) cudaEventDestroy(ev_join2);
         if (gx_setup) cudaGraphExecDestroy(gx_setup);
         if (gx_solve0) cudaGraphExecDestroy(gx_solve0);
-        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_save, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
+        void* ptrs[] = {rho, rho_f, kf, s_f, s, rho_save, mx1, mx2, mL, mU, f, x, xl, r, p, q, z, res0, Bs_d, Minv, Wd,
                         partials, counter, partials2, counter2, ps, ds, stage_f, ynet[0], ynet[1], xc_net, xc_delta, ps_c, ws, lam_d};
         for (void* ptr : ptrs)
             if (ptr) cudaFree(ptr);
@@ -442,6 +447,13 @@ class Solver : public SolverBase {
         OTM_TRY(alloc(s_f, N));
         OTM_TRY(alloc(s, N));
         OTM_TRY(alloc(rho_save, N));
+        if (pin.optimizer == OTM_OPT_MMA) {
+            OTM_TRY(alloc(mx1, N));
+            OTM_TRY(alloc(mx2, N));
+            OTM_TRY(alloc(mL, N));
+            OTM_TRY(alloc(mU, N));
+            mp_ = MmaP{0.0, 1.0, pin.mma_move, pin.mma_c, pin.mma_d, 1.0 / (double)N, pin.mma_eps};
+        }
         OTM_TRY(alloc(f, 3 * N));
         OTM_TRY(alloc(x, 3 * N));
         if (!std::is_same<C, double>::value) OTM_TRY(alloc(xl, 3 * N));
@@ -588,7 +600,7 @@ class Solver : public SolverBase {
         ds_h->governor_on = pin.governor;
         ds_h->objective = pin.objective;
         for (int c = 0; c < 6; ++c) ds_h->target[c] = pin.kappa_target[c];
-        ds_h->vstar = pin.governor ? 1.0 : pin.fixed_volume;
+        ds_h->vstar = pin.optimizer == OTM_OPT_MMA ? 0.0 : (pin.governor ? 1.0 : pin.fixed_volume);
         OTM_CU(cudaMemcpyAsync(ds, ds_h, sizeof(DesignScalars), cudaMemcpyHostToDevice, stream));
         memset(ps_h, 0, sizeof(PcgScalars));
         ps_h->tol2 = pin.cg_tol * pin.cg_tol;
@@ -629,8 +641,15 @@ class Solver : public SolverBase {
         iteration = 0;
         // reset Alg. 1 state
         OTM_CU(cudaMemcpyAsync(&ds->gov, &gov_init, sizeof(GovState), cudaMemcpyHostToDevice, stream));
-        const double v0 = prm.governor ? 1.0 : prm.fixed_volume;
+        const double v0 = use_mma() ? 0.0 : (prm.governor ? 1.0 : prm.fixed_volume);
         OTM_CU(cudaMemcpyAsync(&ds->vstar, &v0, sizeof(double), cudaMemcpyHostToDevice, stream));
+        if (use_mma()) {
+            // MMA restarts: iteration 0 (the history is read only from iteration 2 on)
+            const int k0 = 0;
+            OTM_CU(cudaMemcpyAsync(&ds->mma_k, &k0, sizeof(int), cudaMemcpyHostToDevice, stream));
+            OTM_CU(cudaMemcpyAsync(mx1, rho, N * sizeof(R), cudaMemcpyDeviceToDevice, stream));
+            OTM_CU(cudaMemcpyAsync(mx2, rho, N * sizeof(R), cudaMemcpyDeviceToDevice, stream));
+        }
         OTM_CU(cudaStreamSynchronize(stream));
         return OTM_OK;
     }
@@ -1002,17 +1021,25 @@ if (tma_pcg_.grid > 0)
         return OTM_OK;
     }
     // design tail: tensor, sensitivity, filter transpose, Alg. 1, OC update
+    // (MMA on Eq. model2: no governor; the MMA iteration instead of OC)
     otm_status enqueue_tail(bool with_tensor = true) {
         if (with_tensor) OTM_TRY(tensor_and_sens(true));
-        ++nl_;
-        launch_pdl(k_governor, 1, 1, stream, ds, 1.0 / (double)N, 0, 0.0);
-        OTM_LAUNCH();
+        if (!use_mma()) {
+            ++nl_;
+            launch_pdl(k_governor, 1, 1, stream, ds, 1.0 / (double)N, 0, 0.0);
+            OTM_LAUNCH();
+        }
         if (prm.symmetry) {
             ++nl_;
             launch_pdl(k_symmetrize<R>, grid(N / 2 + 1), 256, stream, N, rho, s);
             OTM_LAUNCH();
         }
-        OTM_TRY(oc_update());
+        if (use_mma()) {
+            nl_ += mma_enqueue<R>(N, rho, mx1, mx2, mL, mU, s, mp_, ds, rbuf(), grid(N), stream);
+            OTM_LAUNCH();
+        } else {
+            OTM_TRY(oc_update());
+        }
         return OTM_OK;
     }
 
@@ -1677,9 +1704,12 @@ if (tma_pcg_.grid > 0)
         GovState gov;
         double vstar;
         uint64_t rho_bytes, chi_bytes;
+        int32_t optimizer, mma_k;   // MMA: iteration count, then its four arrays after the solution
+        uint64_t mma_bytes;
     };
     size_t chi_bytes() const { return (xl ? 6 : 3) * N * sizeof(R); }
-    size_t state_size() const override { return sizeof(StateHeader) + N * sizeof(R) + chi_bytes(); }
+    size_t mma_bytes() const { return use_mma() ? 4 * N * sizeof(R) : 0; }
+    size_t state_size() const override { return sizeof(StateHeader) + N * sizeof(R) + chi_bytes() + mma_bytes(); }
     otm_status get_state(void* buf) override {
         StateHeader h;
         memset(&h, 0, sizeof(h));
@@ -1694,8 +1724,17 @@ if (tma_pcg_.grid > 0)
         h.vstar = ds_h->vstar;
         h.rho_bytes = N * sizeof(R);
         h.chi_bytes = chi_bytes();
+        h.optimizer = prm.optimizer;
+        h.mma_k = ds_h->mma_k;
+        h.mma_bytes = mma_bytes();
         char* b = (char*)buf;
         memcpy(b, &h, sizeof(h));
+        if (use_mma()) {
+            char* m = b + sizeof(h) + h.rho_bytes + h.chi_bytes;
+            R* arr[4] = {mx1, mx2, mL, mU};
+            for (int i = 0; i < 4; ++i)
+                OTM_CU(cudaMemcpyAsync(m + i * N * sizeof(R), arr[i], N * sizeof(R), cudaMemcpyDeviceToHost, stream));
+        }
         OTM_CU(cudaMemcpyAsync(b + sizeof(h), rho, h.rho_bytes, cudaMemcpyDeviceToHost, stream));
         OTM_CU(cudaMemcpyAsync(b + sizeof(h) + h.rho_bytes, x, 3 * N * sizeof(R), cudaMemcpyDeviceToHost, stream));
         if (xl)
@@ -1712,7 +1751,8 @@ if (tma_pcg_.grid > 0)
         StateHeader h;
         memcpy(&h, buf, sizeof(h));
         if (h.magic != 0x4f544d5354415445ull || h.n != n || h.precision != prm.precision ||
-            h.rho_bytes != N * sizeof(R) || h.chi_bytes != chi_bytes() || len < state_size()) {
+            h.rho_bytes != N * sizeof(R) || h.chi_bytes != chi_bytes() || h.optimizer != prm.optimizer ||
+            h.mma_bytes != mma_bytes() || len < state_size()) {
             err = "otm_set_state: blob does not match this context (n, precision or size)";
             return OTM_ESTATE;
         }
@@ -1724,6 +1764,13 @@ if (tma_pcg_.grid > 0)
                                    cudaMemcpyHostToDevice, stream));
         OTM_CU(cudaMemcpyAsync(&ds->gov, &h.gov, sizeof(GovState), cudaMemcpyHostToDevice, stream));
         OTM_CU(cudaMemcpyAsync(&ds->vstar, &h.vstar, sizeof(double), cudaMemcpyHostToDevice, stream));
+        if (use_mma()) {
+            const char* m = b + sizeof(h) + h.rho_bytes + h.chi_bytes;
+            R* arr[4] = {mx1, mx2, mL, mU};
+            for (int i = 0; i < 4; ++i)
+                OTM_CU(cudaMemcpyAsync(arr[i], m + i * N * sizeof(R), N * sizeof(R), cudaMemcpyHostToDevice, stream));
+            OTM_CU(cudaMemcpyAsync(&ds->mma_k, &h.mma_k, sizeof(int), cudaMemcpyHostToDevice, stream));
+        }
         OTM_CU(cudaStreamSynchronize(stream));
         iteration = h.iteration;
         have_prev = h.have_prev != 0;

@@ -15,6 +15,7 @@ STATUS_NAMES = {0: "OTM_OK", 1: "OTM_EINVAL", 2: "OTM_ENOMEM", 3: "OTM_ECUDA",
 OTM_FP64, OTM_FP32, OTM_MIXED = 0, 1, 2
 OTM_WS_NONE, OTM_WS_PREV, OTM_WS_LEARNED = 0, 1, 2
 OTM_OBJ_MSE, OTM_OBJ_FRACMSE, OTM_OBJ_L1 = 0, 1, 2
+OTM_OPT_OC, OTM_OPT_MMA = 0, 1
 (OTM_FIELD_RHO, OTM_FIELD_RHO_FILT, OTM_FIELD_K, OTM_FIELD_CHI, OTM_FIELD_LOAD,
  OTM_FIELD_SENS) = range(6)
 
@@ -46,7 +47,11 @@ class otm_params(C.Structure):
         ("seed", C.c_uint64),
         ("stream", C.c_void_p),
         ("device", C.c_int),
-        ("reserved1", C.c_int),
+        ("optimizer", C.c_int),
+        ("mma_eps", C.c_double),
+        ("mma_move", C.c_double),
+        ("mma_c", C.c_double),
+        ("mma_d", C.c_double),
     ]
 
 
@@ -142,6 +147,7 @@ def _load():
         "otm_op_gs_colour": [i, i, vp, vp, vp, i, vp],
         "otm_op_kappa_sens": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_op_oc_update": [i, i, d, d, d, d, vp, vp, vp, P(C.c_double), vp],
+        "otm_op_mma_update": [i, i, i, d, d, d, d, d, vp, vp, vp, vp, vp, vp, P(C.c_double), vp],
         "otm_op_kappa_sens_noalloc": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_unet_create": [i, P(C.c_int), C.c_uint64, vp, P(vp)],
         "otm_unet_destroy": [vp],
@@ -179,7 +185,7 @@ EXPORTED = [
     "otm_op_oc_update", "otm_op_kappa_sens_noalloc", "otm_unet_create", "otm_unet_destroy",
     "otm_unet_param_count", "otm_unet_get_params", "otm_unet_set_params", "otm_unet_forward",
     "otm_unet_backward", "otm_unet_train_step", "otm_unet_eval", "otm_set_predictor", "otm_op_conv3",
-    "otm_op_conv3_wgrad", "otm_op_conv3_dgrad", "otm_unet_get_activation",
+    "otm_op_conv3_wgrad", "otm_op_conv3_dgrad", "otm_unet_get_activation", "otm_op_mma_update",
 ]
 
 
@@ -356,6 +362,13 @@ def otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, rho, s, rho_new, stre
     lam = C.c_double(0.0)
     check(lib.otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, _p(rho), _p(s), _p(rho_new),
                                C.byref(lam), stream))
+    return lam.value
+
+
+def otm_op_mma_update(dtype, n, it, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, stream=None):
+    lam = C.c_double(0.0)
+    check(lib.otm_op_mma_update(dtype, n, it, g, eps, move, c, d, _p(x), _p(dg), _p(xold1), _p(xold2),
+                                _p(low), _p(upp), C.byref(lam), stream))
     return lam.value
 
 

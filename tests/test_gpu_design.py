@@ -373,3 +373,72 @@ def test_gs_forms_give_the_same_trajectory(n, precision, tmp_path):
     assert np.array_equal(a["g"], b["g"])
     assert np.array_equal(a["rho"].view(np.uint32), b["rho"].view(np.uint32))
     assert np.array_equal(a["chi"].view(np.uint32), b["chi"].view(np.uint32))
+
+
+@pytest.mark.parametrize("precision,n,iters", [(0, 8, 12), (1, 8, 12), (0, 16, 6)])
+def test_mma_model2_trajectory_matches_oracle(precision, n, iters):
+    """optimizer = OTM_OPT_MMA (Eq. model2 by MMA): every iteration's g,
+    kappa and multiplier follow the oracle's MMA loop, and the density stays
+    with it (FP64: 1e-7 after the iterations; FP32: 1e-3, the trajectory
+    tolerance of the OC path)."""
+    import math
+    wl_rho = W.initial_density(n, 0.3, 3).astype(np.float32)
+    otm = _otm()
+    p = otm.otm_params_default(n=n, precision=precision, cg_tol=1e-11 if precision == 0 else 1e-7,
+                               rmin=1.5, kappa_target=W.TARGET_ISOTROPIC, cg_maxit=3000,
+                               optimizer=otm.OTM_OPT_MMA)
+    ctx = otm.otm_create_ex(p)
+    ref = design.Design(design.DesignParams(n=n, kappa_target=W.TARGET_ISOTROPIC, rmin=1.5, cg_tol=1e-12,
+                                            optimizer="mma"), wl_rho.astype(np.float64))
+    try:
+        otm.otm_set_density(ctx, wl_rho.ctypes.data, 0)
+        lams = []
+        for it in range(iters):
+            info, st = otm.otm_step(ctx)
+            assert st in (otm.OTM_OK, otm.OTM_ENOCONV), otm.otm_last_error(ctx)
+            r = ref.step()
+            gtol = 1e-7 if precision == 0 else 1e-3
+            assert abs(info.g - r["g"]) <= gtol * r["g"] + 1e-12, (it, info.g, r["g"])
+            assert info.vstar == 0.0
+            lams.append((info.lambda_, r["lam"]))
+        diff = np.max(np.abs(_rho(ctx, otm, n) - ref.rho))
+        assert diff <= (1e-7 if precision == 0 else 1e-3), diff
+        for lg, lr in lams[:3 if precision else iters]:
+            assert (lg == 0.0) == (lr == 0.0) and math.isclose(lg, lr, rel_tol=1e-5 if precision == 0 else 1e-2)
+    finally:
+        otm.otm_destroy(ctx)
+
+
+def test_mma_checkpoint_resume_is_bitwise():
+    """The MMA state (iteration count, the two previous iterates, the
+    asymptotes) is part of the checkpoint: 3 + 3 iterations with a save and a
+    restore into a fresh context in between equal 6 iterations in one go."""
+    n = 8
+    otm = _otm()
+    rho0 = W.initial_density(n, 0.3, 3).astype(np.float32)
+
+    def mk():
+        p = otm.otm_params_default(n=n, precision=1, cg_tol=1e-7, rmin=1.5, kappa_target=W.TARGET_ISOTROPIC,
+                                   optimizer=otm.OTM_OPT_MMA)
+        c = otm.otm_create_ex(p)
+        otm.otm_set_density(c, rho0.ctypes.data, 0)
+        return c
+    a = mk()
+    try:
+        otm.otm_run(a, 6)
+        ref = _rho(a, otm, n)
+    finally:
+        otm.otm_destroy(a)
+    b = mk()
+    try:
+        otm.otm_run(b, 3)
+        blob = otm.otm_get_state(b)
+    finally:
+        otm.otm_destroy(b)
+    c = mk()
+    try:
+        otm.otm_set_state(c, blob)
+        otm.otm_run(c, 3)
+        assert np.array_equal(_rho(c, otm, n), ref)
+    finally:
+        otm.otm_destroy(c)

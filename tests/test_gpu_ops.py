@@ -364,3 +364,50 @@ def test_stencil_tma_any_chunking(m, tmp_path):
         paths.append(path)
     a, b = np.load(paths[0]), np.load(paths[1])
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def _mma_case(n, k, regime, seed):
+    """Inputs of one MMA iteration of model 2 on n^3 design variables."""
+    rng = np.random.default_rng(seed)
+    N = n ** 3
+    x = rng.uniform(0.05, 0.95, N)
+    x1 = np.clip(x + rng.uniform(-0.05, 0.05, N), 0.0, 1.0)
+    x2 = np.clip(x1 + rng.uniform(-0.05, 0.05, N), 0.0, 1.0)
+    L = x1 - rng.uniform(0.05, 0.5, N)
+    U = x1 + rng.uniform(0.05, 0.5, N)
+    dg = rng.standard_normal(N) * (1e-2 / N)       # the scale of dg/drho of a tensor objective
+    g = {"inactive": 0.0, "active": 3e-3, "infeasible": 10.0}[regime]
+    eps = {"inactive": 1.0, "active": 1e-4, "infeasible": 1e-4}[regime]
+    return x, x1, x2, L, U, dg, g, eps
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("n", [6, 16])
+@pytest.mark.parametrize("k", [0, 1, 3])
+@pytest.mark.parametrize("regime", ["inactive", "active", "infeasible"])
+def test_mma_update(dtype, n, k, regime):
+    """One MMA iteration (otm_op_mma_update) against oracle.mma.mma_update
+    on the same (device-rounded) inputs: the new design, the asymptotes, the
+    shifted history and the multiplier.  FP64 to 1e-10; FP32 to 2e-5 (the
+    per-element arithmetic and the dual sums in FP32 move lambda by about
+    1e-6 relative, and x(lambda) carries that)."""
+    from oracle import mma
+    otm = _otm()
+    t = _tdt(dtype)
+    x, x1, x2, L, U, dg, g, eps = _mma_case(n, k, regime, 40 + 7 * k + n)
+    xd, x1d, x2d, Ld, Ud, dgd = dev(x, t), dev(x1, t), dev(x2, t), dev(L, t), dev(U, t), dev(dg, t)
+    xh, x1h, x2h, Lh, Uh, dgh = host(xd), host(x1d), host(x2d), host(Ld), host(Ud), host(dgd)
+    N = n ** 3
+    lam = otm.otm_op_mma_update(dtype, n, k, g, eps, 0.5, 1000.0, 1.0, xd, dgd, x1d, x2d, Ld, Ud)
+    xr, Lr, Ur, lr = mma.mma_update(k, xh, x1h, x2h, Lh, Uh, np.full(N, 1.0 / N), g - eps, dgh)
+    tol = 1e-10 if dtype == 0 else 2e-5
+    assert np.max(np.abs(host(xd) - xr)) <= tol, np.max(np.abs(host(xd) - xr))
+    assert np.max(np.abs(host(Ld) - Lr)) <= (1e-14 if dtype == 0 else 1e-6)
+    assert np.max(np.abs(host(Ud) - Ur)) <= (1e-14 if dtype == 0 else 1e-6)
+    assert np.array_equal(host(x1d), xh) and np.array_equal(host(x2d), x1h)
+    if regime == "inactive":
+        assert lam == 0.0 and lr == 0.0
+    else:
+        assert lr > 0.0 and abs(lam - lr) <= (1e-9 if dtype == 0 else 1e-4) * lr, (lam, lr)
+        if regime == "infeasible":
+            assert lam > 1000.0
