@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--colour", type=int, default=8, help="--op gs: colour (0-7) or group pass 8 + g")
     ap.add_argument("--widths", default="16,32,64,128", help="--op unet*: network widths")
     ap.add_argument("--smoother", type=int, default=0, help="--op step: coarse_smoother (0 GS, 1 Chebyshev)")
+    ap.add_argument("--optimizer", type=int, default=0, help="--op step: 0 OC (model 3), 1 MMA (model 2)")
     ap.add_argument("--cin", type=int, default=16)
     ap.add_argument("--cout", type=int, default=16)
     ap.add_argument("--async", dest="async_", action="store_true",
@@ -65,12 +66,18 @@ def main():
         wc = (torch.randn((27, args.cin, args.cout), device=dev) / (27 * args.cin) ** 0.5).to(torch.bfloat16)
         bc = torch.zeros(args.cout, device=dev)
         yc = torch.empty((N, args.cout), dtype=torch.bfloat16, device=dev)
+    ctx_bytes = 0
     if args.op == "step":
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         p = otm.otm_params_default(n=n, precision=args.dtype, kappa_target=W.TARGET_ORTHOTROPIC, rmin=2.0,
-                                   stream=st.cuda_stream, coarse_smoother=args.smoother)
+                                   stream=st.cuda_stream, coarse_smoother=args.smoother,
+                                   optimizer=args.optimizer)
         ctx = otm.otm_create_ex(p)
         r0 = W.initial_density(n, 0.3, 1).astype(np.float32)
         otm.otm_set_density(ctx, r0.ctypes.data, 0)
+        torch.cuda.synchronize()
+        ctx_bytes = free0 - torch.cuda.mem_get_info()[0]
 
     def run():
         if args.op == "apply_K" and args.async_:
@@ -110,6 +117,8 @@ def main():
     if args.op == "step":
         info, _ = otm.otm_step(ctx)
         print(f"  PCG iterations per load case {list(info.cg_iters)}, resid {max(info.resid):.2e}")
+        print(f"  tensor + sensitivity + design update {info.stage_ms[4] * 1e3:.1f} us, g {info.g:.3e}, "
+              f"multiplier {info.lambda_:.3e}, context device memory {ctx_bytes / 2**20:.1f} MiB")
     if args.op == "conv3":
         flops = 2.0 * N * 27 * args.cin * args.cout
         print(f"conv3 {args.cin}->{args.cout}: {flops / (e0.elapsed_time(e1) / args.reps * 1e-3) / 1e12:.1f} TFLOP/s")

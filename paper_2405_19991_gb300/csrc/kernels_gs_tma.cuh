@@ -73,12 +73,11 @@ __host__ __device__ constexpr int gs_tma_rows_c(int n) {
 template <int NC, class ST, class FT>
 __global__ void __maxnreg__(96)
 k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S, int group, ST* __restrict__ T,
-         int* err) {
+         int* err, int early) {
     extern __shared__ unsigned char gsm_raw[];
     __shared__ __align__(8) uint64_t full[kTmaMaxStages];    // stage landed (transaction count)
     __shared__ __align__(8) uint64_t empty[kTmaMaxStages];   // every consumer warp done with the stage
     __shared__ int bail_s;                                // a bounded wait ran out somewhere
-    pdl_enter();
     const int n = NC ? NC : n_rt;
     const int TY = NC ? gs_tma_rows_c(NC) : ty_rt;
     unsigned char* tsm = gsm_raw + ((128u - (smem_u32(gsm_raw) & 127u)) & 127u);
@@ -102,23 +101,35 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
     const int N = n * n * n;
 
     auto wrapz = [n](int z) { return z < 0 ? z + n : (z >= n ? z - n : z); };
-    auto issue = [&](int j) {
+    // parts & 1: the stage's transaction count and the copies of k and f;
+    // parts & 2: the copies of T
+    auto issue = [&](int j, int parts) {
         const int slot = j % S;
         unsigned char* st = tsm + slot * stageBytes;
         uint64_t* bar = &full[slot];
         const int zp = wrapz(zb - 1 + j);
         const bool odd = (j & 1) != 0, with_k = j < nst - 1;   // the last stage's elements are not used
-        const int bytes = (odd ? 3 * (TY + 1) * rowU + 3 * TY * rowF : 3 * (2 * TY + 1) * rowU) + (with_k ? kB : 0);
-        mbar_expect_tx(bar, (uint32_t)bytes);
-        if (with_k) {
-            if (r0 < 0) {
-                tma_load_3d(st, &mp.k_row, bar, 0, n - 1, zp);
-                tma_load_3d(st + rowU, &mp.k_lo, bar, 0, 0, zp);
-            } else {
-                tma_load_3d(st, &mp.k_full, bar, 0, r0, zp);
+        unsigned char* d0 = st + kB;
+        if (parts & 1) {
+            const int bytes =
+                (odd ? 3 * (TY + 1) * rowU + 3 * TY * rowF : 3 * (2 * TY + 1) * rowU) + (with_k ? kB : 0);
+            mbar_expect_tx(bar, (uint32_t)bytes);
+            if (with_k) {
+                if (r0 < 0) {
+                    tma_load_3d(st, &mp.k_row, bar, 0, n - 1, zp);
+                    tma_load_3d(st + rowU, &mp.k_lo, bar, 0, 0, zp);
+                } else {
+                    tma_load_3d(st, &mp.k_full, bar, 0, r0, zp);
+                }
+            }
+            if (odd) {
+                unsigned char* df = d0 + 3 * (TY + 1) * rowU;
+#pragma unroll 1
+                for (int c = 0; c < 3; ++c)
+                    tma_load_5d(df + c * TY * rowF, &mp.fp_rows, bar, 0, yo, yb * TY, zp, c);
             }
         }
-        unsigned char* d0 = st + kB;
+        if (!(parts & 2)) return;
         if (!odd) {
 #pragma unroll 1
             for (int c = 0; c < 3; ++c) {
@@ -147,9 +158,6 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
                     tma_load_5d(d, &mp.tp_full, bar, 0, q, h0, zp, c);
                 }
             }
-            unsigned char* df = d0 + 3 * (TY + 1) * rowU;
-#pragma unroll 1
-            for (int c = 0; c < 3; ++c) tma_load_5d(df + c * TY * rowF, &mp.fp_rows, bar, 0, yo, yb * TY, zp, c);
         }
     };
 
@@ -164,11 +172,20 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
     }
     __syncthreads();
 
+    // Programmatic dependent launch: the previous kernel may still run until
+    // griddepcontrol.wait returns.  Every kernel of the solver waits on its
+    // own predecessor before it lets its dependent start, so with `early`
+    // (set where k and f were written two or more kernels back) the first
+    // stages' k and f copies go out before the wait; T, which the previous
+    // kernel writes, and every global write follow it.
     int issued = 0;
     if (tid >= ncons) {
         // Producer: stage i goes into slot i mod S once every consumer warp
         // has released stage i - S.
         if (tid == ncons) {
+            const int pre = early ? (nst < S ? nst : S) : 0;
+            for (int i = 0; i < pre; ++i) issue(i, 1);
+            pdl_enter();
             bool okp = true;
             for (int i = 0; i < nst && okp; ++i) {
                 if (i >= S) {
@@ -176,15 +193,18 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
                           !*(volatile int*)&bail_s;
                     if (!okp) break;
                 }
-                issue(i);
+                issue(i, i < pre ? 2 : 3);
                 issued = i + 1;
             }
             if (!okp) {
                 if (err) *err = 1;
                 *(volatile int*)&bail_s = 1;
             }
+        } else {
+            pdl_enter();
         }
     } else {
+    pdl_enter();
 
     const int xo = 2 * px;                          // index of (x - 1, x), x = 2 px + 1
     const int xh = xo + 2 == n ? 0 : xo + 2;        // index of (x + 1, x + 2)
@@ -433,7 +453,7 @@ inline bool gs_tma_make_maps(TmaGsMaps& mp, int n, const void* k, const void* T,
 // its launch shape.  Static for the reason given at tma_kernel: the
 // shared-memory opt-in belongs to the translation unit's own stub.
 template <class ST, class FT>
-using GsTmaKernel = void (*)(TmaGsMaps, int, int, int, int, int, ST*, int*);
+using GsTmaKernel = void (*)(TmaGsMaps, int, int, int, int, int, ST*, int*, int);
 template <class ST, class FT>
 static GsTmaKernel<ST, FT> gs_tma_kernel(int n) {
     if (n == 64) return k_gs_tma<64, ST, FT>;

@@ -101,6 +101,45 @@ __device__ __forceinline__ C mma_h(C x, const MmaElem<C>& e) {
     return e.p1 / (e.U - x) + e.q1 / (x - e.L);
 }
 
+// h_j(x_j(lambda)) without a division per candidate: with r = (U - x) /
+// (x - L), the unclamped minimiser has r = sqrt(P / Q), x = L + (U - L) /
+// (1 + r) and h = (1 + r) (p1 / r + q1) / (U - L); the box alpha <= x <= beta
+// is r_beta <= r <= r_alpha.  r and 1 / r both come from one reciprocal
+// square root of P Q.
+template <class C>
+struct MmaFast {
+    C p0, q0, p1, q1, iul;      // coefficients and 1 / (U - L)
+    C ra, ira, rb, irb;         // r at alpha (largest) and beta (smallest), and their reciprocals
+};
+template <class C>
+__device__ __forceinline__ void mma_fast(const MmaElem<C>& e, MmaFast<C>& f) {
+    f.p0 = e.p0;
+    f.q0 = e.q0;
+    f.p1 = e.p1;
+    f.q1 = e.q1;
+    f.iul = C(1) / (e.U - e.L);
+    f.ra = (e.U - e.alpha) / (e.alpha - e.L);
+    f.ira = (e.alpha - e.L) / (e.U - e.alpha);
+    f.rb = (e.U - e.beta) / (e.beta - e.L);
+    f.irb = (e.beta - e.L) / (e.U - e.beta);
+}
+__device__ __forceinline__ float mma_rsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double mma_rsqrt(double v) { return rsqrt(v); }
+template <class C>
+__device__ __forceinline__ C mma_h_fast(C lam, const MmaFast<C>& f) {
+    const C P = f.p0 + lam * f.p1, Q = f.q0 + lam * f.q1;
+    const C rs = mma_rsqrt(P * Q);
+    C r = P * rs, ir = Q * rs;
+    if (r > f.ra) {
+        r = f.ra;
+        ir = f.ira;
+    } else if (r < f.rb) {
+        r = f.rb;
+        ir = f.irb;
+    }
+    return (C(1) + r) * (f.p1 * ir + f.q1) * f.iul;
+}
+
 __device__ __forceinline__ double mma_phi(const DesignScalars* ds, double lam, double sum, const MmaP& mp) {
     const double y = lam > mp.c ? (lam - mp.c) / mp.d : 0.0;
     return ds->mma_r1 + sum - y;
@@ -214,8 +253,10 @@ k_mma_search(size_t N, const R* __restrict__ x, const R* __restrict__ L, const R
         MmaElem<C> m;
         const C xe = (C)x[e];
         mma_coeffs<C>(xe, (C)L[e], (C)U[e], (C)s[e], mp, m);
+        MmaFast<C> f;
+        mma_fast<C>(m, f);
 #pragma unroll
-        for (int j = 0; j < kMmaCand; ++j) sum[j] += mma_h<C>(mma_x<C>(cand[j], m), m);
+        for (int j = 0; j < kMmaCand; ++j) sum[j] += mma_h_fast<C>(cand[j], f);
     }
     __shared__ double res[kMmaCand];
     Acc<C> sums[kMmaCand];

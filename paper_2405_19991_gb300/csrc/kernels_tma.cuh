@@ -156,12 +156,11 @@ __host__ __device__ constexpr int tma_rows_c(int n) {
 template <int NC, int MODE, bool DOT, class ST, class FT, class OT, class Fin>
 __global__ void __maxnreg__(96)
 k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, int m, int S, OT* __restrict__ out, int* err,
-              RedBuf rb, Fin fin) {
+              RedBuf rb, Fin fin, int early) {
     extern __shared__ unsigned char tsm_raw[];
     __shared__ __align__(8) uint64_t full[kTmaMaxStages];    // stage landed (transaction count)
     __shared__ __align__(8) uint64_t empty[kTmaMaxStages];   // every consumer warp done with the stage
     __shared__ int bail_s;                                // a bounded wait ran out somewhere
-    pdl_enter();
     const int n = NC ? NC : n_rt;
     const int TY = NC ? tma_rows_c(NC) : ty_rt;
     unsigned char* tsm = tsm_raw + ((128u - (smem_u32(tsm_raw) & 127u)) & 127u);
@@ -180,12 +179,29 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
 
     auto wrapz = [n](int z) { return z < 0 ? z + n : (z >= n ? z - n : z); };
     // stage j: node plane z0 - 1 + j, element plane (and f plane) z0 - 2 + j
-    auto issue = [&](int j) {
+    // parts & 1: the stage's transaction count and the copies of k (and f);
+    // parts & 2: the copies of u
+    auto issue = [&](int j, int parts) {
         const int slot = j % S;
         unsigned char* st = tsm + slot * stageBytes;
         uint64_t* bar = &full[slot];
         const int zn = wrapz(z0 - 1 + j), ze = wrapz(z0 - 2 + j);
-        mbar_expect_tx(bar, (uint32_t)stageBytes);
+        if (parts & 1) {
+            mbar_expect_tx(bar, (uint32_t)stageBytes);
+            unsigned char* dk = st + uBytes;
+            if (y0 == 0) {
+                tma_load_3d(dk + rowU, &mp.k_lo, bar, 0, 0, ze);
+                tma_load_3d(dk, &mp.k_row, bar, 0, n - 1, ze);
+            } else {
+                tma_load_3d(dk, &mp.k_full, bar, 0, y0 - 1, ze);
+            }
+            if (MODE == 1) {
+                unsigned char* df = st + uBytes + kBytes;
+#pragma unroll 1
+                for (int c = 0; c < 3; ++c) tma_load_4d(df + c * TY * rowF, &mp.f_rows, bar, 0, y0, ze, c);
+            }
+        }
+        if (!(parts & 2)) return;
 #pragma unroll 1
         for (int c = 0; c < 3; ++c) {
             unsigned char* d = st + c * (TY + 2) * rowU;
@@ -198,18 +214,6 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
             } else {
                 tma_load_4d(d, &mp.u_full, bar, 0, y0 - 1, zn, c);
             }
-        }
-        unsigned char* dk = st + uBytes;
-        if (y0 == 0) {
-            tma_load_3d(dk + rowU, &mp.k_lo, bar, 0, 0, ze);
-            tma_load_3d(dk, &mp.k_row, bar, 0, n - 1, ze);
-        } else {
-            tma_load_3d(dk, &mp.k_full, bar, 0, y0 - 1, ze);
-        }
-        if (MODE == 1) {
-            unsigned char* df = st + uBytes + kBytes;
-#pragma unroll 1
-            for (int c = 0; c < 3; ++c) tma_load_4d(df + c * TY * rowF, &mp.f_rows, bar, 0, y0, ze, c);
         }
     };
 
@@ -231,7 +235,13 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
         // Producer: stage i goes into slot i mod S once every consumer warp is
         // done with stage i - S (they release a slot one stage after they
         // first read it, since a stage also reads the slot before it).
+        // With `early` (k and f written two or more kernels back) the first
+        // stages' k and f copies go out before griddepcontrol.wait; u,
+        // which the previous kernel may still be writing, follows it.
         if (tid == ncons) {
+            const int pre = early ? (nst < S ? nst : S) : 0;
+            for (int i = 0; i < pre; ++i) issue(i, 1);
+            pdl_enter();
             bool okp = true;
             for (int i = 0; i < nst && okp; ++i) {
                 if (i >= S) {
@@ -239,15 +249,18 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
                           !*(volatile int*)&bail_s;
                     if (!okp) break;
                 }
-                issue(i);
+                issue(i, i < pre ? 2 : 3);
                 issued = i + 1;
             }
             if (!okp) {
                 if (err) *err = 1;
                 *(volatile int*)&bail_s = 1;
             }
+        } else {
+            pdl_enter();
         }
     } else {
+    pdl_enter();
 
     const int xo = 2 * px;                          // index of (x - 1, x), x = 2 px + 1
     const int xh = xo + 2 == n ? 0 : xo + 2;        // index of (x + 1, x + 2)
@@ -451,6 +464,16 @@ inline int stencil_choice() {
     return c;
 }
 
+// 1: the solver's TMA kernels issue their k and f copies before waiting on
+// the previous kernel (OTM_PDL_EARLY=0 turns it off, for comparisons).
+inline int pdl_early() {
+    static int v = [] {
+        const char* e = getenv("OTM_PDL_EARLY");
+        return e && e[0] == '0' ? 0 : 1;
+    }();
+    return v;
+}
+
 typedef CUresult (*TmaEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -575,7 +598,7 @@ struct TmaLaunch {
 // instantiation, and the shared-memory opt-in belongs to the stub, so the
 // opt-in and the launch must take the stub of the same unit.
 template <int MODE, bool DOT, class ST, class FT, class OT, class Fin>
-using TmaKernel = void (*)(TmaStencilMaps, int, int, int, int, OT*, int*, RedBuf, Fin);
+using TmaKernel = void (*)(TmaStencilMaps, int, int, int, int, OT*, int*, RedBuf, Fin, int);
 template <int MODE, bool DOT, class ST, class FT, class OT, class Fin>
 static TmaKernel<MODE, DOT, ST, FT, OT, Fin> tma_kernel(int n) {
     if (n == 64) return k_stencil_tma<64, MODE, DOT, ST, FT, OT, Fin>;

@@ -176,7 +176,7 @@ otm_status apply_K_t(int n, const void* k, const void* u, void* Ku, void* stream
         int* err = nullptr;
         if (cudaGetSymbolAddress((void**)&err, g_op_err) != cudaSuccess) return op_fail(OTM_ECUDA, "otm_op_apply_K: flag");
         otm::launch_pdl_smem(otm::tma_kernel<0, false, float, float, float, otm::FinNone>(n), tl.grid, tl.threads,
-                             tl.smem, oc.st, maps, n, tl.ty, tl.m, tl.stages, (float*)Ku, err, rb, otm::FinNone{});
+                             tl.smem, oc.st, maps, n, tl.ty, tl.m, tl.stages, (float*)Ku, err, rb, otm::FinNone{}, 0);
         return sync ? finish_flagged(oc.st, "otm_op_apply_K") : launched("otm_op_apply_K_async");
     }
     cudaGetLastError();
@@ -209,7 +209,7 @@ otm_status gs_t(int n, const void* k, const void* f, void* T, int colour, void* 
                 if (cudaGetSymbolAddress((void**)&err, g_op_err) != cudaSuccess)
                     return op_fail(OTM_ECUDA, "otm_op_gs_colour: flag");
                 otm::launch_pdl_smem(otm::gs_tma_kernel<float, float>(n), tl.grid, tl.threads, tl.smem, oc.st, maps, n,
-                                     tl.ty, tl.m, tl.stages, group, (float*)T, err);
+                                     tl.ty, tl.m, tl.stages, group, (float*)T, err, 0);
                 return finish_flagged(oc.st, "otm_op_gs_colour");
             }
             cudaGetLastError();

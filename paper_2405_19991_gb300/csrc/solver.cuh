@@ -311,12 +311,12 @@ class Solver : public SolverBase {
         if constexpr (std::is_same<R, float>::value)
             launch_pdl_smem(tma_kernel<0, true, float, float, float, FinAlpha>(n), tma_pcg_.grid, tma_pcg_.threads,
                             tma_pcg_.smem, stream, maps_pcg_, n, tma_pcg_.ty, tma_pcg_.m, tma_pcg_.stages, (float*)q, &ps->dev_err, rb,
-                            FinAlpha{ps});
+                            FinAlpha{ps}, pdl_early());
     }
     void launch_tma_vc() {
         if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value)
             launch_pdl_smem(tma_kernel<1, false, S, float, S, FinNone>(n), tma_vc_.grid, tma_vc_.threads, tma_vc_.smem,
-                            stream, maps_vc_, n, tma_vc_.ty, tma_vc_.m, tma_vc_.stages, res0, &ps->dev_err, rbuf(), FinNone{});
+                            stream, maps_vc_, n, tma_vc_.ty, tma_vc_.m, tma_vc_.stages, res0, &ps->dev_err, rbuf(), FinNone{}, pdl_early());
     }
     size_t inv_smem_ = 0;    // dynamic shared memory of the coarsest inverse
     int inv_use_smem_ = 0;   // its working matrix in shared memory
@@ -794,7 +794,7 @@ class Solver : public SolverBase {
         if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
             if (tma_gs_.grid > 0) {
                 launch_pdl_smem(gs_tma_kernel<S, float>(n), tma_gs_.grid, tma_gs_.threads, tma_gs_.smem, stream,
-                                maps_gs_, n, tma_gs_.ty, tma_gs_.m, tma_gs_.stages, gidx, z, &ps->dev_err);
+                                maps_gs_, n, tma_gs_.ty, tma_gs_.m, tma_gs_.stages, gidx, z, &ps->dev_err, pdl_early());
                 return;
             }
         }
