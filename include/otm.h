@@ -428,6 +428,20 @@ OTM_API otm_status otm_op_mma_update(int dtype, int n, int iter, double g, doubl
                                      void* xold2, void* low, void* upp, double* lambda_out,
                                      void* stream);
 
+/* Bounds-checking build (libotm built with -DOTM_CHECK).  In that build the
+ * kernels with index arithmetic that could leave a buffer -- the tensor-copy
+ * coordinates and staged reads of the TMA stencil and group pass, the
+ * tcgen05 convolution's operand ranges, the node coordinates of the gather
+ * and coarse-level kernels -- test each index against its extent; a failing
+ * index is recorded in a device flag word and its access skipped or clamped
+ * (nothing traps), and the call that launched the kernel returns OTM_ECUDA
+ * with the site, index and bound in otm_last_error.  This call checks the
+ * mechanism itself: it evaluates one out-of-range and one in-range index
+ * (with no memory access behind either) and sets *fired = 1 when exactly the
+ * first was recorded, -1 otherwise.  In the normal build it sets *fired = 0
+ * and returns OTM_ESTATE.  Errors: OTM_EINVAL for NULL. */
+OTM_API otm_status otm_check_selftest(int* fired);
+
 /* ------------------------------------------------- learned warm start (U-Net)
  *
  * A periodic 3-D convolutional U-Net maps the filtered density rho_f (n^3) to

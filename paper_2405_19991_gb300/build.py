@@ -13,6 +13,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libotm.so")
+LIB_CHECK = os.path.join(PKG, "libotm_check.so")
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
@@ -42,12 +43,17 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra_flags=None, check: bool = False) -> str:
+    """Compile every translation unit and link the library; with check=True,
+    the bounds-checking build (-DOTM_CHECK) into libotm_check.so, objects
+    under _build_check/."""
+    bdir = BUILD + "_check" if check else BUILD
+    lib = LIB_CHECK if check else LIB
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + list(extra_flags or []) + (["-DOTM_CHECK"] if check else [])
     srcs = sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(bdir, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
@@ -67,10 +73,10 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
         errs = [e for e in ex.map(compile_one, zip(srcs, objs)) if e]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    relink = force or not os.path.exists(LIB) or any(
-        os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
+    relink = force or not os.path.exists(lib) or any(
+        os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)
     if relink:
-        tmp = LIB + ".tmp"
+        tmp = lib + ".tmp"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ["-gencode", "arch=compute_103a,code=sm_103a",
                                                     "-Xcompiler", "-fPIC", "-lcudart", "-lpthread"]
         if verbose:
@@ -78,12 +84,12 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + res.stdout + res.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     f = "-f" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(verbose=v, force=f, extra_flags=extra))
+    print(build(verbose=v, force=f, extra_flags=extra, check="--check" in sys.argv))

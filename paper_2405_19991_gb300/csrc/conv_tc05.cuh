@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "ptx_async.cuh"
 
 namespace otm {
@@ -104,7 +105,8 @@ k_conv3_tc(int n, int cin, int cout, const __nv_bfloat16* __restrict__ in, const
             gy += gy < 0 ? n : (gy >= n ? -n : 0);
             gz += gz < 0 ? n : (gz >= n ? -n : 0);
             const size_t v = (size_t)gx + (size_t)n * ((size_t)gy + (size_t)n * gz);
-            cp_async16(halo + (size_t)e * 16, in + v * cin + ck * 16 + half * 8);
+            if (OTM_BOUND(v * cin + ck * 16 + half * 8 + 7, (long long)n * n * n * cin, kSiteConvTc))
+                cp_async16(halo + (size_t)e * 16, in + v * cin + ck * 16 + half * 8);
         }
         const unsigned char* wsrc = reinterpret_cast<const unsigned char*>(wtc) + (size_t)ck * wbytes;
         for (int e = tid; e < wbytes / 16; e += 128) cp_async16(wts + (size_t)e * 16, wsrc + (size_t)e * 16);
@@ -118,7 +120,14 @@ k_conv3_tc(int n, int cin, int cout, const __nv_bfloat16* __restrict__ in, const
                 const uint32_t a_addr = halo_s + (uint32_t)((dx + kTcHX * (dy + kTcHY * dz)) * 16);
                 const uint64_t adesc = tc_smem_desc(a_addr, kTcHV * 16, kTcHX * 16);
                 const uint64_t bdesc = tc_smem_desc(wts_s + (uint32_t)(t * 2 * cout * 16), cout * 16, 128);
-                tc_mma_bf16(tmem, adesc, bdesc, idesc, (ck > 0 || t > 0) ? 1u : 0u);
+                // checking build: the last byte each operand reads (the second K half, the last
+                // 8-row group, its last row) inside its buffer, and the accumulator's columns
+                // inside the allocation
+                if (OTM_BOUND((a_addr - halo_s) + kTcHV * 16 + 15 * kTcHX * 16 + 8 * 16 - 1, kTcHaloBytes,
+                              kSiteConvTc) &&
+                    OTM_BOUND(t * 2 * cout * 16 + cout * 16 + (cout / 8 - 1) * 128 + 127, wbytes, kSiteConvTc) &&
+                    OTM_BOUND(cout - 1, (int)ncols, kSiteConvTc))
+                    tc_mma_bf16(tmem, adesc, bdesc, idesc, (ck > 0 || t > 0) ? 1u : 0u);
             }
             tc_commit(&mma_done);
         }
@@ -232,7 +241,8 @@ k_conv3_tcz(int n, int cin, int cout, int m, const __nv_bfloat16* __restrict__ i
             gx += gx < 0 ? n : (gx >= n ? -n : 0);
             gy += gy < 0 ? n : (gy >= n ? -n : 0);
             const size_t v = (size_t)gx + (size_t)n * ((size_t)gy + (size_t)n * gz);
-            cp_async16(dst + (size_t)e * 16, in + v * cin + ck * 16 + half * 8);
+            if (OTM_BOUND(v * cin + ck * 16 + half * 8 + 7, (long long)n * n * n * cin, kSiteConvTc))
+                cp_async16(dst + (size_t)e * 16, in + v * cin + ck * 16 + half * 8);
         }
     };
     // prologue: the weights and halo planes q = 0, 1, 2 (output plane 0)

@@ -36,6 +36,7 @@ struct Nbr {
 
 __device__ __forceinline__ Nbr make_nbr(int x, int y, int z, int n) {
     Nbr g;
+    if (!node_ok(x, y, z, n, kSiteFine)) x = y = z = 0;   // checking build: recorded, then clamped
     const int nn = n * n;
     const int xm = wrapm(x, n), xp = wrapp(x, n);
     const int ym = wrapm(y, n), yp = wrapp(y, n);
@@ -637,6 +638,7 @@ __device__ __forceinline__ void restrict_node(int nc, int X, int Y, int Z, const
                                               OT* __restrict__ fc) {
     using C = typename St<OT>::C;
     using CI = typename St<IT>::C;
+    if (!node_ok(X, Y, Z, nc, kSiteCoarse)) return;
     const int nf = 2 * nc;
     const size_t Nf = (size_t)nf * nf * nf;
     const size_t I = (size_t)X + (size_t)nc * (Y + (size_t)nc * Z);
@@ -689,6 +691,7 @@ __device__ __forceinline__ void prolong_node(int nf, int x, int y, int z, const 
                                              TT* __restrict__ T) {
     using C = typename St<TT>::C;
     using CC = typename St<CT>::C;
+    if (!node_ok(x, y, z, nf, kSiteCoarse)) return;
     const int nc = nf / 2;
     const size_t Nf = (size_t)nf * nf * nf;
     const size_t v = (size_t)x + (size_t)nf * (y + (size_t)nf * z);

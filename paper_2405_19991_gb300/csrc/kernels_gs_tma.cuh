@@ -110,23 +110,30 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
         const int zp = wrapz(zb - 1 + j);
         const bool odd = (j & 1) != 0, with_k = j < nst - 1;   // the last stage's elements are not used
         unsigned char* d0 = st + kB;
+        // checking build: each copy's rows inside its extent (n rows, or P
+        // rows of one parity) and its bytes inside the ring
+        const long long cap = (long long)S * stageBytes;
+        auto ok = [&](const unsigned char* d, int rows, int rb, int row, int total) {
+            return tma_box_ok(d - tsm, rows, rb, cap, row, total, zp, n, kSiteTmaGs);
+        };
         if (parts & 1) {
             const int bytes =
                 (odd ? 3 * (TY + 1) * rowU + 3 * TY * rowF : 3 * (2 * TY + 1) * rowU) + (with_k ? kB : 0);
             mbar_expect_tx(bar, (uint32_t)bytes);
             if (with_k) {
                 if (r0 < 0) {
-                    tma_load_3d(st, &mp.k_row, bar, 0, n - 1, zp);
-                    tma_load_3d(st + rowU, &mp.k_lo, bar, 0, 0, zp);
+                    if (ok(st, 1, rowU, n - 1, n)) tma_load_3d(st, &mp.k_row, bar, 0, n - 1, zp);
+                    if (ok(st + rowU, 2 * TY - 1, rowU, 0, n)) tma_load_3d(st + rowU, &mp.k_lo, bar, 0, 0, zp);
                 } else {
-                    tma_load_3d(st, &mp.k_full, bar, 0, r0, zp);
+                    if (ok(st, 2 * TY, rowU, r0, n)) tma_load_3d(st, &mp.k_full, bar, 0, r0, zp);
                 }
             }
             if (odd) {
                 unsigned char* df = d0 + 3 * (TY + 1) * rowU;
 #pragma unroll 1
                 for (int c = 0; c < 3; ++c)
-                    tma_load_5d(df + c * TY * rowF, &mp.fp_rows, bar, 0, yo, yb * TY, zp, c);
+                    if (ok(df + c * TY * rowF, TY, rowF, yb * TY, P))
+                        tma_load_5d(df + c * TY * rowF, &mp.fp_rows, bar, 0, yo, yb * TY, zp, c);
             }
         }
         if (!(parts & 2)) return;
@@ -135,13 +142,14 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
             for (int c = 0; c < 3; ++c) {
                 unsigned char* d = d0 + c * (2 * TY + 1) * rowU;
                 if (r0 < 0) {
-                    tma_load_4d(d, &mp.t_row, bar, 0, n - 1, zp, c);
-                    tma_load_4d(d + rowU, &mp.t_lo, bar, 0, 0, zp, c);
+                    if (ok(d, 1, rowU, n - 1, n)) tma_load_4d(d, &mp.t_row, bar, 0, n - 1, zp, c);
+                    if (ok(d + rowU, 2 * TY, rowU, 0, n)) tma_load_4d(d + rowU, &mp.t_lo, bar, 0, 0, zp, c);
                 } else if (r0 + 2 * TY + 1 > n) {
-                    tma_load_4d(d, &mp.t_lo, bar, 0, r0, zp, c);
-                    tma_load_4d(d + 2 * TY * rowU, &mp.t_row, bar, 0, 0, zp, c);
+                    if (ok(d, 2 * TY, rowU, r0, n)) tma_load_4d(d, &mp.t_lo, bar, 0, r0, zp, c);
+                    if (ok(d + 2 * TY * rowU, 1, rowU, 0, n))
+                        tma_load_4d(d + 2 * TY * rowU, &mp.t_row, bar, 0, 0, zp, c);
                 } else {
-                    tma_load_4d(d, &mp.t_full, bar, 0, r0, zp, c);
+                    if (ok(d, 2 * TY + 1, rowU, r0, n)) tma_load_4d(d, &mp.t_full, bar, 0, r0, zp, c);
                 }
             }
         } else {
@@ -149,13 +157,13 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
             for (int c = 0; c < 3; ++c) {
                 unsigned char* d = d0 + c * (TY + 1) * rowU;
                 if (h0 < 0) {
-                    tma_load_5d(d, &mp.tp_row, bar, 0, q, P - 1, zp, c);
-                    tma_load_5d(d + rowU, &mp.tp_lo, bar, 0, q, 0, zp, c);
+                    if (ok(d, 1, rowU, P - 1, P)) tma_load_5d(d, &mp.tp_row, bar, 0, q, P - 1, zp, c);
+                    if (ok(d + rowU, TY, rowU, 0, P)) tma_load_5d(d + rowU, &mp.tp_lo, bar, 0, q, 0, zp, c);
                 } else if (h0 + TY + 1 > P) {
-                    tma_load_5d(d, &mp.tp_lo, bar, 0, q, h0, zp, c);
-                    tma_load_5d(d + TY * rowU, &mp.tp_row, bar, 0, q, 0, zp, c);
+                    if (ok(d, TY, rowU, h0, P)) tma_load_5d(d, &mp.tp_lo, bar, 0, q, h0, zp, c);
+                    if (ok(d + TY * rowU, 1, rowU, 0, P)) tma_load_5d(d + TY * rowU, &mp.tp_row, bar, 0, q, 0, zp, c);
                 } else {
-                    tma_load_5d(d, &mp.tp_full, bar, 0, q, h0, zp, c);
+                    if (ok(d, TY + 1, rowU, h0, P)) tma_load_5d(d, &mp.tp_full, bar, 0, q, h0, zp, c);
                 }
             }
         }
@@ -216,6 +224,13 @@ k_gs_tma(const __grid_constant__ TmaGsMaps mp, int n_rt, int ty_rt, int m, int S
     const int csE = (2 * TY + 1) * n, csO = (TY + 1) * n, csF = TY * n;
     const int oa = y * n + xa, ob = y * n + xb;     // output offsets in a plane
     const int fo = 3 * (TY + 1) * n * (int)sizeof(ST);   // f rows, bytes past the node rows
+    // checking build: the furthest staged elements this thread reads and the
+    // furthest output offset; a failure ends the march through the bail flag
+    if (!(OTM_BOUND(ke0 + xh, 2 * TY * n, kSiteTmaGs) && OTM_BOUND(2 * csE + ne + 2 * n + xh + 1, 3 * csE, kSiteTmaGs) &&
+          OTM_BOUND(2 * csO + no + n + xh + 1, 3 * csO, kSiteTmaGs) &&
+          OTM_BOUND(2 * csF + t * n + (xa > xb ? xa : xb), 3 * csF, kSiteTmaGs) &&
+          OTM_BOUND(oa > ob ? oa : ob, n * n, kSiteTmaGs)))
+        *(volatile int*)&bail_s = 1;
 
     // the decision to leave is taken per warp (every lane agrees)
     auto wait = [&](int sl, uint32_t ph) -> bool {

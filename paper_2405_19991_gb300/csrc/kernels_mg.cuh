@@ -283,6 +283,7 @@ __device__ __forceinline__ void cheb_node(int n, size_t N, int x, int y, int z, 
                                           TT* __restrict__ Tout, TT* __restrict__ D, float c_d, float c_r) {
     using C = typename St<TT>::C;
     const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    if (!node_ok(x, y, z, n, kSiteCoarse) || !OTM_BOUND(v, N, kSiteCoarse)) return;
     int xs[3], ys[3], zs[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -361,6 +362,7 @@ __device__ __forceinline__ void gs_stencil_node(int n, size_t N, int x, int y, i
                                                 const FT* __restrict__ f, TT* __restrict__ T) {
     using C = typename St<TT>::C;
     const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    if (!node_ok(x, y, z, n, kSiteCoarse) || !OTM_BOUND(v, N, kSiteCoarse)) return;
     int xs[3], ys[3], zs[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -414,6 +416,7 @@ __device__ __forceinline__ void residual_stencil_node(int n, size_t N, int x, in
                                                       OT* __restrict__ res) {
     using C = typename St<OT>::C;
     const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    if (!node_ok(x, y, z, n, kSiteCoarse) || !OTM_BOUND(v, N, kSiteCoarse)) return;
     int xs[3], ys[3], zs[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -118,6 +118,17 @@ struct Acc2 {
     }
 };
 
+// Checking build: a tensor copy of `rows` rows of `row_bytes` starting at row
+// `row` of a `total`-row extent, plane z of n, into shared-memory offset
+// `off` of a `cap`-byte ring.  A copy that fails is not issued; its stage
+// then never completes and the bounded wait ends the launch with its error
+// flag set.
+__device__ __forceinline__ bool tma_box_ok(long long off, int rows, int row_bytes, long long cap, int row, int total,
+                                           int z, int n, int site) {
+    return OTM_BOUND(off + (long long)rows * row_bytes - 1, cap, site) && OTM_BOUND(row, total - rows + 1, site) &&
+           OTM_BOUND(z, n, site);
+}
+
 // ------------------------------------------------------------------ kernel
 constexpr int kTmaMaxStages = 8;   // ring depth: 3 .. 8 stages (a launch argument)
 constexpr int kTmaThreads = 256;
@@ -186,19 +197,25 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
         unsigned char* st = tsm + slot * stageBytes;
         uint64_t* bar = &full[slot];
         const int zn = wrapz(z0 - 1 + j), ze = wrapz(z0 - 2 + j);
+        const long long cap = (long long)S * stageBytes;
+        auto ok = [&](const unsigned char* d, int rows, int rb, int row, int z) {
+            return tma_box_ok(d - tsm, rows, rb, cap, row, n, z, n, kSiteTmaStencil);
+        };
         if (parts & 1) {
             mbar_expect_tx(bar, (uint32_t)stageBytes);
             unsigned char* dk = st + uBytes;
             if (y0 == 0) {
-                tma_load_3d(dk + rowU, &mp.k_lo, bar, 0, 0, ze);
-                tma_load_3d(dk, &mp.k_row, bar, 0, n - 1, ze);
+                if (ok(dk + rowU, TY, rowU, 0, ze)) tma_load_3d(dk + rowU, &mp.k_lo, bar, 0, 0, ze);
+                if (ok(dk, 1, rowU, n - 1, ze)) tma_load_3d(dk, &mp.k_row, bar, 0, n - 1, ze);
             } else {
-                tma_load_3d(dk, &mp.k_full, bar, 0, y0 - 1, ze);
+                if (ok(dk, TY + 1, rowU, y0 - 1, ze)) tma_load_3d(dk, &mp.k_full, bar, 0, y0 - 1, ze);
             }
             if (MODE == 1) {
                 unsigned char* df = st + uBytes + kBytes;
 #pragma unroll 1
-                for (int c = 0; c < 3; ++c) tma_load_4d(df + c * TY * rowF, &mp.f_rows, bar, 0, y0, ze, c);
+                for (int c = 0; c < 3; ++c)
+                    if (ok(df + c * TY * rowF, TY, rowF, y0, ze))
+                        tma_load_4d(df + c * TY * rowF, &mp.f_rows, bar, 0, y0, ze, c);
             }
         }
         if (!(parts & 2)) return;
@@ -206,13 +223,14 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
         for (int c = 0; c < 3; ++c) {
             unsigned char* d = st + c * (TY + 2) * rowU;
             if (y0 == 0) {
-                tma_load_4d(d + rowU, &mp.u_lo, bar, 0, 0, zn, c);
-                tma_load_4d(d, &mp.u_row, bar, 0, n - 1, zn, c);
+                if (ok(d + rowU, TY + 1, rowU, 0, zn)) tma_load_4d(d + rowU, &mp.u_lo, bar, 0, 0, zn, c);
+                if (ok(d, 1, rowU, n - 1, zn)) tma_load_4d(d, &mp.u_row, bar, 0, n - 1, zn, c);
             } else if (y0 + TY == n) {
-                tma_load_4d(d, &mp.u_lo, bar, 0, y0 - 1, zn, c);
-                tma_load_4d(d + (TY + 1) * rowU, &mp.u_row, bar, 0, 0, zn, c);
+                if (ok(d, TY + 1, rowU, y0 - 1, zn)) tma_load_4d(d, &mp.u_lo, bar, 0, y0 - 1, zn, c);
+                if (ok(d + (TY + 1) * rowU, 1, rowU, 0, zn))
+                    tma_load_4d(d + (TY + 1) * rowU, &mp.u_row, bar, 0, 0, zn, c);
             } else {
-                tma_load_4d(d, &mp.u_full, bar, 0, y0 - 1, zn, c);
+                if (ok(d, TY + 2, rowU, y0 - 1, zn)) tma_load_4d(d, &mp.u_full, bar, 0, y0 - 1, zn, c);
             }
         }
     };
@@ -274,6 +292,14 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
     const int sf = ty * n;                          // staged f, case 0
     const int nn = n * n;
     const int oa = y * n + xa, ob = y * n + xb;     // output offsets in a plane
+    // checking build: the furthest staged element this thread reads (case 2,
+    // row y + 1, x + 2) and the furthest k and f elements; a failure ends
+    // the march through the bail flag
+    if (!(OTM_BOUND(su + 2 * scs + 2 * n + xh + 1, 3 * (TY + 2) * n, kSiteTmaStencil) &&
+          OTM_BOUND(sk0 + xh, (TY + 1) * n, kSiteTmaStencil) &&
+          OTM_BOUND(sf + 2 * TY * n + (xa > xb ? xa : xb), MODE == 1 ? 3 * TY * n : 2147483647, kSiteTmaStencil) &&
+          OTM_BOUND(oa > ob ? oa : ob, n * n, kSiteTmaStencil)))
+        *(volatile int*)&bail_s = 1;
 
     f2p A[3];               // lower-plane partial sums of node plane zj - 1
 

@@ -8,6 +8,7 @@
 #include <stddef.h>
 
 #include "otm.h"
+#include "check.cuh"
 
 namespace otm {
 

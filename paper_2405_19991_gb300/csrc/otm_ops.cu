@@ -75,7 +75,15 @@ otm_status finish(cudaStream_t st, const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return op_fail(OTM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    const std::string c = otm::check_take();   // empty unless a checking build saw a bad index
+    if (!c.empty()) return op_fail(OTM_ECUDA, std::string(what) + ": " + c);
     return OTM_OK;
+}
+
+// Evaluates one out-of-range and one in-range bound without any memory
+// access behind them.
+__global__ void k_check_selftest(int i, int n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)OTM_BOUND(i, n, otm::kSiteSelftest);
 }
 
 // Set by a kernel whose bounded wait ran out (the TMA-staged stencil).
@@ -371,6 +379,22 @@ otm_status otm_op_mma_update(int dtype, int n, int iter, double g, double eps, d
     if (dtype == OTM_FP64)
         return mma_t<double>(n, iter, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, lambda_out, stream);
     return mma_t<float>(n, iter, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, lambda_out, stream);
+}
+
+otm_status otm_check_selftest(int* fired) {
+    OP_CHECK(!fired, "otm_check_selftest: NULL");
+    *fired = 0;
+    if (!otm::kCheckBuild)
+        return op_fail(OTM_ESTATE, "otm_check_selftest: not a checking build (compile with -DOTM_CHECK)");
+    (void)otm::check_take();
+    k_check_selftest<<<1, 32>>>(5, 4);   // index 5 of 4: must be recorded
+    if (cudaDeviceSynchronize() != cudaSuccess) return op_fail(OTM_ECUDA, "otm_check_selftest: launch");
+    const std::string a = otm::check_take();
+    k_check_selftest<<<1, 32>>>(3, 4);   // index 3 of 4: must not be
+    if (cudaDeviceSynchronize() != cudaSuccess) return op_fail(OTM_ECUDA, "otm_check_selftest: launch");
+    const std::string b = otm::check_take();
+    *fired = !a.empty() && b.empty() ? 1 : -1;
+    return OTM_OK;
 }
 
 otm_status otm_op_oc_update(int dtype, int n, double vstar, double move, double damp, double rho_min,

@@ -38,6 +38,17 @@ otm_status ufail(otm_status st, const std::string& m) {
         }                                                                                            \
     } while (0)
 #define U_LAUNCH() U_CU(cudaGetLastError())
+// stream synchronisation of an entry point; in a checking build a failed
+// bounds check in this unit's kernels fails the call
+#define U_SYNC(st)                                                                                   \
+    do {                                                                                             \
+        U_CU(cudaStreamSynchronize(st));                                                             \
+        const std::string c_ = otm::check_take();                                                    \
+        if (!c_.empty()) {                                                                           \
+            otm::set_thread_error(c_);                                                               \
+            return OTM_ECUDA;                                                                        \
+        }                                                                                            \
+    } while (0)
 #define U_TRY(x)                                                                                     \
     do {                                                                                             \
         otm_status s_ = (x);                                                                         \
@@ -445,7 +456,7 @@ struct otm_unet {
         U_CU(cudaMemcpyAsync(p, h.data(), P * sizeof(float), cudaMemcpyHostToDevice, stream));
         U_TRY(reset_moments(stream));
         U_TRY(pack(stream));
-        U_CU(cudaStreamSynchronize(stream));
+        U_SYNC(stream);
         return OTM_OK;
     }
 
@@ -656,7 +667,7 @@ OTM_API otm_status otm_unet_get_params(otm_unet* u, float* p, int on_device) {
     if (!u || !p) return ufail(OTM_EINVAL, "otm_unet_get_params: NULL argument");
     U_CU(cudaMemcpyAsync(p, u->p, u->P * sizeof(float), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                          u->stream));
-    U_CU(cudaStreamSynchronize(u->stream));
+    U_SYNC(u->stream);
     return OTM_OK;
 }
 
@@ -666,7 +677,7 @@ OTM_API otm_status otm_unet_set_params(otm_unet* u, const float* p, int on_devic
                          u->stream));
     U_TRY(u->reset_moments(u->stream));
     U_TRY(u->pack(u->stream));
-    U_CU(cudaStreamSynchronize(u->stream));
+    U_SYNC(u->stream);
     return OTM_OK;
 }
 
@@ -675,7 +686,7 @@ OTM_API otm_status otm_unet_forward(otm_unet* u, const float* x, float* y, void*
     cudaStream_t st = pick(u, stream);
     U_TRY(u->forward(x, st));
     U_CU(cudaMemcpyAsync(y, u->y, 3 * u->Nl[0] * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     return OTM_OK;
 }
 
@@ -685,7 +696,7 @@ OTM_API otm_status otm_unet_backward(otm_unet* u, const float* dy, float* grads,
     cudaStream_t st = pick(u, stream);
     U_TRY(u->backward(dy, st));
     if (grads) U_CU(cudaMemcpyAsync(grads, u->g, u->P * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     return OTM_OK;
 }
 
@@ -702,7 +713,7 @@ OTM_API otm_status otm_unet_get_activation(otm_unet* u, int block, int which, fl
     cudaStream_t st = pick(u, stream);
     otm::nn::k_bf16_to_f32<<<elt_grid(N * C), 256, 0, st>>>(N * C, src, out);
     U_LAUNCH();
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     *channels = C;
     return OTM_OK;
 }
@@ -719,7 +730,7 @@ OTM_API otm_status otm_unet_train_step(otm_unet* u, const float* x, const float*
     U_TRY(u->backward(u->dy, st));
     U_TRY(u->adam(lr, st));
     U_CU(cudaMemcpyAsync(u->loss_h, u->loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     if (loss) *loss = *u->loss_h;
     return OTM_OK;
 }
@@ -733,7 +744,7 @@ OTM_API otm_status otm_unet_eval(otm_unet* u, const float* x, const float* targe
     U_TRY(u->forward(x, st));
     U_TRY(u->loss(target, target_scale, st));
     U_CU(cudaMemcpyAsync(u->loss_h, u->loss_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     *loss = *u->loss_h;
     return OTM_OK;
 }
@@ -746,7 +757,7 @@ OTM_API otm_status otm_op_conv3(int n, int cin, int cout, const void* in, const 
     if (!in || !w || !out) return ufail(OTM_EINVAL, "otm_op_conv3: NULL pointer");
     cudaStream_t st = (cudaStream_t)stream;
     U_TRY(conv3(n, cin, cout, (const bf16*)in, (const bf16*)w, bias, relu != 0, (bf16*)out, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     return conv_flag("otm_op_conv3");
 }
 
@@ -773,7 +784,7 @@ OTM_API otm_status otm_op_conv3_dgrad(int n, int cin, int cout, const void* g, c
     cudaFreeAsync(wc, st);
     cudaFreeAsync(wt, st);
     if (s2 != OTM_OK) return s2;
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     return conv_flag("otm_op_conv3_dgrad");
 }
 
@@ -785,7 +796,7 @@ OTM_API otm_status otm_op_conv3_wgrad(int n, int cin, int cout, const void* in, 
     if (!in || !g || !dw) return ufail(OTM_EINVAL, "otm_op_conv3_wgrad: NULL pointer");
     cudaStream_t st = (cudaStream_t)stream;
     U_TRY(conv3_wgrad(n, cin, cin, cout, (const bf16*)in, (const bf16*)g, dw, db, st));
-    U_CU(cudaStreamSynchronize(st));
+    U_SYNC(st);
     return OTM_OK;
 }
 

@@ -1639,6 +1639,7 @@ if (tma_pcg_.grid > 0)
         loc.kernel_launches = (int)(nl_ - nl0);
         if (info) *info = loc;
         have_prev = false;
+        OTM_TRY(take_check());
         return sst;
     }
 
@@ -1694,7 +1695,15 @@ if (tma_pcg_.grid > 0)
         loc.kernel_launches = (int)(nl_ - nl0);
         iteration += 1;
         if (info) *info = loc;
+        OTM_TRY(take_check());
         return sst;
+    }
+    // Checking build: a bounds check that failed in this unit's kernels fails the call.
+    otm_status take_check() {
+        const std::string c = check_take();
+        if (c.empty()) return OTM_OK;
+        err = c;
+        return OTM_ECUDA;
     }
 
     // ---------------------------------------------------------- checkpoint

@@ -7,7 +7,9 @@ import ctypes as C
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libotm.so")
+# OTM_LIBRARY=check loads the bounds-checking build (libotm_check.so, from
+# build.py --check) instead of the normal one.
+LIB_PATH = os.path.join(_PKG, "libotm_check.so" if os.environ.get("OTM_LIBRARY") == "check" else "libotm.so")
 
 OTM_OK, OTM_EINVAL, OTM_ENOMEM, OTM_ECUDA, OTM_ENOCONV, OTM_ETIMEOUT, OTM_ESTATE = range(7)
 STATUS_NAMES = {0: "OTM_OK", 1: "OTM_EINVAL", 2: "OTM_ENOMEM", 3: "OTM_ECUDA",
@@ -148,6 +150,7 @@ def _load():
         "otm_op_kappa_sens": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_op_oc_update": [i, i, d, d, d, d, vp, vp, vp, P(C.c_double), vp],
         "otm_op_mma_update": [i, i, i, d, d, d, d, d, vp, vp, vp, vp, vp, vp, P(C.c_double), vp],
+        "otm_check_selftest": [P(C.c_int)],
         "otm_op_kappa_sens_noalloc": [i, i, d, d, d, vp, vp, vp, P(C.c_double), P(C.c_double), vp, vp],
         "otm_unet_create": [i, P(C.c_int), C.c_uint64, vp, P(vp)],
         "otm_unet_destroy": [vp],
@@ -186,6 +189,7 @@ EXPORTED = [
     "otm_unet_param_count", "otm_unet_get_params", "otm_unet_set_params", "otm_unet_forward",
     "otm_unet_backward", "otm_unet_train_step", "otm_unet_eval", "otm_set_predictor", "otm_op_conv3",
     "otm_op_conv3_wgrad", "otm_op_conv3_dgrad", "otm_unet_get_activation", "otm_op_mma_update",
+    "otm_check_selftest",
 ]
 
 
@@ -363,6 +367,14 @@ def otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, rho, s, rho_new, stre
     check(lib.otm_op_oc_update(dtype, n, vstar, move, damp, rho_min, _p(rho), _p(s), _p(rho_new),
                                C.byref(lam), stream))
     return lam.value
+
+
+def otm_check_selftest():
+    """1: the checking build recorded exactly the out-of-range index; raises
+    OtmError(OTM_ESTATE) in the normal build."""
+    fired = C.c_int(0)
+    check(lib.otm_check_selftest(C.byref(fired)))
+    return fired.value
 
 
 def otm_op_mma_update(dtype, n, it, g, eps, move, c, d, x, dg, xold1, xold2, low, upp, stream=None):

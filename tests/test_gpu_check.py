@@ -1,0 +1,123 @@
+"""The bounds-checking build (libotm built with -DOTM_CHECK): its flag
+mechanism fires on an out-of-range index and only then, and a workload
+through the checked kernels -- the TMA stencil and group pass at every
+staged size, the gather forms, every V-cycle level shape, MMA, the tcgen05
+convolution and the network -- records no bad index and gives the same
+bits as the normal build.  Nothing here makes an out-of-range access: the
+self-test evaluates an index with no memory access behind it."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def check_lib():
+    res = subprocess.run([sys.executable, "-c",
+                          "import importlib, sys; sys.path.insert(0, sys.argv[1]); "
+                          "b = importlib.import_module('paper_2405_19991_gb300.build'); print(b.build(check=True))",
+                          ROOT],
+                         capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stdout + res.stderr
+    return res.stdout.strip().splitlines()[-1]
+
+
+def _run(script, lib, *args, timeout=600):
+    env = dict(os.environ)
+    if lib == "check":
+        env["OTM_LIBRARY"] = "check"
+    else:
+        env.pop("OTM_LIBRARY", None)
+    res = subprocess.run([sys.executable, "-c", script, ROOT, *map(str, args)], env=env, capture_output=True,
+                         text=True, timeout=timeout)
+    assert res.returncode == 0, res.stdout + res.stderr
+    return res.stdout
+
+
+_SELF = r"""
+import sys
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+try:
+    print("FIRED", otm.otm_check_selftest(), otm.LIB_PATH)
+except otm.OtmError as e:
+    print("STATUS", e.status)
+"""
+
+
+def test_selftest_fires_only_in_the_checking_build(check_lib):
+    out = _run(_SELF, "check")
+    assert "FIRED 1" in out and "libotm_check.so" in out, out
+    out = _run(_SELF, "normal")
+    assert "STATUS 6" in out, out   # OTM_ESTATE: not a checking build
+
+
+_WORK = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+from paper_2405_19991_gb300 import otm
+import workloads as W
+out = {}
+dev = "cuda"
+def t32(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev)
+# fine operators: TMA-staged sizes and gather sizes
+for n in (6, 8, 32, 64, 96, 128):
+    rho = W.random_density(n, 3)
+    k = t32(1e-3 + rho ** 3 * (1 - 1e-3))
+    u = t32(W.random_field(n, 4).ravel())
+    o = torch.empty(3 * n ** 3, dtype=torch.float32, device=dev)
+    otm.otm_op_apply_K(1, n, k, u, o)
+    out[f"K{n}"] = o.cpu().numpy()
+    T = t32(W.random_field(n, 5).ravel())
+    f = t32(W.random_field(n, 6).ravel())
+    for g in range(4):
+        otm.otm_op_gs_colour(1, n, k, f, T, 8 + g)
+    otm.otm_op_gs_colour(1, n, k, f, T, 3)
+    out[f"T{n}"] = T.cpu().numpy()
+# design iterations: every hierarchy shape, precision and optimizer
+cases = [(8, 0, 0), (12, 0, 0), (16, 1, 0), (24, 2, 0), (48, 1, 0), (64, 2, 0), (128, 1, 0), (16, 1, 1), (32, 2, 1)]
+for n, prec, opt in cases:
+    p = otm.otm_params_default(n=n, precision=prec, cg_tol=1e-6 if prec else 1e-10, rmin=1.5,
+                               kappa_target=W.TARGET_ORTHOTROPIC, optimizer=opt)
+    ctx = otm.otm_create_ex(p)
+    r0 = W.initial_density(n, 0.3, 7).astype(np.float32)
+    otm.otm_set_density(ctx, r0.ctypes.data, 0)
+    otm.otm_run(ctx, 2)
+    rho = np.empty(n ** 3, np.float32)
+    otm.otm_get_density(ctx, rho.ctypes.data, 0)
+    out[f"rho{n}_{prec}_{opt}"] = rho
+    otm.otm_destroy(ctx)
+# the network: tcgen05 convolutions, forward and one training step
+n = 16
+un = otm.otm_unet_create(n, [16, 32, 64, 128], 1, None)
+x = t32(W.random_density(n, 8).ravel())
+y = torch.empty(3 * n ** 3, dtype=torch.float32, device=dev)
+otm.otm_unet_forward(un, x, y)
+out["net"] = y.cpu().numpy()
+tgt = t32(W.random_field(n, 9).ravel())
+otm.otm_unet_train_step(un, x, tgt, 1e-3, 1.0)
+otm.otm_unet_forward(un, x, y)
+out["net2"] = y.cpu().numpy()
+otm.otm_unet_destroy(un)
+np.savez(sys.argv[2], **out)
+print("DONE", len(out))
+"""
+
+
+def test_checked_workload_records_nothing_and_matches_the_normal_build(check_lib, tmp_path):
+    a, b = str(tmp_path / "check.npz"), str(tmp_path / "normal.npz")
+    assert "DONE" in _run(_WORK, "check", a)
+    assert "DONE" in _run(_WORK, "normal", b)
+    A, B = np.load(a), np.load(b)
+    assert sorted(A.files) == sorted(B.files)
+    for key in A.files:
+        assert np.array_equal(A[key].view(np.uint32), B[key].view(np.uint32)), key
