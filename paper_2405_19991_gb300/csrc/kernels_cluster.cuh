@@ -102,13 +102,10 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
     S* Rs = reinterpret_cast<S*>(sm + a.tR);
     {
         const int nb = a.n[a.lb];
-        const int m = 4 * nb * nb * nb;
-        for (int i = t0; i < m; i += ts) Fs(a.lb)[i] = a.F[a.lb][i];
-        for (int l = a.lb; l <= a.L; ++l) {
-            const int ma = cl_aw<S>() * a.n[l] * a.n[l] * a.n[l];
-            S* dst = reinterpret_cast<S*>(sm + a.tA[l]);
-            for (int i = t0; i < ma; i += ts) dst[i] = a.A[l][i];
-        }
+        block_copy_async(Fs(a.lb), a.F[a.lb], (size_t)4 * nb * nb * nb * sizeof(S));
+        for (int l = a.lb; l <= a.L; ++l)
+            block_copy_async(sm + a.tA[l], a.A[l], (size_t)cl_aw<S>() * a.n[l] * a.n[l] * a.n[l] * sizeof(S));
+        cp_async_wait_all();
     }
     __syncthreads();
     for (int l = a.lb; l < a.L; ++l) {

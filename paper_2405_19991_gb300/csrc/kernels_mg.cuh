@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "otm_internal.cuh"
+#include "ptx_async.cuh"
 
 namespace otm {
 
@@ -670,12 +671,28 @@ __device__ void coarse_solve_block(int n, const C* __restrict__ Minv, const FT* 
     }
 }
 
+// Block-wide copy of `bytes` from global to shared memory: every thread
+// issues its share of 16-byte asynchronous copies, all in flight at once
+// (an element loop would wait one L2 round trip per element: the compiler
+// cannot move a global load past a shared store through generic pointers),
+// and a ragged tail is copied byte by byte.  Both addresses 16-byte
+// aligned.  The caller waits (cp_async_wait_all) and then synchronises the
+// block.
+__device__ __forceinline__ void block_copy_async(void* dst, const void* src, size_t bytes) {
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    const size_t n16 = bytes / 16;
+    for (size_t i = threadIdx.x; i < n16; i += blockDim.x) cp_async16(d + 16 * i, s + 16 * i);
+    for (size_t i = 16 * n16 + threadIdx.x; i < bytes; i += blockDim.x) d[i] = s[i];
+}
+
 // Stage Minv in dynamic shared memory when use_smem (blockDim threads copy).
 template <class C>
 __device__ __forceinline__ const C* stage_minv(const C* __restrict__ Minv_g, int q, int use_smem, unsigned char* sm) {
     if (!use_smem) return Minv_g;
     C* ms = reinterpret_cast<C*>(sm);
-    for (int i = threadIdx.x; i < q * q; i += blockDim.x) ms[i] = Minv_g[i];
+    block_copy_async(ms, Minv_g, (size_t)q * q * sizeof(C));
+    cp_async_wait_all();
     __syncthreads();
     return ms;
 }
