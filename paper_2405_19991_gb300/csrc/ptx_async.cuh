@@ -72,6 +72,16 @@ __device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, u
 }
 
 
+// Distributed shared memory: the generic address of the same shared-memory
+// location in CTA `rank` of this thread-block cluster; ordinary loads and
+// stores through it reach that CTA's shared memory.
+template <class T>
+__device__ __forceinline__ T* dsm_ptr(T* p, uint32_t rank) {
+    uint64_t r;
+    asm("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(p), "r"(rank));
+    return reinterpret_cast<T*>(r);
+}
+
 // 16-byte global -> shared copy through the asynchronous copy unit (L2 only)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");

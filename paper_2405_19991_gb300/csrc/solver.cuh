@@ -288,13 +288,37 @@ class Solver : public SolverBase {
             if (sz[l] <= tail_maxn && tail_layout<S, C>(l, L, szs, mv).total <= kTailSmemBudget) return l;
         return L + 1;
     }
-    size_t cluster_smem_bytes() const {
+    size_t cluster_smem_base() const {
         const int L = nlev - 1;
         const int lb = tail_lb();
         if (lb > L) return minv_smem_bytes(L);
         int szs[kMaxLevelsDev] = {};
         for (int l = 0; l <= L; ++l) szs[l] = sz[l];
         return tail_layout<S, C>(lb, L, szs, minv_smem_bytes(L) > 0 ? 1 : 0).total;
+    }
+    // The one cluster-wide level above the tail in the CTAs' shared memory
+    // (Gauss-Seidel smoothing only; OTM_CLUSTER_DSM=0 keeps it in global
+    // memory): its index, or -1 when that form does not apply.
+    bool dsm_on_ = true;
+    int dsm_level() const {
+        const int L = nlev - 1;
+        const int lc = cluster_lc();
+        if (!dsm_on_ || cheb_ || lc > L || tail_lb() != lc + 1) return -1;
+        return lc;
+    }
+    static size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+    // per-CTA bytes of that level with G CTAs: stencil rows, right-hand side,
+    // field and residual of 8 ceil(h^3 / G) slots
+    size_t dsm_bytes(int l, int G) const {
+        const size_t h = (size_t)sz[l] / 2, slots = 8 * ((h * h * h + G - 1) / G);
+        return al16(slots * CL<S>::AW * sizeof(S)) + 3 * al16(slots * 4 * sizeof(S));
+    }
+    // dynamic shared memory of the cluster kernel: the tail, then (sized for
+    // 8 CTAs, the larger share, so either cluster size fits) the level above it
+    size_t cluster_smem_bytes() const {
+        const size_t base = cluster_smem_base();
+        const int dl = dsm_level();
+        return dl < 0 ? base : al16(base) + dsm_bytes(dl, 8);
     }
     size_t minv_smem_bytes(int l) const {
         const size_t q = Nl[l] - 1;
@@ -525,6 +549,8 @@ class Solver : public SolverBase {
             OTM_CU(cudaFuncGetAttributes(&fa, k_coarse_cluster<S, C>));
             int optin = 0;
             OTM_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+            if (const char* e = getenv("OTM_CLUSTER_DSM")) dsm_on_ = e[0] != '0';
+            if (fa.sharedSizeBytes + cluster_smem_bytes() > (size_t)optin) dsm_on_ = false;
             if (fa.sharedSizeBytes + cluster_smem_bytes() > (size_t)optin) tail_maxn = 0;
             const size_t cs = cluster_smem_bytes();
             if (fa.sharedSizeBytes + cs > (size_t)optin) {
@@ -898,6 +924,23 @@ class Solver : public SolverBase {
                 ca.A[l] = Al[l];
             }
             ca.Minv = Minv;
+            const int dl = dsm_level();
+            if (dl >= 0) {
+                const int G = cl_ctas_;
+                const size_t h = (size_t)sz[dl] / 2, mg = (h * h * h + G - 1) / G, slots = 8 * mg;
+                size_t off = al16(cluster_smem_base());
+                ca.dA = (unsigned)off;
+                off += al16(slots * CL<S>::AW * sizeof(S));
+                ca.dF = (unsigned)off;
+                off += al16(slots * 4 * sizeof(S));
+                ca.dT = (unsigned)off;
+                off += al16(slots * 4 * sizeof(S));
+                ca.dR = (unsigned)off;
+                ca.dsm = 1;
+                ca.dmg = (int)mg;
+                ca.dlg = G == 16 ? 4 : 3;
+            }
+            OTM_TRY(raise_cluster_smem(cluster_smem_bytes()));
             ++nl_;
             const cudaError_t le = launch_cluster_pdl(k_coarse_cluster<S, C>, cl_ctas_, kClusterThreads,
                                                       cluster_smem_bytes(), stream, ca);
