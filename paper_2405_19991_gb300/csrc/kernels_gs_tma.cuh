@@ -59,9 +59,12 @@ __host__ __device__ inline int gs_tma_stage_bytes(int n, int ty, int st, int ft)
 }
 
 // Output rows per CTA: the largest TY with 2 TY | n, (n / 2) TY <= 256
-// threads in whole warps, and at least two row blocks.
+// threads in whole warps, and at least two row blocks; at most 2 from
+// n = 128 on (128^3 design iteration: 2.326 ms FP32 with two rows against
+// 2.338 with four, 2.294 against 2.299 mixed -- more, smaller CTAs hide the
+// ring's fill latency better).
 __host__ __device__ constexpr int gs_tma_rows_c(int n) {
-    for (int t = n / 4; t >= 1; --t)
+    for (int t = n >= 128 ? 2 : n / 4; t >= 1; --t)
         if (n % (2 * t) == 0 && (n / 2) * t <= kTmaThreads && ((n / 2) * t) % 32 == 0 && n / (2 * t) >= 2) return t;
     return 0;
 }
@@ -371,7 +374,7 @@ inline int gs_choice() {
 }
 
 inline int gs_tma_rows(int n) {
-    for (int t = n / 4; t >= 1; --t)
+    for (int t = n >= 128 ? 2 : n / 4; t >= 1; --t)
         if (n % (2 * t) == 0 && (n / 2) * t <= kTmaThreads && ((n / 2) * t) % 32 == 0 && n / (2 * t) >= 2) return t;
     return 0;
 }
