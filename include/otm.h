@@ -237,6 +237,10 @@ OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
  *                   1 gather (OTM_GS); every form gives the same bits
  *   gs_chunks       runs of output planes per row block of the TMA-staged
  *                   group pass (0: not used)
+ *   gs_stages       its ring depth: timed by the tuner after the cluster
+ *                   choice, among 4, 5 and 6 (OTM_GS_STAGES fixes it)
+ *   gs_tune_us      measured time of one V-cycle at depths 4, 5, 6; 0 when
+ *                   not measured
  * Errors: OTM_EINVAL for NULL arguments; CUDA errors as OTM_ECUDA. */
 typedef struct {
     int stencil_form;
@@ -250,6 +254,9 @@ typedef struct {
     double tune_us[4];
     int gs_form;
     int gs_chunks;
+    int gs_stages;
+    int reserved_cfg;
+    double gs_tune_us[3];
 } otm_config;
 OTM_API otm_status otm_get_config(otm_ctx* ctx, otm_config* out);
 

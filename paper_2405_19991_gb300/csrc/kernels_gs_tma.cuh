@@ -393,6 +393,7 @@ inline bool gs_tma_ok(int n, int st_size, int ft_size) {
 // iteration at 5 stages, 2.45 at 4, 2.59 at 6, 2.55 at 8; six FP32 stages
 // fill 215 KB of each SM's shared memory with two CTAs, which costs more
 // than the deeper ring gains where the pass overlaps its neighbours).
+inline bool gs_tma_stages_fixed() { return getenv("OTM_GS_STAGES") != nullptr; }
 inline int gs_tma_stages() {
     static int s = [] {
         const char* e = getenv("OTM_GS_STAGES");
@@ -480,14 +481,15 @@ static GsTmaKernel<ST, FT> gs_tma_kernel(int n) {
     return k_gs_tma<0, ST, FT>;
 }
 
+// stages: ring depth (0: the default, gs_tma_stages)
 template <class ST, class FT>
-static bool gs_tma_launch_shape(TmaLaunch& L, int n, int sm_count) {
+static bool gs_tma_launch_shape(TmaLaunch& L, int n, int sm_count, int stages = 0) {
     if (!gs_tma_ok(n, (int)sizeof(ST), (int)sizeof(FT))) return false;
     auto kern = gs_tma_kernel<ST, FT>(n);
     L.n = n;
     L.ty = gs_tma_rows(n);
     L.threads = (n / 2) * L.ty + 32;   // consumer warps + the producer warp
-    L.stages = gs_tma_stages();
+    L.stages = stages >= 4 && stages <= kTmaMaxStages ? stages : gs_tma_stages();
     L.smem = (size_t)L.stages * gs_tma_stage_bytes(n, L.ty, (int)sizeof(ST), (int)sizeof(FT)) + 128;
     {
         static std::mutex mu;

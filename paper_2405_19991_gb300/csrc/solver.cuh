@@ -263,6 +263,7 @@ class Solver : public SolverBase {
     bool tuned_ = false;
     int autotuned_ = 0;
     double tune_us_[4] = {0, 0, 0, 0};
+    double gs_tune_us_[3] = {0, 0, 0};   // V-cycle us of the group pass at ring depths 4, 5, 6
     int cluster_lc() const {
         const int L = nlev - 1;
         if (!use_cluster || nlev < 2) return L + 1;
@@ -1317,6 +1318,8 @@ if (tma_pcg_.grid > 0)
     struct TuneVal {
         int maxn, ctas;
         double us[4];
+        int gs_stages;      // ring depth of the TMA group pass (0: not tuned)
+        double gs_us[3];    // V-cycle us at depths 4, 5, 6 (0: not measured)
     };
     static std::mutex& tune_mutex() {
         static std::mutex m;
@@ -1340,7 +1343,19 @@ if (tma_pcg_.grid > 0)
             cudaEvent_t e0, e1;
             OTM_CU(cudaEventCreate(&e0));
             OTM_CU(cudaEventCreate(&e1));
-            TuneVal best{keep_maxn, keep_ctas, {0, 0, 0, 0}};
+            // microseconds of one V-cycle (two warm-up cycles, four timed)
+            auto time_vcycle = [&](otm_status& st) -> double {
+                for (int w = 0; w < 2 && st == OTM_OK; ++w) st = vcycle();
+                if (st != OTM_OK) return 0.0;
+                if (cudaEventRecord(e0, stream) != cudaSuccess) st = OTM_ECUDA;
+                for (int r = 0; r < 4 && st == OTM_OK; ++r) st = vcycle();
+                if (st == OTM_OK && cudaEventRecord(e1, stream) != cudaSuccess) st = OTM_ECUDA;
+                if (st == OTM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = OTM_ECUDA;
+                float ms = 0.f;
+                if (st == OTM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = OTM_ECUDA;
+                return st == OTM_OK ? 1000.0 * ms / 4.0 : 0.0;
+            };
+            TuneVal best{keep_maxn, keep_ctas, {0, 0, 0, 0}, 0, {0, 0, 0}};
             double best_us = 0.0;
             otm_status st = OTM_OK;
             for (int c = 0; c < 4 && st == OTM_OK; ++c) {
@@ -1349,21 +1364,39 @@ if (tma_pcg_.grid > 0)
                 if (cand[c][1] == 16 && !cl16_ok_) continue;
                 cluster_maxn = cand[c][0];
                 cl_ctas_ = cand[c][1];
-                for (int w = 0; w < 2 && st == OTM_OK; ++w) st = vcycle();
+                const double us = time_vcycle(st);
                 if (st != OTM_OK) break;
-                if (cudaEventRecord(e0, stream) != cudaSuccess) st = OTM_ECUDA;
-                for (int r = 0; r < 4 && st == OTM_OK; ++r) st = vcycle();
-                if (st == OTM_OK && cudaEventRecord(e1, stream) != cudaSuccess) st = OTM_ECUDA;
-                if (st == OTM_OK && cudaEventSynchronize(e1) != cudaSuccess) st = OTM_ECUDA;
-                float ms = 0.f;
-                if (st == OTM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = OTM_ECUDA;
-                if (st != OTM_OK) break;
-                const double us = 1000.0 * ms / 4.0;
                 best.us[c] = us;
                 if (best_us == 0.0 || us < best_us) {
                     best_us = us;
                     best.maxn = cand[c][0];
                     best.ctas = cand[c][1];
+                }
+            }
+            // then, with that cluster configuration, the TMA group pass's ring
+            // depth (a shape change only: every depth gives the same bits)
+            if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
+                if (st == OTM_OK && tma_gs_.grid > 0 && !gs_tma_stages_fixed()) {
+                    cluster_maxn = best.maxn;
+                    cl_ctas_ = best.ctas;
+                    const TmaLaunch keep_gs = tma_gs_;
+                    double gbest = 0.0;
+                    for (int d = 4; d <= 6 && st == OTM_OK; ++d) {
+                        TmaLaunch L;
+                        if (!gs_tma_launch_shape<S, float>(L, n, sm_count, d)) {
+                            cudaGetLastError();
+                            continue;
+                        }
+                        tma_gs_ = L;
+                        const double us = time_vcycle(st);
+                        if (st != OTM_OK) break;
+                        best.gs_us[d - 4] = us;
+                        if (gbest == 0.0 || us < gbest) {
+                            gbest = us;
+                            best.gs_stages = d;
+                        }
+                    }
+                    tma_gs_ = keep_gs;
                 }
             }
             cudaEventDestroy(e0);
@@ -1379,6 +1412,14 @@ if (tma_pcg_.grid > 0)
         cluster_maxn = it->second.maxn;
         cl_ctas_ = it->second.ctas;
         for (int c = 0; c < 4; ++c) tune_us_[c] = it->second.us[c];
+        for (int d = 0; d < 3; ++d) gs_tune_us_[d] = it->second.gs_us[d];
+        if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value) {
+            TmaLaunch L;
+            if (it->second.gs_stages > 0 && tma_gs_.grid > 0 &&
+                gs_tma_launch_shape<S, float>(L, n, sm_count, it->second.gs_stages))
+                tma_gs_ = L;
+            cudaGetLastError();
+        }
         autotuned_ = 1;
         return OTM_OK;
     }
@@ -1399,6 +1440,8 @@ if (tma_pcg_.grid > 0)
         for (int c = 0; c < 4; ++c) out->tune_us[c] = tune_us_[c];
         out->gs_form = tma_gs_.grid > 0 ? 0 : 1;
         out->gs_chunks = tma_gs_.grid > 0 ? tma_gs_.m : 0;
+        out->gs_stages = tma_gs_.grid > 0 ? tma_gs_.stages : 0;
+        for (int d = 0; d < 3; ++d) out->gs_tune_us[d] = gs_tune_us_[d];
         return OTM_OK;
     }
 

@@ -70,10 +70,14 @@ class otm_config(C.Structure):
         ("tune_us", C.c_double * 4),
         ("gs_form", C.c_int),
         ("gs_chunks", C.c_int),
+        ("gs_stages", C.c_int),
+        ("reserved_cfg", C.c_int),
+        ("gs_tune_us", C.c_double * 3),
     ]
 
     def as_dict(self):
-        return {f: (list(getattr(self, f)) if f == "tune_us" else getattr(self, f)) for f, _ in self._fields_}
+        return {f: (list(getattr(self, f)) if f in ("tune_us", "gs_tune_us") else getattr(self, f))
+                for f, _ in self._fields_}
 
 
 class otm_step_info(C.Structure):

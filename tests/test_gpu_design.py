@@ -288,6 +288,11 @@ def test_autotuned_configuration_is_valid(n, precision):
                         if per_m * m <= 8 * sms}
                 ok.append(cost[cfg["stencil_chunks"]] <= min(cost.values()) * (1 + 1e-12))
             assert any(ok), cfg
+        if cfg["gs_form"] == 0:
+            # the group pass's ring depth: the fastest of the timed depths 4, 5, 6
+            gus = cfg["gs_tune_us"]
+            assert cfg["gs_stages"] in (4, 5, 6) and all(u >= 0 for u in gus) and max(gus) > 0, cfg
+            assert gus[cfg["gs_stages"] - 4] == min(u for u in gus if u > 0), cfg
         info, st = otm.otm_step(ctx)
         assert st == otm.OTM_OK and max(info.resid) <= 1e-6 * 1.0001
     finally:
