@@ -813,6 +813,18 @@ class Solver : public SolverBase {
     }
 
     // One fine-grid Gauss-Seidel group pass.
+    // One colour pass of a standalone coarse level l; early_f: f was written
+    // two or more kernels back, so it may be loaded before the wait on the
+    // previous kernel (the stencil always is)
+    template <bool ZERO>
+    void coarse_gs_pass(int l, int c, int early_f) {
+        const auto cfg = rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]));
+        if (pdl_early())
+            launch_pdl(k_gs_stencil_pf<ZERO, S, S, S>, OTM_ROWS_CFG(cfg), stream, sz[l], c, Al[l], Fl[l], Tl[l],
+                       early_f);
+        else
+            launch_pdl(k_gs_stencil<ZERO, S, S, S>, OTM_ROWS_CFG(cfg), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+    }
     // TMA-staged fine group pass (FP32 or BF16 storage, f in FP32); grid 0
     // when the gather form runs
     TmaLaunch tma_gs_;
@@ -882,10 +894,10 @@ class Solver : public SolverBase {
                 Tcur = T2l[l];
             } else {
                 ++nl_;
-                launch_pdl(k_gs_stencil<true, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], 0, Al[l], Fl[l], Tl[l]);
+                coarse_gs_pass<true>(l, 0, 0);   // f: written by the restriction just before
                 for (int c = 1; c < 8; ++c) {
                     ++nl_;
-                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                    coarse_gs_pass<false>(l, c, 1);
                 }
             }
             ++nl_;
@@ -964,7 +976,7 @@ class Solver : public SolverBase {
             } else {
                 for (int c = 7; c >= 0; --c) {
                     ++nl_;
-                    launch_pdl(k_gs_stencil<false, S, S, S>, OTM_ROWS_CFG(rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]))), stream, sz[l], c, Al[l], Fl[l], Tl[l]);
+                    coarse_gs_pass<false>(l, c, 1);
                 }
             }
             OTM_LAUNCH();
