@@ -111,8 +111,8 @@ __device__ void coarse_tail_block(const ClusterArgs<S, C>& a, unsigned char* sm)
         // (with the level above in distributed shared memory, its restriction
         // has written F_lb here already)
         if (!a.dsm) block_copy_async(Fs(a.lb), a.F[a.lb], (size_t)4 * nb * nb * nb * sizeof(S));
-        for (int l = a.lb; l <= a.L; ++l)
-            block_copy_async(sm + a.tA[l], a.A[l], (size_t)cl_aw<S>() * a.n[l] * a.n[l] * a.n[l] * sizeof(S));
+        // (the stencils were issued at the kernel's start, before its wait on
+        // the previous kernel)
         cp_async_wait_all();
     }
     __syncthreads();
@@ -319,13 +319,35 @@ __device__ void dsm_prolong(const DsmLevel<S>& L, const S* __restrict__ Tc) {
 template <class S, class C>
 __global__ void __launch_bounds__(kClusterThreads)
 k_coarse_cluster(ClusterArgs<S, C> a) {
-    pdl_enter();
     extern __shared__ __align__(16) unsigned char cl_sm[];
     // node index t runs over the CTAs fastest, so a small pass spreads over
     // every SM of the cluster instead of filling CTA 0 first
     const int t0 = threadIdx.x * gridDim.x + blockIdx.x;
     const int ts = gridDim.x * blockDim.x;
     const int lend = a.lb <= a.L ? a.lb : a.L;   // first level not swept by the whole cluster
+    // The stencils were written at the hierarchy's setup, so their staging
+    // goes out before the wait on the previous kernel (whose output -- the
+    // cluster's first right-hand side -- is read only after it): the tail's
+    // in CTA 0, and the shared-memory level's rows in every CTA.
+    if (blockIdx.x == 0 && a.lb <= a.L)
+        for (int l = a.lb; l <= a.L; ++l)
+            block_copy_async(cl_sm + a.tA[l], a.A[l], (size_t)cl_aw<S>() * a.n[l] * a.n[l] * a.n[l] * sizeof(S));
+    if (a.dsm) {
+        const int l = a.lc, n = a.n[l], h = n / 2, M = h * h * h, lg = a.dlg;
+        constexpr int kRowBytes = cl_aw<S>() * (int)sizeof(S);   // a multiple of 16
+        for (int k = threadIdx.x; k < 8 * a.dmg; k += blockDim.x) {
+            const int c = k / a.dmg, j = k - c * a.dmg;
+            const int t = (int)blockIdx.x + (j << lg);
+            if (t >= M) continue;
+            const int x = 2 * (t % h) + (c & 1), y = 2 * ((t / h) % h) + ((c >> 1) & 1), z = 2 * (t / (h * h)) + (c >> 2);
+            const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(a.A[l] + v * cl_aw<S>());
+            unsigned char* dst = cl_sm + a.dA + (size_t)k * kRowBytes;
+#pragma unroll
+            for (int q = 0; q < kRowBytes / 16; ++q) cp_async16(dst + 16 * q, src + 16 * q);
+        }
+    }
+    pdl_enter();
     if (a.dsm) {
         // the one cluster-wide level lc in distributed shared memory, then the tail
         using CS = typename St<S>::C;
@@ -340,18 +362,13 @@ k_coarse_cluster(ClusterArgs<S, C> a) {
         Ld.F = reinterpret_cast<S*>(cl_sm + a.dF);
         Ld.T = reinterpret_cast<S*>(cl_sm + a.dT);
         Ld.R = reinterpret_cast<S*>(cl_sm + a.dR);
-        constexpr int kRowBytes = cl_aw<S>() * (int)sizeof(S);   // a multiple of 16
-        // this CTA's stencil rows (16-byte asynchronous copies) and right-hand
-        // side; its field starts at zero
+        // this CTA's right-hand side (its stencil rows are in flight since the
+        // kernel's start); its field starts at zero
         for (int k = threadIdx.x; k < 8 * Ld.MG; k += blockDim.x) {
             const int c = k / Ld.MG, j = k - c * Ld.MG;
             int x, y, z;
             if (!Ld.node(c, j, x, y, z)) continue;
             const size_t v = (size_t)x + (size_t)Ld.n * (y + (size_t)Ld.n * z);
-            const unsigned char* src = reinterpret_cast<const unsigned char*>(a.A[l] + v * cl_aw<S>());
-            unsigned char* dst = reinterpret_cast<unsigned char*>(Ld.A + (size_t)k * cl_aw<S>());
-#pragma unroll
-            for (int q = 0; q < kRowBytes / 16; ++q) cp_async16(dst + 16 * q, src + 16 * q);
             CS f3[3];
             ld_f3<S>(a.F[l], v, f3);
             st_f3<S>(Ld.F, k, f3[0], f3[1], f3[2]);

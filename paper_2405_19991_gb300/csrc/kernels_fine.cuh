@@ -737,6 +737,54 @@ k_prolong_add(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
     }
 }
 
+// k_prolong_add on a node-major coarse level that loads its first node's own
+// field value before waiting on the previous kernel (the level's field was
+// last written by its pre-smoothing, two or more kernels back; the coarser
+// field it adds comes from the previous kernel and is read after the wait).
+// The per-node arithmetic is prolong_node's.
+template <class CT, class TT>
+__global__ void __launch_bounds__(256)
+k_prolong_add_pf(int nf, const CT* __restrict__ Tc, TT* __restrict__ T) {
+    using C = typename St<TT>::C;
+    const int row0 = blockIdx.x * blockDim.y + threadIdx.y, x = threadIdx.x;
+    const bool first = row0 < nf * nf && x < nf;
+    const int y = row0 % nf, z = row0 / nf;
+    const size_t v = (size_t)x + (size_t)nf * (y + (size_t)nf * z);
+    C t0[3];
+    if (first) ld_f3<TT>(T, v, t0);
+    pdl_enter();
+    if (first && node_ok(x, y, z, nf, kSiteCoarse)) {
+        const int nc = nf / 2;
+        int xi[2], yi[2], zi[2];
+        C wx[2], wy[2], wz[2];
+        int cx, cy, cz;
+        if (x & 1) { xi[0] = x >> 1; xi[1] = wrapp(x >> 1, nc); wx[0] = wx[1] = C(0.5); cx = 2; }
+        else { xi[0] = xi[1] = x >> 1; wx[0] = C(1); wx[1] = 0; cx = 1; }
+        if (y & 1) { yi[0] = y >> 1; yi[1] = wrapp(y >> 1, nc); wy[0] = wy[1] = C(0.5); cy = 2; }
+        else { yi[0] = yi[1] = y >> 1; wy[0] = C(1); wy[1] = 0; cy = 1; }
+        if (z & 1) { zi[0] = z >> 1; zi[1] = wrapp(z >> 1, nc); wz[0] = wz[1] = C(0.5); cz = 2; }
+        else { zi[0] = zi[1] = z >> 1; wz[0] = C(1); wz[1] = 0; cz = 1; }
+        C acc[3] = {C(0), C(0), C(0)};
+        for (int c = 0; c < cz; ++c)
+            for (int b = 0; b < cy; ++b)
+                for (int a = 0; a < cx; ++a) {
+                    typename St<CT>::C t[3];
+                    ld_f3<CT>(Tc, (size_t)xi[a] + (size_t)nc * (yi[b] + (size_t)nc * zi[c]), t);
+                    const C w = wz[c] * wy[b] * wx[a];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) acc[i] += w * (C)t[i];
+                }
+        st_f3<TT>(T, v, t0[0] + acc[0], t0[1] + acc[1], t0[2] + acc[2]);
+    }
+    OTM_FOR_ROWS(row, nf * nf) {
+        const int yy = row % nf, zz = row / nf;
+        OTM_FOR_X(xx, nf) {
+            if (row == row0 && xx == x) continue;
+            prolong_node<CT, TT, true>(nf, xx, yy, zz, Tc, T);
+        }
+    }
+}
+
 // x_i += alpha_i p_i (x held as hi + lo when xl is not null: the update is
 // added with TwoSum/TwoProduct and renormalised); r_i -= alpha_i q_i;
 // reduce r_i.r_i and (flexible) r_i.z_i.

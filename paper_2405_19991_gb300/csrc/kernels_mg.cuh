@@ -523,6 +523,53 @@ k_residual_stencil(int n, const AT* __restrict__ A, const FT* __restrict__ f, co
     }
 }
 
+// k_residual_stencil that loads its first node's stencil row and right-hand
+// side before waiting on the previous kernel (both written two or more
+// kernels back in the V-cycle: the stencils at setup, f by the restriction
+// before the level's pre-smoothing); the field follows the wait.  The
+// per-node arithmetic is residual_stencil_node's.
+template <class AT, class FT, class TT, class OT>
+__global__ void __launch_bounds__(256)
+k_residual_stencil_pf(int n, const AT* __restrict__ A, const FT* __restrict__ f, const TT* __restrict__ T,
+                      OT* __restrict__ res) {
+    using C = typename St<OT>::C;
+    const size_t N = (size_t)n * n * n;
+    const int row0 = blockIdx.x * blockDim.y + threadIdx.y, x = threadIdx.x;
+    const bool first = row0 < n * n && x < n;
+    const int y = row0 % n, z = row0 / n;
+    const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
+    C a[27], s[3];
+    if (first) {
+        ld_arow<AT>(A, v, a);
+        ld_f3<FT>(f, v, s);
+    }
+    pdl_enter();
+    if (first && node_ok(x, y, z, n, kSiteCoarse) && OTM_BOUND(v, N, kSiteCoarse)) {
+        int xs[3], ys[3], zs[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            xs[d] = wrapd(x, d - 1, n);
+            ys[d] = wrapd(y, d - 1, n) * n;
+            zs[d] = wrapd(z, d - 1, n) * n * n;
+        }
+#pragma unroll
+        for (int o = 0; o < 27; ++o) {
+            C t[3];
+            ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) s[i] -= a[o] * t[i];
+        }
+        st_f3<OT>(res, v, s[0], s[1], s[2]);
+    }
+    OTM_FOR_ROWS(row_, n * n) {
+        const int yy = row_ % n, zz = row_ / n;
+        OTM_FOR_X(xx, n) {
+            if (row_ == row0 && xx == x) continue;
+            residual_stencil_node<AT, FT, TT, OT>(n, N, xx, yy, zz, A, f, T, res);
+        }
+    }
+}
+
 // ---- coarsest level: dense inverse of the node-0-pinned operator ----
 // One CTA.  The dense matrix of the stencil without node 0's row and column
 // is inverted in place by Gauss-Jordan elimination without pivoting (the

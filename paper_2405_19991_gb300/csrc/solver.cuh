@@ -901,7 +901,12 @@ class Solver : public SolverBase {
                 }
             }
             ++nl_;
-            launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Al[l], Fl[l], (const S*)Tcur, Rl[l]);
+            if (pdl_early())   // stencil and f loaded before the wait on the last pre-smoothing pass
+                launch_pdl(k_residual_stencil_pf<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l],
+                           Al[l], Fl[l], (const S*)Tcur, Rl[l]);
+            else
+                launch_pdl(k_residual_stencil<S, S, S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l],
+                           Al[l], Fl[l], (const S*)Tcur, Rl[l]);
             ++nl_;
             launch_pdl(k_restrict<S, S, true>, OTM_ROWS_CFG(rl(sz[l + 1], sz[l + 1] * sz[l + 1])), stream, sz[l + 1], Rl[l], Fl[l + 1]);
             OTM_LAUNCH();
@@ -969,7 +974,11 @@ class Solver : public SolverBase {
         OTM_LAUNCH();
         for (int l = Lsep - 1; l >= 1; --l) {
             ++nl_;
-            launch_pdl(k_prolong_add<S, S, true>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
+            if (pdl_early())   // the level's own field loaded before the wait on the coarser level
+                launch_pdl(k_prolong_add_pf<S, S>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
+                           cheb_ ? T2l[l] : Tl[l]);
+            else
+                launch_pdl(k_prolong_add<S, S, true>, OTM_ROWS_CFG(rl(sz[l], sz[l] * sz[l])), stream, sz[l], Tl[l + 1],
                        cheb_ ? T2l[l] : Tl[l]);
             if (cheb_) {
                 cheb_smooth(l, false);
