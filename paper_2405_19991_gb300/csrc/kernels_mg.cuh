@@ -97,8 +97,7 @@ k_stencil1_from_k(int nc, const KT* __restrict__ k, const C* __restrict__ Bs, AT
             acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += e[j];
         }
     }
-#pragma unroll
-    for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
+    st_arow<AT, C>(A, v, acc);
 }
 
 // ---- deeper levels: K_E = sum_s P_s^T K_child P_s, one warp per coarse
@@ -207,8 +206,7 @@ k_stencil_from_elem(int n, const C* __restrict__ Kel, AT* __restrict__ A) {
                 acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += row[j];
             }
         }
-#pragma unroll
-        for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
+        st_arow<AT, C>(A, v, acc);
     }
     }
 }
@@ -239,8 +237,7 @@ k_stencil_from_k(int n, const KT* __restrict__ k, AT* __restrict__ A) {
                 acc[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] += ke * k0;
             }
         }
-#pragma unroll
-        for (int o = 0; o < cl_aw<AT>(); ++o) St<AT>::st(A, v * cl_aw<AT>() + o, o < 27 ? acc[o] : C(0));
+        st_arow<AT, C>(A, v, acc);
     }
     }
 }

@@ -163,6 +163,47 @@ __device__ __forceinline__ void ld_arow<__nv_bfloat16>(const __nv_bfloat16* __re
     }
 }
 
+// store the 27 couplings of node v (padding zeroed) as 16-byte vectors: an
+// element-wise store of a row would make every store of a warp touch as many
+// sectors as it has lanes; each element is rounded to S exactly as St<S>::st
+// rounds it
+template <class S, class C>
+__device__ __forceinline__ void st_arow(S* __restrict__ A, size_t v, const C (&a)[27]);
+template <>
+__device__ __forceinline__ void st_arow<float, float>(float* __restrict__ A, size_t v, const float (&a)[27]) {
+    float4* p = reinterpret_cast<float4*>(A + v * 28);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const int e = 4 * q;
+        p[q] = make_float4(a[e], a[e + 1], a[e + 2], e + 3 < 27 ? a[e + 3] : 0.0f);
+    }
+}
+template <>
+__device__ __forceinline__ void st_arow<double, double>(double* __restrict__ A, size_t v, const double (&a)[27]) {
+    double2* p = reinterpret_cast<double2*>(A + v * 28);
+#pragma unroll
+    for (int q = 0; q < 14; ++q) {
+        const int e = 2 * q;
+        p[q] = make_double2(e < 27 ? a[e] : 0.0, e + 1 < 27 ? a[e + 1] : 0.0);
+    }
+}
+template <>
+__device__ __forceinline__ void st_arow<__nv_bfloat16, float>(__nv_bfloat16* __restrict__ A, size_t v,
+                                                              const float (&a)[27]) {
+    uint4* p = reinterpret_cast<uint4*>(A + v * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        unsigned u[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int e = 8 * q + 2 * h;
+            const __nv_bfloat162 b2 = __floats2bfloat162_rn(e < 27 ? a[e] : 0.0f, e + 1 < 27 ? a[e + 1] : 0.0f);
+            u[h] = *reinterpret_cast<const unsigned*>(&b2);
+        }
+        p[q] = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+}
+
 // the three load cases at node v of a [N][4] field
 template <class S>
 __device__ __forceinline__ void ld_f3(const S* __restrict__ T, size_t v, typename St<S>::C (&t)[3]);
