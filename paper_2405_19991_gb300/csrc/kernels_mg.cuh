@@ -394,52 +394,21 @@ __device__ __forceinline__ void gs_stencil_node(int n, size_t N, int x, int y, i
     }
 }
 
-// The second half of gs_stencil_node: with the node's stencil row a[] and
-// right-hand side s[] already loaded, read the neighbours, relax, store.
-template <bool ZERO, class TT>
-__device__ __forceinline__ void gs_stencil_finish(int n, int x, int y, int z, size_t v, const typename St<TT>::C (&a)[27],
-                                                  typename St<TT>::C (&s)[3], TT* __restrict__ T) {
-    using C = typename St<TT>::C;
-    int xs[3], ys[3], zs[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        xs[d] = wrapd(x, d - 1, n);
-        ys[d] = wrapd(y, d - 1, n) * n;
-        zs[d] = wrapd(z, d - 1, n) * n * n;
-    }
-    const C inv = C(1) / a[13];
-    if (!ZERO) {
-#pragma unroll
-        for (int o = 0; o < 27; ++o) {
-            if (o == 13) continue;
-            C t[3];
-            ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) s[i] -= a[o] * t[i];
-        }
-    }
-    st_f3<TT>(T, v, s[0] * inv, s[1] * inv, s[2] * inv);
-    if (ZERO) {
-#pragma unroll
-        for (int q = 1; q < 8; ++q) {
-            const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
-            st_f3<TT>(T, w, C(0), C(0), C(0));
-        }
-    }
-}
-
 // A colour pass that loads its first node's stencil row -- and, with
-// early_f, its right-hand side -- before waiting on the previous kernel:
-// the V-cycle writes both two or more kernels earlier (the stencils in the
-// hierarchy setup, f by the restriction before the level's first pass, which
-// is the one launch that passes early_f = 0), while the field it reads is the
-// previous pass's output.  The L2 round trip of those loads then overlaps the
-// previous kernel's tail.  The per-node arithmetic is gs_stencil_node's (the
-// same bits); nodes past a thread's first, which the solver's launch shapes
-// do not produce, take gs_stencil_node itself.
+// early_f, its right-hand side, and the neighbours that tmask marks (bit o
+// for coupling o) -- before waiting on the previous kernel.  The V-cycle
+// writes the stencils at setup and f with the restriction before the
+// level's first pass (the one launch that passes early_f = 0); a neighbour
+// may be read early unless the previous kernel wrote it: the previous colour
+// pass writes only its own colour, the zero-start pass and the prolongation
+// write every node (tmask = 0).  The L2 round trips of those loads then
+// overlap the previous kernel's tail.  The per-node arithmetic is
+// gs_stencil_node's (the same bits); nodes past a thread's first, which the
+// solver's launch shapes do not produce, take gs_stencil_node itself.
 template <bool ZERO, class AT, class FT, class TT>
 __global__ void __launch_bounds__(256)
-k_gs_stencil_pf(int n, int colour, const AT* __restrict__ A, const FT* __restrict__ f, TT* __restrict__ T, int early_f) {
+k_gs_stencil_pf(int n, int colour, const AT* __restrict__ A, const FT* __restrict__ f, TT* __restrict__ T, int early_f,
+                unsigned tmask) {
     using C = typename St<TT>::C;
     const size_t N = (size_t)n * n * n;
     const int h = n >> 1;
@@ -448,15 +417,47 @@ k_gs_stencil_pf(int n, int colour, const AT* __restrict__ A, const FT* __restric
     const bool first = row0 < h * h && xi0 < h;
     const int x = 2 * xi0 + xo, y = 2 * (row0 % h) + yo, z = 2 * (row0 / h) + zo;
     const size_t v = (size_t)x + (size_t)n * (y + (size_t)n * z);
-    C a[27], s[3];
+    int xs[3], ys[3], zs[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d] = wrapd(x, d - 1, n);
+        ys[d] = wrapd(y, d - 1, n) * n;
+        zs[d] = wrapd(z, d - 1, n) * n * n;
+    }
+    C a[27], s[3], t[27][3];
     if (first) {
         ld_arow<AT>(A, v, a);
         if (early_f) ld_f3<FT>(f, v, s);
+        if (!ZERO) {
+#pragma unroll
+            for (int o = 0; o < 27; ++o)
+                if (o != 13 && ((tmask >> o) & 1u)) ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t[o]);
+        }
     }
     pdl_enter();
     if (first && node_ok(x, y, z, n, kSiteCoarse) && OTM_BOUND(v, N, kSiteCoarse)) {
         if (!early_f) ld_f3<FT>(f, v, s);
-        gs_stencil_finish<ZERO, TT>(n, x, y, z, v, a, s, T);
+        const C inv = C(1) / a[13];
+        if (!ZERO) {
+#pragma unroll
+            for (int o = 0; o < 27; ++o)
+                if (o != 13 && !((tmask >> o) & 1u)) ld_f3<TT>(T, (size_t)(xs[o % 3] + ys[(o / 3) % 3] + zs[o / 9]), t[o]);
+            // per load case the same accumulation order as a scalar sweep over o
+#pragma unroll
+            for (int o = 0; o < 27; ++o) {
+                if (o == 13) continue;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) s[i] -= a[o] * t[o][i];
+            }
+        }
+        st_f3<TT>(T, v, s[0] * inv, s[1] * inv, s[2] * inv);
+        if (ZERO) {
+#pragma unroll
+            for (int q = 1; q < 8; ++q) {
+                const size_t w = (size_t)(x + (q & 1)) + (size_t)n * ((y + ((q >> 1) & 1)) + (size_t)n * (z + (q >> 2)));
+                st_f3<TT>(T, w, C(0), C(0), C(0));
+            }
+        }
     }
     OTM_FOR_ROWS(row_, h * h) {
         const int yy = 2 * (row_ % h) + yo, zz = 2 * (row_ / h) + zo;
@@ -465,6 +466,21 @@ k_gs_stencil_pf(int n, int colour, const AT* __restrict__ A, const FT* __restric
             gs_stencil_node<ZERO, AT, FT, TT>(n, N, 2 * xi + xo, yy, zz, A, f, T);
         }
     }
+}
+
+// Couplings o of a colour-c node whose neighbour the pass of colour prev
+// writes (odd offsets flip a coordinate's parity); the complement may be read
+// before the wait on that pass.  prev < 0: the previous kernel wrote every
+// node.
+inline unsigned gs_early_mask(int c, int prev) {
+    if (prev < 0) return 0u;
+    unsigned m = 0u;
+    for (int o = 0; o < 27; ++o) {
+        const int dx = o % 3 - 1, dy = (o / 3) % 3 - 1, dz = o / 9 - 1;
+        const int nc = c ^ ((dx & 1) | ((dy & 1) << 1) | ((dz & 1) << 2));
+        if (o != 13 && nc != prev) m |= 1u << o;
+    }
+    return m;
 }
 
 template <bool ZERO, class AT, class FT, class TT>
