@@ -3,7 +3,8 @@ mechanism fires on an out-of-range index and only then, and a workload
 through the checked kernels -- the TMA stencil and group pass at every
 staged size, the gather forms, every V-cycle level shape, MMA, the tcgen05
 convolution and the network -- records no bad index and gives the same
-bits as the normal build.  Nothing here makes an out-of-range access: the
+bits as the normal build (the network after a training step, whose weight
+gradient sums with float atomics, to rounding).  Nothing here makes an out-of-range access: the
 self-test evaluates an index with no memory access behind it."""
 import os
 import subprocess
@@ -119,5 +120,13 @@ def test_checked_workload_records_nothing_and_matches_the_normal_build(check_lib
     assert "DONE" in _run(_WORK, "normal", b)
     A, B = np.load(a), np.load(b)
     assert sorted(A.files) == sorted(B.files)
-    for key in A.files:
-        assert np.array_equal(A[key].view(np.uint32), B[key].view(np.uint32)), key
+    # the training step's weight gradient adds per-CTA partials with float
+    # atomics, so its result is not reproducible to the bit from run to run
+    # in either build: that one output is compared to rounding
+    nondet = {"net2"}
+    diff = {key: float(np.max(np.abs(A[key].astype(np.float64) - B[key].astype(np.float64))))
+            for key in A.files if key not in nondet and not np.array_equal(A[key].view(np.uint32), B[key].view(np.uint32))}
+    assert not diff, diff
+    for key in nondet:
+        ref = np.max(np.abs(B[key]))
+        assert np.max(np.abs(A[key].astype(np.float64) - B[key].astype(np.float64))) <= 1e-5 * ref, key
