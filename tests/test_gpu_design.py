@@ -447,3 +447,35 @@ def test_mma_checkpoint_resume_is_bitwise():
         assert np.array_equal(_rho(c, otm, n), ref)
     finally:
         otm.otm_destroy(c)
+
+
+@pytest.mark.parametrize("n,precision", [(64, 1), (64, 2), (128, 1)])
+def test_launch_forms_give_the_same_trajectory(n, precision, tmp_path):
+    """The forms that change only where data lives or when it is loaded --
+    the cluster-wide level in global memory or in the CTAs' shared memory
+    (OTM_CLUSTER_DSM), every load after the dependent-launch wait or the old
+    ones before it (OTM_PDL_EARLY), the coarse passes' neighbours read before
+    the wait or after it (OTM_COARSE_NBR), and a fixed group-pass ring depth
+    against the tuned one -- give the same density, chi and PCG iteration
+    counts to the bit over three design iterations."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    forms = {"default": {}, "global_level": {"OTM_CLUSTER_DSM": "0"}, "late_loads": {"OTM_PDL_EARLY": "0"},
+             "late_neighbours": {"OTM_COARSE_NBR": "0"}, "ring4": {"OTM_GS_STAGES": "4"}}
+    res = {}
+    for name, env in forms.items():
+        path = str(tmp_path / f"{name}.npz")
+        r = subprocess.run([sys.executable, "-c", _GS_TRAJ, root, str(n), str(precision), path],
+                           env=dict(os.environ, **env), capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stdout + r.stderr
+        assert json.loads(r.stdout.split("CFG")[1].strip().splitlines()[0])["st"] == 0
+        res[name] = np.load(path)
+    a = res["default"]
+    for name in forms:
+        b = res[name]
+        assert np.array_equal(a["iters"], b["iters"]), name
+        assert np.array_equal(a["rho"].view(np.uint32), b["rho"].view(np.uint32)), name
+        assert np.array_equal(a["chi"].view(np.uint32), b["chi"].view(np.uint32)), name
