@@ -241,6 +241,12 @@ OTM_API otm_status otm_get_density(otm_ctx* ctx, float* rho, int on_device);
  *                   choice, among 4, 5 and 6 (OTM_GS_STAGES fixes it)
  *   gs_tune_us      measured time of one V-cycle at depths 4, 5, 6; 0 when
  *                   not measured
+ *   head_form       initial residual of a solve's first pass: 0 the
+ *                   TMA-staged stencil's residual form on the iterate's
+ *                   high part (its low part cleared first), 1 the pair form
+ *                   f - K (hi + lo) (OTM_HEAD=pair; FP64 and sizes the staged
+ *                   form does not cover); refinement passes always use the
+ *                   pair form
  * Errors: OTM_EINVAL for NULL arguments; CUDA errors as OTM_ECUDA. */
 typedef struct {
     int stencil_form;
@@ -255,7 +261,7 @@ typedef struct {
     int gs_form;
     int gs_chunks;
     int gs_stages;
-    int reserved_cfg;
+    int head_form;
     double gs_tune_us[3];
 } otm_config;
 OTM_API otm_status otm_get_config(otm_ctx* ctx, otm_config* out);

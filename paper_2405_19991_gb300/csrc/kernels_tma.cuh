@@ -151,7 +151,8 @@ __host__ __device__ inline int tma_stage_bytes(int mode, int n, int ty, int st_s
 }
 
 // MODE 0: out_i = K(k) u_i (with DOT: reduces u_i . out_i, i = 0..2).
-// MODE 1: out_i = f_i - K(k) u_i (no reduction).
+// MODE 1: out_i = f_i - K(k) u_i (with DOT: reduces out_i . out_i and
+// f_i . f_i, i = 0..2, in that order).
 // ST: storage of k and u (FP32 or BF16); FT: f; OT: out.  Grid: (n / TY)
 // row blocks (fastest) x m z-chunks; block: (n / 2) TY threads.
 // Rows per CTA for n known at compile time (the rule of tma_rows below).
@@ -247,7 +248,10 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
     }
     __syncthreads();
 
-    Acc2 acc[3];   // the consumers' p . Kp partial sums (zero in the producer warp)
+    // the consumers' partial sums (zero in the producer warp): MODE 0 p . Kp
+    // of the pair's two nodes on the two lanes; MODE 1 r . r on the low lane
+    // and f . f on the high lane, the pair's nodes one after the other
+    Acc2 acc[3];
     int issued = 0;
     if (tid >= ncons) {
         // Producer: stage i goes into slot i mod S once every consumer warp is
@@ -401,8 +405,13 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
                     const FT* F = reinterpret_cast<const FT*>(st + uBytes + kBytes) + sf + c * TY * n;
                     const float fx = ld_one(F, xa), fy = ld_one(F, xb);
                     const float kx = pk_lo(nd) * (-1.0f / 12.0f), ky = pk_hi(nd) * (-1.0f / 12.0f);
-                    St<OT>::st(o_c, oa, fx - kx);
-                    St<OT>::st(o_c, ob, fy - ky);
+                    const float rx = fx - kx, ry = fy - ky;
+                    St<OT>::st(o_c, oa, rx);
+                    St<OT>::st(o_c, ob, ry);
+                    if constexpr (DOT) {
+                        acc[c].add_prod(pk(rx, fx), pk(rx, fx));
+                        acc[c].add_prod(pk(ry, fy), pk(ry, fy));
+                    }
                 }
             }
             if (START) {
@@ -464,12 +473,25 @@ k_stencil_tma(const __grid_constant__ TmaStencilMaps mp, int n_rt, int ty_rt, in
     if (tid == ncons && *(volatile int*)&bail_s)
         for (int i = issued > S ? issued - S : 0; i < issued; ++i)
             (void)mbar_wait_bounded(&full[i % S], (uint32_t)((i / S) & 1));
-    if (DOT) {
+    if constexpr (DOT && MODE == 0) {
         __shared__ double res[3];
         Acc<float> sums[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) sums[c] = acc[c].merged();
         if (grid_reduce<3>(sums, rb, res)) {
+            if (is_thread0()) fin(res);
+        }
+    } else if constexpr (DOT) {
+        __shared__ double res[6];
+        Acc<float> sums[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            sums[c].s = pk_lo(acc[c].s);
+            sums[c].c = pk_lo(acc[c].c);
+            sums[3 + c].s = pk_hi(acc[c].s);
+            sums[3 + c].c = pk_hi(acc[c].c);
+        }
+        if (grid_reduce<6>(sums, rb, res)) {
             if (is_thread0()) fin(res);
         }
     }

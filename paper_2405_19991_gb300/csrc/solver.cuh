@@ -330,8 +330,8 @@ class Solver : public SolverBase {
     // TMA-staged fine stencil (FP32 PCG fields, 32 | n or 64 | n for BF16
     // storage): the PCG product q = K p with p . q, and the V-cycle's
     // residual f - K T; grid 0 when the form is not used
-    TmaLaunch tma_pcg_, tma_vc_;
-    TmaStencilMaps maps_pcg_, maps_vc_;
+    TmaLaunch tma_pcg_, tma_vc_, tma_head_;
+    TmaStencilMaps maps_pcg_, maps_vc_, maps_head_;
     void launch_tma_pcg(const RedBuf& rb) {
         if constexpr (std::is_same<R, float>::value)
             launch_pdl_smem(tma_kernel<0, true, float, float, float, FinAlpha>(n), tma_pcg_.grid, tma_pcg_.threads,
@@ -342,6 +342,22 @@ class Solver : public SolverBase {
         if constexpr (std::is_same<R, float>::value && !std::is_same<S, double>::value)
             launch_pdl_smem(tma_kernel<1, false, S, float, S, FinNone>(n), tma_vc_.grid, tma_vc_.threads, tma_vc_.smem,
                             stream, maps_vc_, n, tma_vc_.ty, tma_vc_.m, tma_vc_.stages, res0, &ps->dev_err, rbuf(), FinNone{}, pdl_early());
+    }
+    // First pass of a solve (FP32 PCG fields): the iterate starts from its
+    // high part alone (lo cleared), so the initial residual f - K hi is the
+    // stencil's residual form with the ||r||^2 and ||f||^2 reductions; a
+    // refinement pass keeps the pair form (lo then carries the solve's
+    // accumulated updates).
+    bool head_tma(int use_true) const { return !use_true && tma_head_.grid > 0; }
+    otm_status clear_lo() {
+        if (xl) OTM_CU(cudaMemsetAsync(xl, 0, 3 * N * sizeof(R), stream));
+        return OTM_OK;
+    }
+    void launch_tma_head() {
+        if constexpr (std::is_same<R, float>::value)
+            launch_pdl_smem(tma_kernel<1, true, float, float, float, FinInit>(n), tma_head_.grid, tma_head_.threads,
+                            tma_head_.smem, stream, maps_head_, n, tma_head_.ty, tma_head_.m, tma_head_.stages,
+                            (float*)r, &ps->dev_err, rbuf(), FinInit{ps, 0}, pdl_early());
     }
     size_t inv_smem_ = 0;    // dynamic shared memory of the coarsest inverse
     int inv_use_smem_ = 0;   // its working matrix in shared memory
@@ -499,6 +515,13 @@ class Solver : public SolverBase {
                 if (tma_launch_shape<1, false, S, float, S, FinNone>(tma_vc_, n, sm_count, max_blocks) &&
                     !tma_make_maps<S, float>(maps_vc_, n, k_vc, z, r))
                     tma_vc_.grid = 0;
+                // OTM_HEAD=pair: the pair form for every pass (for comparisons)
+                const char* he = getenv("OTM_HEAD");
+                const bool pair_head = he && he[0] == 'p';
+                if (xl && !pair_head &&
+                    tma_launch_shape<1, true, float, float, float, FinInit>(tma_head_, n, sm_count, max_blocks) &&
+                    !tma_make_maps<float, float>(maps_head_, n, kf, x, f))
+                    tma_head_.grid = 0;
                 cudaGetLastError();   // a refused shape leaves the older forms in place
             }
             if (gs_choice() == 0) {
@@ -1068,9 +1091,12 @@ if (tma_pcg_.grid > 0)
         OTM_LAUNCH();
         return OTM_OK;
     }
-    otm_status enqueue_pass_head(int use_true) {
+    otm_status enqueue_pass_head(int use_true, bool lo_cleared = false) {
         ++nl_;
-        if (wr_)
+        if (head_tma(use_true)) {
+            if (!lo_cleared) OTM_TRY(clear_lo());
+            launch_tma_head();
+        } else if (wr_)
             launch_pdl(k_residual_x2_wr<FinInit>, wr_grid((long long)n * n * (n / 128)), 256, stream, n,
                        (const float*)kf, (const float*)x, (const float*)xl, (const float*)f, (float*)r, rbuf(),
                        FinInit{ps, use_true});
@@ -1170,7 +1196,7 @@ if (tma_pcg_.grid > 0)
         // side branch of the graph, beside the macro loads and the pass's
         // initial residual; the branches join before the PCG loop, whose
         // first V-cycle is the first reader of the coarse levels.
-        bool forked = false;
+        bool forked = false, lo_cleared = false;
         if (with_setup) {
             st = filter_simp();
             if (st == OTM_OK && nlev > 1) {
@@ -1180,6 +1206,12 @@ if (tma_pcg_.grid > 0)
                     forked = true;
                     stream = side;
                     st = coarse_hierarchy();
+                    // the first pass's lo is cleared on this branch too: no
+                    // kernel before the PCG loop reads it
+                    if (st == OTM_OK && head_tma(use_true)) {
+                        st = clear_lo();
+                        lo_cleared = true;
+                    }
                     stream = main;
                     if (st == OTM_OK) e = cudaEventRecord(ev_join, side);
                 }
@@ -1197,7 +1229,7 @@ if (tma_pcg_.grid > 0)
                 st = OTM_ECUDA;
             }
         }
-        if (st == OTM_OK) st = enqueue_pass_head(use_true);
+        if (st == OTM_OK) st = enqueue_pass_head(use_true, lo_cleared);
         if (st == OTM_OK && forked) {
             e = cudaStreamWaitEvent(main, ev_join, 0);
             if (e != cudaSuccess) {
@@ -1476,6 +1508,7 @@ if (tma_pcg_.grid > 0)
         out->gs_chunks = tma_gs_.grid > 0 ? tma_gs_.m : 0;
         out->gs_stages = tma_gs_.grid > 0 ? tma_gs_.stages : 0;
         for (int d = 0; d < 3; ++d) out->gs_tune_us[d] = gs_tune_us_[d];
+        out->head_form = tma_head_.grid > 0 ? 0 : 1;
         return OTM_OK;
     }
 

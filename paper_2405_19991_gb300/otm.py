@@ -71,7 +71,7 @@ class otm_config(C.Structure):
         ("gs_form", C.c_int),
         ("gs_chunks", C.c_int),
         ("gs_stages", C.c_int),
-        ("reserved_cfg", C.c_int),
+        ("head_form", C.c_int),
         ("gs_tune_us", C.c_double * 3),
     ]
 
