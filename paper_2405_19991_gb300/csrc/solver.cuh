@@ -850,10 +850,34 @@ class Solver : public SolverBase {
     // previous kernel (the stencil always is); prev: the colour the previous
     // kernel relaxed (-1: it wrote every node), whose neighbours are the only
     // ones read after the wait
+    // The prefetching form of a colour pass holds a node's 27 couplings and
+    // up to 26 neighbours in registers (about 200 per thread), so it runs
+    // where its grid fits in one wave of resident blocks; a larger level
+    // (the 128^3 level at n = 256: 1024 blocks of 256 threads, one resident
+    // per SM) takes the plain form, whose lower register count keeps more
+    // blocks resident.  OTM_CGS_PF=1 takes the prefetching form everywhere
+    // (for comparisons).  Decided once per level.
+    signed char cgs_pf_[kMaxLevels] = {};   // 0 unknown, 1 prefetching, -1 plain
+    bool cgs_prefetch(int l, const RowLaunch& cfg) {
+        if (cgs_pf_[l] == 0) {
+            const char* e = getenv("OTM_CGS_PF");
+            bool pf = e && e[0] == '1';
+            if (!pf) {
+                int per_sm = 0;
+                const int thr = cfg.block.x * cfg.block.y * cfg.block.z;
+                pf = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gs_stencil_pf<false, S, S, S>, thr, 0) ==
+                         cudaSuccess &&
+                     per_sm > 0 && (long long)cfg.grid <= (long long)per_sm * sm_count;
+                cudaGetLastError();
+            }
+            cgs_pf_[l] = pf ? 1 : -1;
+        }
+        return cgs_pf_[l] > 0;
+    }
     template <bool ZERO>
     void coarse_gs_pass(int l, int c, int early_f, int prev) {
         const auto cfg = rl(sz[l] / 2, (sz[l] / 2) * (sz[l] / 2), cgs_thr(sz[l]));
-        if (pdl_early())
+        if (pdl_early() && (ZERO || cgs_prefetch(l, cfg)))
             launch_pdl(k_gs_stencil_pf<ZERO, S, S, S>, OTM_ROWS_CFG(cfg), stream, sz[l], c, Al[l], Fl[l], Tl[l],
                        early_f, coarse_nbr_early() ? gs_early_mask(c, prev) : 0u);
         // (BF16 storage: measured slower with the neighbours read early, 2.160
