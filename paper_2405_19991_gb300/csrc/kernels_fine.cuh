@@ -202,9 +202,91 @@ __device__ __forceinline__ C nd_sum2(const C* __restrict__ hi, const C* __restri
     return acc;
 }
 
-// Error-free version for the convergence check: every one of the 32 element
-// terms k_e (u_w - u_v) is formed with TwoProduct and summed with TwoSum,
-// so the result is nd(u) of the stored k and u up to O(eps^2).
+// Convergence check, element form: nd(u) = sum over the node's eight
+// elements e of k_e d_e, with d_e = (u_a + u_b + u_c + u_d) - 4 u_v over the
+// four corners of e that v couples to (the three face diagonals and the body
+// diagonal; the edge neighbours carry K^0 = 0).  Each u = hi + lo.  d_e is
+// held unrounded as t + sg: the four high parts are summed with TwoSum and
+// 4 hv subtracted with TwoSum (4 hv is exact), the TwoSum errors and the low
+// parts going into sg.  k_e d_e = TwoProduct(k_e, t) + k_e sg, summed with
+// TwoSum into (s, c).  The result is nd of the stored k and hi + lo with an
+// error of order eps^2 of the terms (the pair form below rounds each of the
+// 20 differences once: order eps).  The corners of element (a, b, cz) are
+// taken in the order (xc, Y[b], Z[cz]), (X[a], Y[b], Z[cz]), (X[a], Y[b],
+// zc), (X[a], yc, Z[cz]), the elements with a fastest, then b, then cz.
+template <class C>
+__device__ __forceinline__ void elem_add(C& t, C& sg, C h, C l) {
+    C u, e;
+    two_sum(t, h, u, e);
+    t = u;
+    sg = sg + (e + l);
+}
+// t - 4 hv with the error and - 4 lv into sg (two_sum(t, -h4), written with
+// subtractions as in df_diff)
+template <class C>
+__device__ __forceinline__ void elem_sub4(C& t, C& sg, C h4, C l4) {
+    const C u = t - h4;
+    const C bp = u - t;
+    const C e = (t - (u - bp)) - (h4 + bp);
+    t = u;
+    sg = sg + (e - l4);
+}
+template <class C>
+__device__ __forceinline__ void elem_term(C& s, C& c, C kv, C t, C sg) {
+    const C p = mul_rn(kv, t);
+    const C pe = fma(kv, sg, fma(kv, t, -p));
+    C u, e;
+    two_sum(s, p, u, e);
+    s = u;
+    c = c + (e + pe);
+}
+template <class C>
+__device__ __forceinline__ void nd_sum_elem(const C* __restrict__ hi, const C* __restrict__ lo, const Nbr& g,
+                                            const C (&kk)[2][2][2], size_t v, C& s_out, C& c_out) {
+    const C h4 = C(4) * hi[v], l4 = lo ? C(4) * lo[v] : C(0);
+    C s = 0, c = 0;
+    auto H = [&](size_t w) -> C { return hi[w]; };
+    auto L = [&](size_t w) -> C { return lo ? lo[w] : C(0); };
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const size_t w0 = (size_t)(g.xc + g.Y[b] + g.Z[cz]);
+                C t = H(w0), sg = L(w0);
+                const size_t w1 = (size_t)(g.X[a] + g.Y[b] + g.Z[cz]);
+                elem_add(t, sg, H(w1), L(w1));
+                const size_t w2 = (size_t)(g.X[a] + g.Y[b] + g.zc);
+                elem_add(t, sg, H(w2), L(w2));
+                const size_t w3 = (size_t)(g.X[a] + g.yc + g.Z[cz]);
+                elem_add(t, sg, H(w3), L(w3));
+                elem_sub4(t, sg, h4, l4);
+                elem_term(s, c, kk[cz][b][a], t, sg);
+            }
+    s_out = s;
+    c_out = c;
+}
+
+// r = f + (s + c) / 12 for the check: 1/12 as the double-float th + tl (th
+// the rounded 1/12, tl its remainder), so the scaling is the exact
+// operator's (the rounded 1/12 alone is 3e-8 high in FP32, comparable with
+// a converged residual); TwoSum of f and s th, the product's error, s tl and
+// c th in the small part, one rounding of the final sum.
+template <class C>
+__device__ __forceinline__ C resid_exact12(C fv, C s, C c) {
+    constexpr C th = C(1.0 / 12.0);
+    constexpr C tl = C(1.0 / 12.0 - (double)C(1.0 / 12.0));
+    const C s12 = mul_rn(s, th);
+    C t, e;
+    two_sum(fv, s12, t, e);
+    return t + (e + (fma(s, th, -s12) + fma(s, tl, c * th)));
+}
+
+// Pair form of the check (the warp-row kernel's OTM_CHECK_FORM=pair, for
+// comparisons): every one of the 32 element terms k_e (u_w - u_v) with the
+// difference rounded once (df_diff), formed with TwoProduct and summed with
+// TwoSum.
 template <class C>
 __device__ __forceinline__ void nd_sum_exact(const C* __restrict__ hi, const C* __restrict__ lo, const Nbr& g,
                                              const C (&kk)[2][2][2], size_t v, C& s_out, C& c_out) {
@@ -443,7 +525,8 @@ k_residual_x2(int n, const R* __restrict__ k, const R* __restrict__ xh, const R*
 }
 
 // Convergence check (k_true_residual below): ||f_i - K x_i||^2 of the
-// stored iterate with error-free element terms (no FP64 arithmetic).
+// stored iterate with error-free element terms (nd_sum_elem; no FP64
+// arithmetic on the FP32 paths).
 
 // True residual norms at solver exit.
 struct FinTrue {
@@ -475,13 +558,10 @@ k_true_residual(int n, const R* __restrict__ k, const R* __restrict__ xh, const 
         for (int i = 0; i < 3; ++i) {
             const size_t o = (size_t)i * N;
             C s, c;
-            nd_sum_exact<C>(xh + o, xl ? xl + o : nullptr, g, kk, v, s, c);
+            nd_sum_elem<C>(xh + o, xl ? xl + o : nullptr, g, kk, v, s, c);
             // r = f + nd / 12, nd = s + c; one rounding of the final sum
             const C fv = f[o + v];
-            C t, e;
-            const C s12 = mul_rn(s, C(1.0 / 12.0));
-            two_sum(fv, s12, t, e);
-            const C rv = t + (e + c * C(1.0 / 12.0) + fma(s, C(1.0 / 12.0), -s12));
+            const C rv = resid_exact12<C>(fv, s, c);
             acc[i].add_prod(rv, rv);
             acc[3 + i].add_prod(fv, fv);
         }

@@ -263,10 +263,35 @@ k_residual_x2_wr(int n, const float* __restrict__ k, const float* __restrict__ x
     }
 }
 
-// ||f - K (hi + lo)||^2 with error-free element terms (see k_true_residual):
-// each of the 32 terms k_e (u_w - u_v) of a node is formed with TwoProduct
-// and summed with TwoSum, two nodes per packed instruction.
-template <class Fin>
+// Packed forms of elem_add / elem_sub4 (kernels_fine.cuh): each lane runs
+// the scalar sequence, so both lanes are bitwise the scalar element form.
+__device__ __forceinline__ void elem_add2(float2& t, float2& sg, float2 h, float2 l) {
+    float2 u, e;
+    two_sum2(t, h, u, e);
+    t = u;
+    sg = __fadd2_rn(sg, __fadd2_rn(e, l));
+}
+__device__ __forceinline__ void elem_sub4_2(float2& t, float2& sg, float2 h4, float2 l4) {
+    const float2 u = f2_sub(t, h4);
+    const float2 bp = f2_sub(u, t);
+    const float2 e = f2_sub(f2_sub(t, f2_sub(u, bp)), __fadd2_rn(h4, bp));
+    t = u;
+    sg = __fadd2_rn(sg, f2_sub(e, l4));
+}
+
+// ||f - K (hi + lo)||^2 with error-free element terms (see k_true_residual).
+// ELEM (default): the element form of nd_sum_elem -- per node eight element
+// sums d_e held unrounded as t + sg and eight TwoProduct terms -- two nodes
+// per packed instruction; a quadrant (b, c) of elements reads its three
+// neighbour rows (dy, dz), (dy, 0) and (0, dz) in turn.  !ELEM: the pair
+// form (OTM_CHECK_FORM=pair): each of the 32 terms k_e (u_w - u_v) with the
+// difference rounded once, formed with TwoProduct and summed with TwoSum.
+// Measured at 128^3 against the residual of the stored iterate recomputed
+// in FP64: the element form within 1e-9 relative, the pair form 0.1-0.4 %
+// off; and faster (the design iteration 1974 -> 1951 us at 128^3, 11.47 ->
+// 11.16 ms at 256^3), with 44 bytes of spills at 80 registers against the
+// pair form's 244.
+template <class Fin, bool ELEM = true>
 __global__ void __launch_bounds__(256, OTM_WR_MINB)
 k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__ xh, const float* __restrict__ xl,
                    const float* __restrict__ f, RedBuf rb, Fin fin) {
@@ -285,8 +310,10 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
         const int xb = seg * 128 + 4 * lane;
         unsigned ro[3][3];
         row_offsets(n, y, z, ro);
+        // the pair form holds the four element rows for the whole warp row;
+        // the element form loads each quadrant's row where it needs it
         float kr[2][2][6];
-        load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
+        if constexpr (!ELEM) load_k_rows<float>(k, n, y, z, xb, lane, whole, kr);
         const size_t vb = ro[1][1] + (size_t)xb;
 #pragma unroll 1
         for (int i = 0; i < 3; ++i) {
@@ -299,6 +326,75 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
             // running sums s + c of the pair (jp, jp + 2), both lanes at once
             float2 S[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
             float2 Cc[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            if constexpr (ELEM) {
+                const float2 four = make_float2(4.f, 4.f);
+                const float2 H4[2] = {__fmul2_rn(four, ch2[0]), __fmul2_rn(four, ch2[1])};
+                const float2 L4[2] = {__fmul2_rn(four, cl2[0]), __fmul2_rn(four, cl2[1])};
+                // one quadrant per trip (not unrolled: a quadrant's rows are
+                // loaded where it needs them, which bounds the registers and
+                // the code size)
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                        const int cc = q >> 1, b = q & 1;
+                        const int dy = 1 - 2 * b, dz = 1 - 2 * cc;
+                        const unsigned nn = (unsigned)n * n;
+                        const unsigned oy = (unsigned)wrapd(y, dy, n) * n, oz = (unsigned)wrapd(z, dz, n) * nn;
+                        // T[a][jp], G[a][jp]: element (a, b, cc) of the pair jp
+                        float2 T[2][2], G[2][2];
+                        float kq[6];   // element row (y - b, z - cc)
+                        row6<float>(k, (size_t)wrapd(y, -b, n) * n + (size_t)wrapd(z, -cc, n) * nn, xb, n, lane,
+                                    whole, kq);
+                        {
+                            float vh[6], vl[6];
+                            pair_row(xh + fo, xl ? xl + fo : nullptr, oy + oz, xb, n, lane, whole, vh, vl);
+                            float2 PH[4], PL[4];
+                            pair_cols(vh, PH);
+                            pair_cols(vl, PL);
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int jp = 0; jp < 2; ++jp) {
+                                    const int dx = 1 - 2 * a;
+                                    T[a][jp] = PH[1 + jp];   // (x, y + dy, z + dz)
+                                    G[a][jp] = PL[1 + jp];
+                                    elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
+                                }
+                        }
+#pragma unroll
+                        for (int r2 = 0; r2 < 2; ++r2) {
+                            // rows (dy, 0), then (0, dz)
+                            float vh[6], vl[6];
+                            pair_row(xh + fo, xl ? xl + fo : nullptr,
+                                     r2 == 0 ? oy + (unsigned)z * nn : (unsigned)y * n + oz, xb, n, lane, whole, vh, vl);
+                            float2 PH[4], PL[4];
+                            pair_cols(vh, PH);
+                            pair_cols(vl, PL);
+#pragma unroll
+                            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                                for (int jp = 0; jp < 2; ++jp) {
+                                    const int dx = 1 - 2 * a;
+                                    elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
+                                }
+                        }
+#pragma unroll
+                        for (int a = 0; a < 2; ++a)
+#pragma unroll
+                            for (int jp = 0; jp < 2; ++jp) {
+                                elem_sub4_2(T[a][jp], G[a][jp], H4[jp], L4[jp]);
+                                // conductivity k_{cc,b,a} of nodes jp and jp + 2; TwoProduct per lane
+                                const float k0 = kq[1 + jp - a], k1 = kq[3 + jp - a];
+                                const float2 t = T[a][jp], sg = G[a][jp];
+                                const float2 p = make_float2(__fmul_rn(k0, t.x), __fmul_rn(k1, t.y));
+                                const float2 pe = make_float2(fmaf(k0, sg.x, fmaf(k0, t.x, -p.x)),
+                                                              fmaf(k1, sg.y, fmaf(k1, t.y, -p.y)));
+                                float2 u, e;
+                                two_sum2(S[jp], p, u, e);
+                                S[jp] = u;
+                                Cc[jp] = __fadd2_rn(Cc[jp], __fadd2_rn(e, pe));
+                            }
+                    }
+            } else {
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz)
 #pragma unroll
@@ -347,15 +443,13 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
                         }
                     }
                 }
+            }
             const Q4<float> fv = ld4f(f + fo, vb);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const float fvj = fv.v[j];
                 const float sj = pair_lane(S[j & 1], j), cj = pair_lane(Cc[j & 1], j);
-                const float s12 = __fmul_rn(sj, 1.0f / 12.0f);
-                float t, e;
-                two_sum(fvj, s12, t, e);
-                const float rv = t + (e + cj * (1.0f / 12.0f) + fmaf(sj, 1.0f / 12.0f, -s12));
+                const float rv = resid_exact12<float>(fvj, sj, cj);
                 acc[i].add_prod(rv, rv);
                 acc[3 + i].add_prod(fvj, fvj);
             }

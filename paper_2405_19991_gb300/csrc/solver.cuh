@@ -1130,11 +1130,24 @@ if (tma_pcg_.grid > 0)
         OTM_LAUNCH();
         return OTM_OK;
     }
+    // OTM_CHECK_FORM=pair: the warp-row check in its pair form (each
+    // neighbour difference rounded once) instead of the element form, for
+    // comparisons
+    static bool check_pair_form() {
+        static const bool pair = [] {
+            const char* e = getenv("OTM_CHECK_FORM");
+            return e && e[0] == 'p';
+        }();
+        return pair;
+    }
     otm_status enqueue_check() {
         ++nl_;
-        if (wr_)
-            launch_pdl(k_true_residual_wr<FinTrue>, wr_grid((long long)n * n * (n / 128)), 256, stream, n, (const float*)kf,
-                       (const float*)x, (const float*)xl, (const float*)f, rbuf(), FinTrue{ps});
+        if (wr_ && check_pair_form())
+            launch_pdl(k_true_residual_wr<FinTrue, false>, wr_grid((long long)n * n * (n / 128)), 256, stream, n,
+                       (const float*)kf, (const float*)x, (const float*)xl, (const float*)f, rbuf(), FinTrue{ps});
+        else if (wr_)
+            launch_pdl(k_true_residual_wr<FinTrue>, wr_grid((long long)n * n * (n / 128)), 256, stream, n,
+                       (const float*)kf, (const float*)x, (const float*)xl, (const float*)f, rbuf(), FinTrue{ps});
         else
             launch_pdl(k_true_residual<R>, OTM_ROWS_CFG(rl(n, n * n)), stream, n, kf, x, xl, f, rbuf(), FinTrue{ps});
         OTM_LAUNCH();

@@ -290,6 +290,48 @@ def test_96_sampled_residual():
         otm.otm_destroy(ctx)
 
 
+def _state_chi_pair(otm, ctx, n):
+    """The stored iterate (hi, lo) of an FP32-path context, from the tail of
+    its checkpoint blob (density, then the solution's high and low parts)."""
+    N = n ** 3
+    blob = np.frombuffer(otm.otm_get_state(ctx), dtype=np.uint8)
+    chi = blob[blob.size - 24 * N:].view(np.float32).reshape(2, 3, N)
+    return chi[0].astype(np.float64), chi[1].astype(np.float64)
+
+
+@pytest.mark.parametrize("n,precision", [(64, 1), (128, 1), (128, 2)])
+def test_convergence_check_is_the_exact_residual(n, precision):
+    """The convergence check reports ||f - K (hi + lo)|| / ||f|| of the
+    stored iterate, with the GPU's own FP32 k and f, to the accuracy of its
+    error-free element sums: recomputed here in FP64 by the oracle's
+    element-by-element operator, the two agree to 1e-6 relative (n = 64 runs
+    the row-mapped check, n = 128 the warp-row one; measured: within 1e-9).
+    A check that rounds each neighbour difference once is 0.1-0.4 % off at
+    these residuals (the warp-row pair form, OTM_CHECK_FORM=pair), and one
+    that scales by the FP32-rounded 1/12 about 1 %."""
+    otm = _otm()
+    N = n ** 3
+    p = otm.otm_params_default(n=n, precision=precision, cg_tol=1e-6, rmin=2.0, kappa_target=W.TARGET_ORTHOTROPIC)
+    ctx = otm.otm_create_ex(p)
+    try:
+        rho = W.initial_density(n, 0.3, 11).astype(np.float32)
+        kap, info, st = _homogenize_host(ctx, otm, rho)
+        assert st == otm.OTM_OK, otm.otm_last_error(ctx)
+        k = np.empty(N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_K, k.ctypes.data, N, 0)
+        f = np.empty(3 * N, np.float32)
+        otm.otm_get_field(ctx, otm.OTM_FIELD_LOAD, f.ctypes.data, 3 * N, 0)
+        hi, lo = _state_chi_pair(otm, ctx, n)
+        f = f.reshape(3, N).astype(np.float64)
+        r = f - fem.apply_operator(n, k.astype(np.float64), hi + lo)
+        for i in range(3):
+            rel = np.linalg.norm(r[i]) / np.linalg.norm(f[i])
+            assert 0 < rel <= 1e-6 * 1.0001
+            assert abs(info.resid[i] - rel) <= 1e-6 * rel, (i, info.resid[i], rel)
+    finally:
+        otm.otm_destroy(ctx)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("n", [4, 5, 6, 7])
 def test_single_level_direct_inverse_is_exact(precision, n):
