@@ -335,65 +335,65 @@ k_true_residual_wr(int n, const float* __restrict__ k, const float* __restrict__
                 // the code size)
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
-                        const int cc = q >> 1, b = q & 1;
-                        const int dy = 1 - 2 * b, dz = 1 - 2 * cc;
-                        const unsigned nn = (unsigned)n * n;
-                        const unsigned oy = (unsigned)wrapd(y, dy, n) * n, oz = (unsigned)wrapd(z, dz, n) * nn;
-                        // T[a][jp], G[a][jp]: element (a, b, cc) of the pair jp
-                        float2 T[2][2], G[2][2];
-                        float kq[6];   // element row (y - b, z - cc)
-                        row6<float>(k, (size_t)wrapd(y, -b, n) * n + (size_t)wrapd(z, -cc, n) * nn, xb, n, lane,
-                                    whole, kq);
-                        {
-                            float vh[6], vl[6];
-                            pair_row(xh + fo, xl ? xl + fo : nullptr, oy + oz, xb, n, lane, whole, vh, vl);
-                            float2 PH[4], PL[4];
-                            pair_cols(vh, PH);
-                            pair_cols(vl, PL);
-#pragma unroll
-                            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                                for (int jp = 0; jp < 2; ++jp) {
-                                    const int dx = 1 - 2 * a;
-                                    T[a][jp] = PH[1 + jp];   // (x, y + dy, z + dz)
-                                    G[a][jp] = PL[1 + jp];
-                                    elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
-                                }
-                        }
-#pragma unroll
-                        for (int r2 = 0; r2 < 2; ++r2) {
-                            // rows (dy, 0), then (0, dz)
-                            float vh[6], vl[6];
-                            pair_row(xh + fo, xl ? xl + fo : nullptr,
-                                     r2 == 0 ? oy + (unsigned)z * nn : (unsigned)y * n + oz, xb, n, lane, whole, vh, vl);
-                            float2 PH[4], PL[4];
-                            pair_cols(vh, PH);
-                            pair_cols(vl, PL);
-#pragma unroll
-                            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                                for (int jp = 0; jp < 2; ++jp) {
-                                    const int dx = 1 - 2 * a;
-                                    elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
-                                }
-                        }
+                    const int cc = q >> 1, b = q & 1;
+                    const int dy = 1 - 2 * b, dz = 1 - 2 * cc;
+                    const unsigned nn = (unsigned)n * n;
+                    const unsigned oy = (unsigned)wrapd(y, dy, n) * n, oz = (unsigned)wrapd(z, dz, n) * nn;
+                    // T[a][jp], G[a][jp]: element (a, b, cc) of the pair jp
+                    float2 T[2][2], G[2][2];
+                    float kq[6];   // element row (y - b, z - cc)
+                    row6<float>(k, (size_t)wrapd(y, -b, n) * n + (size_t)wrapd(z, -cc, n) * nn, xb, n, lane,
+                                whole, kq);
+                    {
+                        float vh[6], vl[6];
+                        pair_row(xh + fo, xl ? xl + fo : nullptr, oy + oz, xb, n, lane, whole, vh, vl);
+                        float2 PH[4], PL[4];
+                        pair_cols(vh, PH);
+                        pair_cols(vl, PL);
 #pragma unroll
                         for (int a = 0; a < 2; ++a)
 #pragma unroll
                             for (int jp = 0; jp < 2; ++jp) {
-                                elem_sub4_2(T[a][jp], G[a][jp], H4[jp], L4[jp]);
-                                // conductivity k_{cc,b,a} of nodes jp and jp + 2; TwoProduct per lane
-                                const float k0 = kq[1 + jp - a], k1 = kq[3 + jp - a];
-                                const float2 t = T[a][jp], sg = G[a][jp];
-                                const float2 p = make_float2(__fmul_rn(k0, t.x), __fmul_rn(k1, t.y));
-                                const float2 pe = make_float2(fmaf(k0, sg.x, fmaf(k0, t.x, -p.x)),
-                                                              fmaf(k1, sg.y, fmaf(k1, t.y, -p.y)));
-                                float2 u, e;
-                                two_sum2(S[jp], p, u, e);
-                                S[jp] = u;
-                                Cc[jp] = __fadd2_rn(Cc[jp], __fadd2_rn(e, pe));
+                                const int dx = 1 - 2 * a;
+                                T[a][jp] = PH[1 + jp];   // (x, y + dy, z + dz)
+                                G[a][jp] = PL[1 + jp];
+                                elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
                             }
                     }
+#pragma unroll
+                    for (int r2 = 0; r2 < 2; ++r2) {
+                        // rows (dy, 0), then (0, dz)
+                        float vh[6], vl[6];
+                        pair_row(xh + fo, xl ? xl + fo : nullptr,
+                                 r2 == 0 ? oy + (unsigned)z * nn : (unsigned)y * n + oz, xb, n, lane, whole, vh, vl);
+                        float2 PH[4], PL[4];
+                        pair_cols(vh, PH);
+                        pair_cols(vl, PL);
+#pragma unroll
+                        for (int a = 0; a < 2; ++a)
+#pragma unroll
+                            for (int jp = 0; jp < 2; ++jp) {
+                                const int dx = 1 - 2 * a;
+                                elem_add2(T[a][jp], G[a][jp], PH[1 + jp + dx], PL[1 + jp + dx]);
+                            }
+                    }
+#pragma unroll
+                    for (int a = 0; a < 2; ++a)
+#pragma unroll
+                        for (int jp = 0; jp < 2; ++jp) {
+                            elem_sub4_2(T[a][jp], G[a][jp], H4[jp], L4[jp]);
+                            // conductivity k_{cc,b,a} of nodes jp and jp + 2; TwoProduct per lane
+                            const float k0 = kq[1 + jp - a], k1 = kq[3 + jp - a];
+                            const float2 t = T[a][jp], sg = G[a][jp];
+                            const float2 p = make_float2(__fmul_rn(k0, t.x), __fmul_rn(k1, t.y));
+                            const float2 pe = make_float2(fmaf(k0, sg.x, fmaf(k0, t.x, -p.x)),
+                                                          fmaf(k1, sg.y, fmaf(k1, t.y, -p.y)));
+                            float2 u, e;
+                            two_sum2(S[jp], p, u, e);
+                            S[jp] = u;
+                            Cc[jp] = __fadd2_rn(Cc[jp], __fadd2_rn(e, pe));
+                        }
+                }
             } else {
 #pragma unroll
             for (int dz = -1; dz <= 1; ++dz)
