@@ -593,15 +593,24 @@ k_residual_stencil_pf(int n, const AT* __restrict__ A, const FT* __restrict__ f,
 // pivot block K of the current matrix W (D = W[K][K]) is
 //   W[K][K] <- D^-1,            W[K][j] <- D^-1 W[K][j],
 //   W[i][K] <- -W[i][K] D^-1,   W[i][j] <- W[i][j] - W[i][K] D^-1 W[K][j]
-// for i, j outside K -- the same as kInvB single-pivot steps, with the bulk
-// as a rank-kInvB update that each thread applies to its entries in
-// registers (warp w: rows w, w + warps, ...; lane l: columns l, l + 32, ...).
-// D^-1 itself comes from single-pivot steps by one warp.  W lives in shared
-// memory when it fits the opt-in limit, else in Wg.
-constexpr int kInvB = 8;
+// for i, j outside K -- the same as kInvB single-pivot steps.  D^-1 comes
+// from single-pivot steps by one warp; the two panel products run as
+// (4 columns or rows) x (4 panel rows or columns) units, one per thread;
+// the rank-kInvB update of the rows outside K runs as 4 x 4 register tiles
+// (the old panel column and R = D^-1 W[K][j] read as 4-wide vectors).  W has
+// a row stride of q rounded up to a multiple of 4 (zero padding), so rows
+// are 16-byte aligned and tiles cover it; it lives in shared memory when it
+// fits the opt-in limit, else in Wg.  No index needs an integer division
+// except the tile number of the update.
+constexpr int kInvB = 16;
 constexpr int kInvThreads = 512;
+// 1 / x correctly rounded (the same value as the division 1 / x)
+__device__ __forceinline__ float inv_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double inv_rcp(double x) { return __drcp_rn(x); }
+__host__ __device__ inline int inv_ld(int q) { return (q + 3) & ~3; }
 inline size_t invert_smem_bytes(int q, int elem, bool with_w) {
-    return (size_t)elem * ((size_t)kInvB * kInvB + 3 * (size_t)kInvB * q + (with_w ? (size_t)q * q : 0));
+    const size_t ld = (size_t)inv_ld(q);
+    return (size_t)elem * ((size_t)kInvB * kInvB + 2 * (size_t)kInvB * ld + (with_w ? ld * ld : 0));
 }
 template <class AT, class C>
 __global__ void __launch_bounds__(kInvThreads)
@@ -609,152 +618,175 @@ k_coarse_invert(int n, const AT* __restrict__ A, C* __restrict__ Wg, C* __restri
     pdl_enter();
     extern __shared__ __align__(16) unsigned char inv_sm[];
     constexpr int B = kInvB;
-    constexpr int kCols = 8;                   // columns per lane held in registers (q <= 256)
     const int m = n * n * n;
     const int q = m - 1;
-    const int qq = q * q;
-    C* Dp = reinterpret_cast<C*>(inv_sm);      // [B][B]: D, then D^-1
-    C* Prow = Dp + B * B;                      // [B][q]: panel rows, then D^-1 W[K][j]
-    C* Pcol = Prow + (size_t)B * q;            // [q][B]: panel columns
-    C* Cn = Pcol + (size_t)q * B;              // [q][B]: -W[i][K] D^-1
-    C* W = use_smem ? Cn + (size_t)q * B : Wg;
+    const int ld = inv_ld(q);
+    const int nq = ld >> 2;                    // 4-wide groups of columns (and of rows)
+    C* Dp = reinterpret_cast<C*>(inv_sm);      // [B][B]: D, then D^-1 (zero past the panel)
+    C* Prow = Dp + B * B;                      // [B][ld]: panel rows W[K][j], then R = D^-1 W[K][j]
+    C* PcT = Prow + (size_t)B * ld;            // [B][ld]: panel columns, transposed: PcT[c][i] = W[i][k0 + c]
+    C* W = use_smem ? PcT + (size_t)B * ld : Wg;
     const int nthr = blockDim.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
-    for (int i = tid; i < qq; i += nthr) W[i] = C(0);
-    for (int i = tid; i < B * B; i += nthr) Dp[i] = C(0);   // entries past a short last panel stay finite
+    const Q4<C> zero4 = {{C(0), C(0), C(0), C(0)}};
+    for (int i = tid; i < ld * ld; i += nthr) W[i] = C(0);
     __syncthreads();
     for (int v = 1 + tid; v < m; v += nthr) {
         const int x = v % n, y = (v / n) % n, z = v / (n * n);
         for (int o = 0; o < 27; ++o) {
             const int c = wrapd(x, o % 3 - 1, n) + n * (wrapd(y, (o / 3) % 3 - 1, n) + n * wrapd(z, o / 9 - 1, n));
             if (c == 0) continue;
-            W[(size_t)(v - 1) * q + (c - 1)] += (C)St<AT>::ld(A, (size_t)v * cl_aw<AT>() + o);
+            W[(size_t)(v - 1) * ld + (c - 1)] += (C)St<AT>::ld(A, (size_t)v * cl_aw<AT>() + o);
         }
     }
     __syncthreads();
+    const int nu = 4 * nq;   // panel-product units of each kind
     for (int k0 = 0; k0 < q; k0 += B) {
         const int b = min(B, q - k0);
         auto inK = [&](int i) { return (unsigned)(i - k0) < (unsigned)b; };
-        // 1. panel rows and columns (before this sweep), and D
-        for (int t = tid; t < b * q; t += nthr) {
-            const int c = t / q, j = t - c * q;
-            Prow[c * q + j] = W[(size_t)(k0 + c) * q + j];
-        }
-        for (int t = tid; t < q * b; t += nthr) {
-            const int i = t / b, c = t - i * b;
-            Pcol[i * B + c] = W[(size_t)i * q + k0 + c];
-        }
-        for (int t = tid; t < b * b; t += nthr) {
-            const int r = t / b, c = t - r * b;
-            Dp[r * B + c] = W[(size_t)(k0 + r) * q + k0 + c];
+        // 1. panel rows (zero past b) and panel columns, transposed (zero past b)
+        for (int c = warp; c < B; c += nw)
+            for (int jq = lane; jq < nq; jq += 32)
+                st4(Prow, (size_t)c * ld + 4 * jq, c < b ? ld4(W, (size_t)(k0 + c) * ld + 4 * jq) : zero4);
+        for (int t = tid; t < 4 * ld; t += nthr) {
+            const int i = t >> 2, cq = t & 3;
+            const Q4<C> w = 4 * cq < b ? ld4(W, (size_t)i * ld + k0 + 4 * cq) : zero4;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) PcT[(size_t)(4 * cq + e) * ld + i] = 4 * cq + e < b ? w.v[e] : C(0);
         }
         __syncthreads();
-        // D^-1 by single-pivot steps (one warp, two entries per lane)
+        // 2. D^-1 by single-pivot steps in one warp's registers: lane l holds
+        //    row l / 2, columns 8 (l % 2) .. 8 (l % 2) + 7; the pivot, the
+        //    pivot row and the pivot column come by shuffles, read before any
+        //    lane updates its entries (the q pivots of the inverse form its
+        //    serial chain, so no step goes through shared memory)
         if (warp == 0) {
-            for (int p = 0; p < b; ++p) {
-                const C ip = C(1) / Dp[p * B + p];
-                C nv[2];
+            const int r = lane >> 1, c0 = 8 * (lane & 1);
+            C d[8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int e = lane + 32 * h, r = e / B, c = e % B;
-                    nv[h] = C(0);
+            for (int k = 0; k < 8; ++k) d[k] = (r < b && c0 + k < b) ? PcT[(size_t)(c0 + k) * ld + k0 + r] : C(0);
+#pragma unroll
+            for (int p = 0; p < B; ++p) {
+                if (p >= b) break;
+                const C ip = inv_rcp(__shfl_sync(0xffffffffu, d[p & 7], 2 * p + (p >> 3)));
+                const C colp = __shfl_sync(0xffffffffu, d[p & 7], 2 * r + (p >> 3));
+                C rowp[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) rowp[k] = __shfl_sync(0xffffffffu, d[k], 2 * p + (lane & 1));
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int c = c0 + k;
                     if (r < b && c < b) {
-                        const C w = Dp[r * B + c];
                         if (r == p) {
-                            nv[h] = (c == p ? C(1) : w) * ip;
+                            d[k] = (c == p ? C(1) : d[k]) * ip;
                         } else {
-                            const C wk = (c == p ? C(1) : Dp[p * B + c]) * ip;
-                            nv[h] = (c == p ? C(0) : w) - Dp[r * B + p] * wk;
+                            const C wk = (c == p ? C(1) : rowp[k]) * ip;
+                            d[k] = (c == p ? C(0) : d[k]) - colp * wk;
                         }
                     }
                 }
-                __syncwarp();
+            }
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int e = lane + 32 * h, r = e / B, c = e % B;
-                    if (r < b && c < b) Dp[r * B + c] = nv[h];
+            for (int k = 0; k < 8; ++k) Dp[r * B + c0 + k] = d[k];
+        }
+        __syncthreads();
+        // 3. R = D^-1 W[K][j] into Prow (zero in the columns of K) and
+        //    Cn = -W[i][K] D^-1 into W[i][K] for the rows outside K.  A unit
+        //    of R reads all of its four columns of Prow before any unit of
+        //    the round writes them; the units of one column group share a
+        //    round (nthr is a multiple of 4).
+        for (int base = 0; base < 2 * nu; base += nthr) {
+            const int u = base + tid;
+            const bool isR = u < nu, isC = !isR && u < 2 * nu;
+            const int g = isR ? u >> 2 : (u - nu) >> 2, cg = u & 3;
+            Q4<C> xs[B];
+            if (isR) {
+#pragma unroll
+                for (int d = 0; d < B; ++d) xs[d] = ld4(Prow, (size_t)d * ld + 4 * g);
+            } else if (isC) {
+#pragma unroll
+                for (int d = 0; d < B; ++d) xs[d] = ld4(PcT, (size_t)d * ld + 4 * g);
+            }
+            __syncthreads();
+            if (isR && 4 * cg < b) {
+                // R[c][4g + f] = sum_d D^-1[c][d] Prow[d][4g + f], c = 4cg .. 4cg + 3
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = 4 * cg + cc;
+                    if (c >= b) break;
+                    Q4<C> r = zero4;
+#pragma unroll
+                    for (int d = 0; d < B; ++d) {
+                        const C dv = Dp[c * B + d];
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) r.v[f] += dv * xs[d].v[f];
+                    }
+#pragma unroll
+                    for (int f = 0; f < 4; ++f)
+                        if (inK(4 * g + f)) r.v[f] = C(0);
+                    st4(Prow, (size_t)c * ld + 4 * g, r);
                 }
-                __syncwarp();
+            } else if (isC && 4 * cg < b && 4 * g < q && !inK(4 * g)) {
+                // Cn[4g + e][c] = -sum_d PcT[d][4g + e] D^-1[d][c], c = 4cg .. 4cg + 3
+                Q4<C> cn[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cn[e] = zero4;
+#pragma unroll
+                for (int d = 0; d < B; ++d) {
+                    const Q4<C> dr = ld4(Dp, (size_t)d * B + 4 * cg);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+#pragma unroll
+                        for (int cc = 0; cc < 4; ++cc) cn[e].v[cc] += xs[d].v[e] * dr.v[cc];
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int i = 4 * g + e;
+                    if (i >= q) break;
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        if (4 * cg + cc < b) W[(size_t)i * ld + k0 + 4 * cg + cc] = -cn[e].v[cc];
+                }
             }
         }
         __syncthreads();
-        // 2. R = D^-1 W[K][j] (in place, zero inside K) and Cn = -W[i][K] D^-1
-        for (int j = tid; j < q; j += nthr) {
-            C xr[B];
+        // 4. rank-b update of the rows outside K in 4 x 4 tiles (the columns
+        //    of K see R = 0 and keep Cn), and 5. the panel rows: W[K][j] = R
+        //    outside K, D^-1 inside (rows disjoint from the tiles')
+        for (int t = tid; t < nq * nq; t += nthr) {
+            const int iq = t / nq, jq = t - iq * nq;
+            if (4 * iq >= q || inK(4 * iq)) continue;
+            Q4<C> acc[4];
 #pragma unroll
-            for (int d = 0; d < B; ++d) xr[d] = d < b ? Prow[d * q + j] : C(0);
-            const bool k_col = inK(j);
+            for (int e = 0; e < 4; ++e) acc[e] = ld4(W, (size_t)(4 * iq + e) * ld + 4 * jq);
+            // all B panel columns: those past b are zero in PcT and Prow, so
+            // the loop needs no bound and its loads can be issued early
 #pragma unroll
             for (int c = 0; c < B; ++c) {
-                if (c >= b) break;
-                C r = 0;
+                const Q4<C> a = ld4(PcT, (size_t)c * ld + 4 * iq);
+                const Q4<C> r = ld4(Prow, (size_t)c * ld + 4 * jq);
 #pragma unroll
-                for (int d = 0; d < B; ++d) r += Dp[c * B + d] * xr[d];
-                Prow[c * q + j] = k_col ? C(0) : r;
+                for (int e = 0; e < 4; ++e)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) acc[e].v[f] -= a.v[e] * r.v[f];
             }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) st4(W, (size_t)(4 * iq + e) * ld + 4 * jq, acc[e]);
         }
-        for (int i = tid; i < q; i += nthr) {
-            if (inK(i)) continue;
-            C xc[B];   // this row's panel entries; zero past the panel's b columns
+        for (int c = warp; c < b; c += nw)
+            for (int jq = lane; jq < nq; jq += 32) {
+                Q4<C> w = ld4(Prow, (size_t)c * ld + 4 * jq);
 #pragma unroll
-            for (int d = 0; d < B; ++d) xc[d] = d < b ? Pcol[i * B + d] : C(0);
-#pragma unroll
-            for (int c = 0; c < B; ++c) {
-                C r = 0;
-#pragma unroll
-                for (int d = 0; d < B; ++d) r += xc[d] * Dp[d * B + c];
-                Cn[i * B + c] = -r;
-            }
-        }
-        __syncthreads();
-        // 3. rank-b update of the rows outside K (columns inside K see R = 0)
-        {
-            C Rr[kCols][B];
-#pragma unroll
-            for (int cc = 0; cc < kCols; ++cc) {
-                const int j = lane + 32 * cc;
-#pragma unroll
-                for (int c = 0; c < B; ++c) Rr[cc][c] = (j < q && c < b) ? Prow[c * q + j] : C(0);
-            }
-            for (int i = warp; i < q; i += nw) {
-                if (inK(i)) continue;
-                C pc[B];
-#pragma unroll
-                for (int c = 0; c < B; ++c) pc[c] = c < b ? Pcol[i * B + c] : C(0);
-                C* Wi = W + (size_t)i * q;
-#pragma unroll
-                for (int cc = 0; cc < kCols; ++cc) {
-                    const int j = lane + 32 * cc;
-                    if (j >= q) break;
-                    C w = Wi[j];
-#pragma unroll
-                    for (int c = 0; c < B; ++c) w -= pc[c] * Rr[cc][c];
-                    Wi[j] = w;
+                for (int f = 0; f < 4; ++f) {
+                    const int j = 4 * jq + f;
+                    if (inK(j)) w.v[f] = Dp[c * B + (j - k0)];
                 }
-                for (int j = lane + 32 * kCols; j < q; j += 32) {
-                    C w = Wi[j];
-#pragma unroll
-                    for (int c = 0; c < B; ++c) w -= pc[c] * (c < b ? Prow[c * q + j] : C(0));
-                    Wi[j] = w;
-                }
+                st4(W, (size_t)(k0 + c) * ld + 4 * jq, w);
             }
-        }
-        __syncthreads();
-        // 4. the swept panel: rows D^-1 W[K][j], columns -W[i][K] D^-1, block D^-1
-        for (int t = tid; t < b * q; t += nthr) {
-            const int c = t / q, j = t - c * q;
-            W[(size_t)(k0 + c) * q + j] = inK(j) ? Dp[c * B + (j - k0)] : Prow[c * q + j];
-        }
-        for (int t = tid; t < q * b; t += nthr) {
-            const int i = t / b, c = t - i * b;
-            if (!inK(i)) W[(size_t)i * q + k0 + c] = Cn[i * B + c];
-        }
         __syncthreads();
     }
-    for (int t = tid; t < qq; t += nthr) {
-        const int i = t / q, j = t - i * q;
-        Minv[t] = C(0.5) * (W[t] + W[(size_t)j * q + i]);
-    }
+    for (int i = warp; i < q; i += nw)
+        for (int j = lane; j < q; j += 32) Minv[(size_t)i * q + j] = C(0.5) * (W[(size_t)i * ld + j] + W[(size_t)j * ld + i]);
 }
 
 // T = Minv f with T_0 = 0, then shifted to zero mean.  Executed by every

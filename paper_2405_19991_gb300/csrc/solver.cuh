@@ -545,7 +545,7 @@ class Solver : public SolverBase {
         }
         if (nlev == 1) OTM_TRY(alloc(Al[0], (size_t)CL<S>::AW * Nl[0]));
         const size_t m = Nl[nlev - 1];
-        OTM_TRY(alloc(Wd, (m - 1) * (m - 1)));
+        OTM_TRY(alloc(Wd, (size_t)inv_ld((int)m - 1) * inv_ld((int)m - 1)));   // row stride padded to 4
         OTM_TRY(alloc(Minv, (m - 1) * (m - 1)));
         {
             // the coarsest inverse keeps its working matrix in shared memory
