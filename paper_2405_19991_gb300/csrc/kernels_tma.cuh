@@ -677,7 +677,7 @@ static bool tma_launch_shape(TmaLaunch& L, int n, int sm_count, int max_blocks) 
             if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem) != cudaSuccess)
                 return false;
             // OTM_TMA_CARVEOUT=p: prefer p % of the unified L1 / shared array as
-            // shared memory (default: the driver's choice)
+            // shared memory (default: the CUDA runtime's choice)
             if (const char* cv = getenv("OTM_TMA_CARVEOUT"))
                 cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, atoi(cv));
             granted[ki][d] = L.smem;
