@@ -56,6 +56,11 @@ int main(void) {
          offsetof(otm_params, seed), offsetof(otm_params, stream), offsetof(otm_params, device));
   printf("%zu %zu %zu\n", offsetof(otm_step_info, cg_iters), offsetof(otm_step_info, resid),
          offsetof(otm_step_info, stage_ms));
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(otm_config), offsetof(otm_config, tune_us),
+         offsetof(otm_config, gs_form), offsetof(otm_config, gs_stages), offsetof(otm_config, head_form),
+         offsetof(otm_config, gs_tune_us));
+  printf("%zu %zu %zu\n", offsetof(otm_params, optimizer), offsetof(otm_params, mma_eps),
+         offsetof(otm_params, mma_d));
   return 0;
 }
 ''')
@@ -69,6 +74,12 @@ int main(void) {
     assert s == [ctypes.sizeof(P), ctypes.sizeof(I), ctypes.sizeof(G)]
     assert o1 == [P.cg_maxit.offset, P.fixed_volume.offset, P.seed.offset, P.stream.offset, P.device.offset]
     assert o2 == [I.cg_iters.offset, I.resid.offset, I.stage_ms.offset]
+    Cf = otm.otm_config
+    o3 = [int(v) for v in lines[3].split()]
+    assert o3 == [ctypes.sizeof(Cf), Cf.tune_us.offset, Cf.gs_form.offset, Cf.gs_stages.offset,
+                  Cf.head_form.offset, Cf.gs_tune_us.offset]
+    o4 = [int(v) for v in lines[4].split()]
+    assert o4 == [P.optimizer.offset, P.mma_eps.offset, P.mma_d.offset]
 
 
 def test_check_target_on_the_papers_traversal_grid():
